@@ -1,0 +1,390 @@
+"""FP64 CPU oracle of the ray-parameterized reverberation hot path.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg are the only users.  The product path never imports this package,
+and this package never imports the product package.  Inputs come from the seeded
+scene generator (a module that holds none of the method's arithmetic).
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, built with gcc
+without FMA contraction); this file only marshals arguments through ctypes.
+Which paper passage each function follows is stated in ``oracle.c``.
+
+Pins of every function against something other than itself (closed forms,
+library routines, brute force, physical invariants) are in
+``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "mlp.c")]
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+MAXB = 8
+MAXK = 16
+ST_COUNT = 48
+EP_COUNT = 32
+DIRECT_STRIDE = 21
+RANGE_NAMES = {0: "none", 1: "T30", 2: "T20", 3: "T10"}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (C11, -O2, no FMA contraction, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    srcs = [s for s in _SRC if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp, *srcs, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _TraceParams(C.Structure):
+    _fields_ = [
+        ("num_rays", C.c_int64),
+        ("max_order", C.c_int32),
+        ("sh_order", C.c_int32),
+        ("num_bins", C.c_int32),
+        ("min_order", C.c_int32),
+        ("ir_rate_hz", C.c_double),
+        ("speed_of_sound", C.c_double),
+        ("source_radius", C.c_double),
+        ("seed", C.c_uint64),
+        ("scene_id", C.c_uint32),
+        ("budget_refill", C.c_int32),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = C.CDLL(_LIB_PATH)
+        P = C.POINTER
+        dp, fp, ip = P(C.c_double), P(C.c_float), P(C.c_int)
+        lib.orc_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+        lib.orc_sh_eval.argtypes = [C.c_int, dp, dp]
+        lib.orc_intersect_tri.argtypes = [dp, dp, dp, dp, dp, dp]
+        lib.orc_intersect_tri.restype = C.c_int
+        lib.orc_scene_create.argtypes = [fp, C.c_int, ip, C.c_int, ip, fp, fp, C.c_int, C.c_int,
+                                         C.c_double, C.c_int]
+        lib.orc_scene_create.restype = C.c_void_p
+        lib.orc_scene_destroy.argtypes = [C.c_void_p]
+        lib.orc_scene_tmin.argtypes = [C.c_void_p]
+        lib.orc_scene_tmin.restype = C.c_double
+        lib.orc_scene_num_nodes.argtypes = [C.c_void_p]
+        lib.orc_closest_hit.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_double, C.c_int, dp]
+        lib.orc_closest_hit.restype = C.c_int
+        lib.orc_any_hit.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_double, C.c_int]
+        lib.orc_any_hit.restype = C.c_int
+        lib.orc_trace_rays.argtypes = [C.c_void_p, P(_TraceParams), dp, dp, C.c_int, C.c_int64,
+                                       C.c_int64, dp, dp, P(C.c_uint64)]
+        lib.orc_trace.argtypes = [C.c_void_p, P(_TraceParams), dp, dp, C.c_int, dp, dp,
+                                  P(C.c_uint64), C.c_int64]
+        lib.orc_trace.restype = C.c_int
+        lib.orc_direct.argtypes = [C.c_void_p, P(_TraceParams), dp, dp, C.c_int, dp]
+        lib.orc_next_wave.argtypes = [C.c_int64, C.c_int, C.c_double]
+        lib.orc_next_wave.restype = C.c_int64
+        lib.orc_estimate.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                     C.c_double, C.c_double, dp, dp]
+        lib.orc_mean_free_path.argtypes = [dp]
+        lib.orc_mean_free_path.restype = C.c_double
+        if hasattr(lib, "orc_mlp_forward"):
+            _bind_mlp(lib)
+        _lib = lib
+        return lib
+
+
+def _bind_mlp(lib):
+    P = C.POINTER
+    dp = P(C.c_double)
+    lib.orc_mlp_forward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp]
+    lib.orc_mlp_loss_grad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp,
+                                      dp, dp]
+    lib.orc_mlp_loss_grad.restype = C.c_double
+    lib.orc_adamw_step.argtypes = [C.c_int64, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, C.c_int]
+
+
+def _d(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _i(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+# ----------------------------------------------------------------------------
+# elementary functions
+# ----------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block of counter ctr (4 x u32) under key (2 x u32)."""
+    lib = _load()
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (C.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def sh_eval(order: int, direction) -> np.ndarray:
+    """Real orthonormal SH (Condon-Shortley phase, ACN order) of one direction."""
+    lib = _load()
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    Y = np.zeros((order + 1) ** 2, dtype=np.float64)
+    lib.orc_sh_eval(order, _d(d), _d(Y))
+    return Y
+
+
+def intersect_tri(o, d, v0, v1, v2):
+    lib = _load()
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (o, d, v0, v1, v2)]
+    t = np.zeros(1)
+    hit = lib.orc_intersect_tri(*[_d(a) for a in arrs], _d(t))
+    return float(t[0]) if hit else None
+
+
+# ----------------------------------------------------------------------------
+# scene
+# ----------------------------------------------------------------------------
+class OracleScene:
+    """The mesh and materials in double precision; use_bvh=False means brute force."""
+
+    def __init__(self, verts, tris, tri_material, absorption, scattering, ray_eps=0.0,
+                 use_bvh=None):
+        lib = _load()
+        self._v = np.ascontiguousarray(verts, dtype=np.float32)
+        self._t = np.ascontiguousarray(tris, dtype=np.int32)
+        self._m = np.ascontiguousarray(tri_material, dtype=np.int32)
+        self._a = np.ascontiguousarray(absorption, dtype=np.float32)
+        self._s = np.ascontiguousarray(scattering, dtype=np.float32)
+        self.B = int(self._a.shape[1])
+        if use_bvh is None:
+            use_bvh = self._t.shape[0] > 64
+        self.use_bvh = bool(use_bvh)
+        self._h = lib.orc_scene_create(_f(self._v), self._v.shape[0], _i(self._t), self._t.shape[0],
+                                       _i(self._m), _f(self._a), _f(self._s), self._a.shape[0],
+                                       self.B, float(ray_eps), int(self.use_bvh))
+        if not self._h:
+            raise ValueError("oracle rejected the scene")
+
+    @classmethod
+    def from_scene(cls, sc, **kw):
+        return cls(sc.verts, sc.tris, sc.tri_material, sc.absorption, sc.scattering, **kw)
+
+    @property
+    def tmin(self) -> float:
+        return float(_load().orc_scene_tmin(self._h))
+
+    def closest_hit(self, o, d, tmin=None, tmax=np.inf, exclude=-1):
+        lib = _load()
+        o = np.ascontiguousarray(o, np.float64)
+        d = np.ascontiguousarray(d, np.float64)
+        t = np.zeros(1)
+        tri = lib.orc_closest_hit(self._h, _d(o), _d(d), self.tmin if tmin is None else tmin,
+                                  float(tmax), int(exclude), _d(t))
+        return (tri, float(t[0])) if tri >= 0 else (-1, np.inf)
+
+    def any_hit(self, o, d, tmin=None, tmax=np.inf, exclude=-1) -> bool:
+        lib = _load()
+        o = np.ascontiguousarray(o, np.float64)
+        d = np.ascontiguousarray(d, np.float64)
+        return bool(lib.orc_any_hit(self._h, _d(o), _d(d), self.tmin if tmin is None else tmin,
+                                    float(tmax), int(exclude)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.orc_scene_destroy(self._h)
+            self._h = None
+
+
+# ----------------------------------------------------------------------------
+# trace, direct sound, estimator
+# ----------------------------------------------------------------------------
+@dataclass
+class TraceParams:
+    num_rays: int = 10000
+    max_order: int = 20
+    sh_order: int = 1
+    num_bins: int = 1000
+    min_order: int = 1
+    ir_rate_hz: float = 1000.0
+    speed_of_sound: float = 343.0
+    source_radius: float = 0.5
+    seed: int = 0xC0FFEE
+    scene_id: int = 0
+    budget_refill: int = 0
+
+    def c(self) -> _TraceParams:
+        return _TraceParams(int(self.num_rays), int(self.max_order), int(self.sh_order),
+                            int(self.num_bins), int(self.min_order), float(self.ir_rate_hz),
+                            float(self.speed_of_sound), float(self.source_radius),
+                            int(self.seed) & 0xFFFFFFFFFFFFFFFF, int(self.scene_id) & 0xFFFFFFFF,
+                            int(self.budget_refill))
+
+
+STAT_NAMES = {
+    "escaped": (0, 8), "absorbed": (8, 16), "remaining": (16, 24), "late": (24, 32),
+}
+STAT_SCALARS = {
+    "mfp_sum": 32, "mfp_count": 33, "mfp_sum_np": 34, "mfp_count_np": 35, "segments": 36,
+    "shadow_rays": 37, "primaries": 38, "contributions": 39, "sphere_hits": 40, "waves": 41,
+}
+
+
+def stats_dict(st: np.ndarray, B: int) -> dict:
+    out = {k: st[a:a + B].copy() for k, (a, _) in STAT_NAMES.items()}
+    out.update({k: float(st[i]) for k, i in STAT_SCALARS.items()})
+    out["mean_free_path"] = out["mfp_sum"] / out["mfp_count"] if out["mfp_count"] else np.nan
+    out["mean_free_path_np"] = (out["mfp_sum_np"] / out["mfp_count_np"]
+                                if out["mfp_count_np"] else np.nan)
+    return out
+
+
+def _src_arrays(listener, sources):
+    lis = np.ascontiguousarray(listener, dtype=np.float64).reshape(3)
+    src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
+    return lis, src
+
+
+def trace(scene: OracleScene, p: TraceParams, listener, sources, hash_cap: int = 0):
+    """Single-threaded trace step.  Returns (H [S,B,K,T] float64, stats dict, hashes)."""
+    lib = _load()
+    lis, src = _src_arrays(listener, sources)
+    S, B, K, T = src.shape[0], scene.B, (p.sh_order + 1) ** 2, p.num_bins
+    H = np.zeros((S, B, K, T))
+    st = np.zeros(ST_COUNT)
+    hashes = np.zeros(max(hash_cap, 1), dtype=np.uint64)
+    cp = p.c()
+    lib.orc_trace(scene._h, C.byref(cp), _d(lis), _d(src), S, _d(H), _d(st),
+                  hashes.ctypes.data_as(C.POINTER(C.c_uint64)) if hash_cap else None, int(hash_cap))
+    return H, stats_dict(st, B), hashes[:hash_cap]
+
+
+def trace_rays(scene: OracleScene, p: TraceParams, listener, sources, begin: int, end: int,
+               want_hash: bool = False):
+    """Raw (un-normalised) sums over primaries [begin, end): (H_raw, stats array, hashes)."""
+    lib = _load()
+    lis, src = _src_arrays(listener, sources)
+    S, B, K, T = src.shape[0], scene.B, (p.sh_order + 1) ** 2, p.num_bins
+    H = np.zeros((S, B, K, T))
+    st = np.zeros(ST_COUNT)
+    hashes = np.zeros(max(end - begin, 1), dtype=np.uint64)
+    cp = p.c()
+    lib.orc_trace_rays(scene._h, C.byref(cp), _d(lis), _d(src), S, int(begin), int(end), _d(H),
+                       _d(st), hashes.ctypes.data_as(C.POINTER(C.c_uint64)) if want_hash else None)
+    return H, st, hashes[: end - begin]
+
+
+def trace_parallel(scene: OracleScene, p: TraceParams, listener, sources, threads: int = 0,
+                   chunk: int = 0, hash_cap: int = 0):
+    """The same step as `trace`, with each wave's primaries split into contiguous
+    chunks traced by threads (ctypes releases the GIL).  Partial sums are added in
+    chunk order, so the result differs from `trace` only by FP64 rounding order."""
+    threads = threads or os.cpu_count() or 1
+    lis, src = _src_arrays(listener, sources)
+    S, B, K, T = src.shape[0], scene.B, (p.sh_order + 1) ** 2, p.num_bins
+    H = np.zeros((S, B, K, T))
+    st = np.zeros(ST_COUNT)
+    hashes = np.zeros(max(hash_cap, 1), dtype=np.uint64)
+    begin, count, waves = 0, int(p.num_rays), 0
+    lib = _load()
+    while count > 0:
+        csz = chunk or max(1, -(-count // (threads * 4)))
+        ranges = [(a, min(a + csz, begin + count)) for a in range(begin, begin + count, csz)]
+        results: list = [None] * len(ranges)
+        nxt = [0]
+        lk = threading.Lock()
+
+        def worker():
+            while True:
+                with lk:
+                    i = nxt[0]
+                    nxt[0] += 1
+                if i >= len(ranges):
+                    return
+                a, b = ranges[i]
+                results[i] = trace_rays(scene, p, lis, src, a, b, want_hash=hash_cap > a)
+
+        ths = [threading.Thread(target=worker) for _ in range(min(threads, len(ranges)))]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        for (a, b), (h, s, hh) in zip(ranges, results):
+            H += h
+            st += s
+            if hash_cap > a:
+                n = min(b, hash_cap) - a
+                hashes[a:a + n] = hh[:n]
+        begin += count
+        waves += 1
+        count = (int(lib.orc_next_wave(int(p.num_rays), int(p.max_order), float(st[36])))
+                 if p.budget_refill else 0)
+    st[41] = waves
+    kp = st[38]
+    if kp > 0:
+        H /= kp
+        st[24:32] /= kp
+    if p.min_order == 0:
+        dd = direct(scene, p, lis, src)
+        for s in range(S):
+            if dd["visible"][s] and dd["bin"][s] < T:
+                H[s, :, :, int(dd["bin"][s])] += dd["sh"][s][None, :K]
+    return H, stats_dict(st, B), hashes[:hash_cap]
+
+
+def direct(scene: OracleScene, p: TraceParams, listener, sources) -> dict:
+    lib = _load()
+    lis, src = _src_arrays(listener, sources)
+    S = src.shape[0]
+    K = (p.sh_order + 1) ** 2
+    out = np.zeros((S, DIRECT_STRIDE))
+    cp = p.c()
+    lib.orc_direct(scene._h, C.byref(cp), _d(lis), _d(src), S, _d(out))
+    return {"visible": out[:, 0] > 0, "dist": out[:, 1], "time": out[:, 2], "energy": out[:, 3],
+            "bin": out[:, 4].astype(np.int64), "sh": out[:, 5:5 + K].copy()}
+
+
+EP_FIELDS = ["rt60_raw", "rt60_smoothed", "fit_hi_db", "fit_lo_db", "fit_r2", "slope_db_per_s",
+             "intercept_db", "i_total", "g_reverb", "e_direct", "drr_db", "predelay_s",
+             "range_kind", "n_fit", "fit_j0", "fit_j1"]
+
+
+def estimate(H, e_direct, ir_rate_hz: float, dt_update: float = 0.0, tau: float = 0.0,
+             state=None) -> dict:
+    """Reverb parameters per (source, band) from H [S,B,K,T] (float64 view taken)."""
+    lib = _load()
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    S, B, K, T = H.shape
+    ed = np.ascontiguousarray(e_direct if e_direct is not None else np.zeros(S), np.float64)
+    out = np.zeros((S, B, EP_COUNT))
+    st = None
+    if state is not None:
+        st = state if (isinstance(state, np.ndarray) and state.dtype == np.float64
+                       and state.flags.c_contiguous) else np.ascontiguousarray(state, np.float64)
+    lib.orc_estimate(_d(H), _d(ed), S, B, K, T, float(ir_rate_hz), float(dt_update), float(tau),
+                     _d(out), _d(st) if st is not None else None)
+    res = {name: out[:, :, i].copy() for i, name in enumerate(EP_FIELDS)}
+    res["xbar"] = out[:, :, 16:16 + K].copy()
+    res["range_kind"] = res["range_kind"].astype(np.int64)
+    return res
