@@ -1,0 +1,275 @@
+/*
+ * rpr.h -- C ABI of the GB300 ray-parameterized reverberation library.
+ *
+ * The library computes, on one GPU, the sound-propagation and parameter-estimation
+ * hot path of "Interactive Sound Rendering on Mobile Devices using
+ * Ray-Parameterized Reverberation Filters" (Schissler & Manocha):
+ *
+ *   rp_scene_create  builds a bounding-volume hierarchy of the scene mesh on the
+ *                    device (the paper's ray tracer, Section 6 "Performance", does
+ *                    not describe its acceleration structure).
+ *   rp_trace         backward path tracing from the listener with diffuse rain
+ *                    (next-event estimation) at every reflection (Section 5, "Sound
+ *                    Propagation"), binned into a low-rate energy impulse response
+ *                    per source and band together with its spherical-harmonic
+ *                    projection X_lm(t) (Section 4.2 first paragraph; Table of
+ *                    symbols), plus direct sound (Section 5) and the mean free path
+ *                    statistic (Section 4.2 "Reflection Density").
+ *   rp_estimate      per-band reverberation parameters from those IRs (Section 4.2):
+ *                    RT60 by backward energy integration and a least-squares decay
+ *                    fit, its exponential smoothing (RT60 smoothing equation), total
+ *                    intensity and reverberator gain (Eq. reverb_gain with
+ *                    I_reverb^total = RT60 / (6 ln 10)), predelay, direct-to-
+ *                    reverberant ratio and the weighted average directivity of
+ *                    Section 4.1 ("Directional Loudness").
+ *   rp_update        trace + estimate with host buffers (copies included).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an int status: RP_OK (0) or a negative RP_ERR_* code.
+ *     Nothing throws across the ABI.  rp_status_string() names a code.
+ *   - Work is enqueued asynchronously on the context's CUDA stream.  Errors that
+ *     kernels detect (capacity, traversal stack, iteration cap) are recorded in a
+ *     device status word and returned by rp_sync_status(), which synchronises the
+ *     stream.  Device pointers passed in must stay valid until then.
+ *   - The caller owns every output buffer; the library owns rp_ctx and rp_scene
+ *     objects and its internal workspace, released by the matching destroy call.
+ *   - Arrays are dense, row-major, in the index order written next to them.
+ *   - A context is not thread-safe: one host thread at a time per rp_ctx.
+ *   - Limits: bands B <= RP_MAX_BANDS, SH order n <= RP_MAX_SH_ORDER
+ *     (K = (n+1)^2 <= RP_MAX_SH), sources S <= RP_MAX_SOURCES.
+ */
+#ifndef RPR_H
+#define RPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RP_MAX_BANDS 8
+#define RP_MAX_SH_ORDER 3
+#define RP_MAX_SH 16
+#define RP_MAX_SOURCES 4096
+
+enum {
+    RP_OK = 0,
+    RP_ERR_INVALID_ARG = -1,    /* a pointer, size or parameter is out of range */
+    RP_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+    RP_ERR_OOM = -3,            /* device memory allocation failed */
+    RP_ERR_CAPACITY = -4,       /* an internal buffer overflowed; results incomplete */
+    RP_ERR_STACK_OVERFLOW = -5, /* BVH traversal stack overflowed; results incomplete */
+    RP_ERR_TIMEOUT = -6,        /* a traversal exceeded its iteration cap */
+    RP_ERR_NAN_INPUT = -7,      /* a vertex, material or position is not finite */
+    RP_ERR_EMPTY_SCENE = -8,    /* zero triangles */
+    RP_ERR_NO_DEVICE = -9       /* no CUDA device or wrong architecture */
+};
+
+/* Where an input array lives. */
+enum { RP_MEM_HOST = 0, RP_MEM_DEVICE = 1 };
+
+/* rp_trace_params.flags */
+enum {
+    RP_FLAG_RAY_HASH = 1,      /* write one 64-bit FNV-1a hash of each primary ray's
+                                  triangle sequence (debug/divergence checks) */
+    RP_FLAG_COUNT_VISITS = 2,  /* count BVH node visits and triangle tests in stats */
+    RP_FLAG_DEVICE_POSITIONS = 4, /* listener and sources are device pointers */
+    RP_FLAG_FP32_PATHS = 8       /* carry path origin, direction and length in FP32 instead
+                                    of FP64 (faster; paths drift from the FP64 reference
+                                    after tens of reflections) */
+};
+
+typedef struct rp_ctx rp_ctx;
+typedef struct rp_scene rp_scene;
+
+/* Scene mesh with frequency-dependent materials (Section 5 uses 4 bands).
+ * Surfaces are two-sided; triangle winding is not used.  All five arrays are in
+ * the memory named by `memory`; they are copied, the caller keeps ownership. */
+typedef struct {
+    const float *verts;          /* [num_verts][3] metres */
+    const int32_t *tris;         /* [num_tris][3] vertex indices */
+    const int32_t *tri_material; /* [num_tris] material index */
+    const float *absorption;     /* [num_materials][num_bands] alpha in [0,1] */
+    const float *scattering;     /* [num_materials][num_bands] s in [0,1] */
+    int32_t num_verts;
+    int32_t num_tris;
+    int32_t num_materials;
+    int32_t num_bands;           /* B, 1..RP_MAX_BANDS */
+    int32_t memory;              /* RP_MEM_HOST or RP_MEM_DEVICE */
+    float ray_epsilon;           /* self-intersection guard t_min; 0 = 1e-6 x bbox diagonal */
+} rp_mesh_desc;
+
+typedef struct {
+    int32_t num_tris;
+    int32_t num_nodes;     /* internal BVH nodes */
+    int32_t max_depth;     /* deepest leaf */
+    int32_t num_bands;
+    float bounds_lo[3];
+    float bounds_hi[3];
+    float ray_epsilon;     /* t_min used by every ray */
+    float build_ms;        /* device time of the BVH build */
+} rp_scene_info;
+
+/* One trace step (Section 5): num_rays primaries from the listener, each followed to
+ * max_order reflections.  At every reflection of order >= min_order a shadow ray to
+ * each source adds the diffusely reflected direct energy; after a specular
+ * continuation the next segment also tests the sources as spheres of radius
+ * source_radius.  Contributions land in bin floor(t * ir_rate_hz), t = path length / c.
+ * Random numbers: Philox4x32-10, counter (ray id, scene_id, bounce, 0), key = seed. */
+typedef struct {
+    uint64_t num_rays;        /* N primaries (first wave) */
+    uint64_t seed;            /* Philox key (lo, hi words) */
+    uint64_t first_ray;       /* id of the first primary: rays first_ray .. first_ray + N - 1
+                                 (a shard of a larger ray budget); 0 normally */
+    int32_t max_order;        /* M reflections per path, >= 0 */
+    int32_t sh_order;         /* n, 0..RP_MAX_SH_ORDER */
+    int32_t num_bins;         /* T histogram bins, >= 1 */
+    int32_t min_order;        /* reflections of lower order are not binned; 0 bins direct sound */
+    float ir_rate_hz;         /* IR sample rate (the paper uses 100 Hz) */
+    float speed_of_sound;     /* c, m/s */
+    float source_radius;      /* r_s, m, > 0 */
+    uint32_t scene_id;        /* Philox counter word 1 */
+    int32_t budget_refill;    /* 1: spend the unused part of the N*M segment budget on
+                                 extra primaries, in deterministic waves (Section 5) */
+    int32_t flags;            /* RP_FLAG_* */
+} rp_trace_params;
+
+/* Direct sound of one source (Section 5, reduced to a point source): visible when the
+ * listener-source segment is unoccluded; energy 1/(4 pi d^2) per unit source power in
+ * every band, arrival d/c, SH of the direction toward the source times the energy. */
+typedef struct {
+    int32_t visible;
+    int32_t bin;          /* floor(time * ir_rate_hz) */
+    float dist;
+    float time;
+    float energy;
+    float sh[RP_MAX_SH];  /* energy * Y_k(direction), k < K */
+} rp_direct;
+
+/* Tracer statistics (totals over the whole step, un-normalised unless stated). */
+typedef struct {
+    double escaped[RP_MAX_BANDS];    /* path weight leaving the scene */
+    double absorbed[RP_MAX_BANDS];   /* path weight absorbed by surfaces */
+    double remaining[RP_MAX_BANDS];  /* path weight alive after max_order reflections */
+    double late[RP_MAX_BANDS];       /* binned energy that fell beyond the last bin,
+                                        normalised like H */
+    double mfp_sum;                  /* lengths of segments that ended on a surface */
+    double mfp_sum_np;               /* the same without primary segments */
+    uint64_t mfp_count;
+    uint64_t mfp_count_np;
+    uint64_t segments;               /* closest-hit rays traced (the segment budget) */
+    uint64_t shadow_rays;            /* next-event (diffuse rain) shadow rays traced */
+    uint64_t primaries;              /* K primaries over all waves; H is divided by K */
+    uint64_t contributions;          /* shadow + sphere contributions (binned or late) */
+    uint64_t sphere_hits;
+    uint64_t waves;
+    uint64_t node_visits[2];         /* with RP_FLAG_COUNT_VISITS: BVH nodes visited by
+                                        [0] closest-hit segments, [1] shadow rays */
+    uint64_t tri_tests[2];           /* with RP_FLAG_COUNT_VISITS: triangle tests, same split */
+    uint64_t hits_stored;            /* reflections kept for next-event estimation */
+    int32_t error;                   /* first RP_ERR_* raised by a kernel, or 0 */
+    int32_t reserved;
+} rp_trace_stats;
+
+typedef struct {
+    double ir_rate_hz;   /* rate of the histogram */
+    double dt_update;    /* seconds since the previous update (smoothing) */
+    double tau;          /* smoothing time constant tau, s (paper: 3 s for late reverb);
+                            0 disables smoothing */
+} rp_estimate_params;
+
+/* Reverberation parameters of one (source, band), Section 4.2. */
+typedef struct {
+    double rt60_raw;        /* -60 / slope of the least-squares fit; NaN without a fit */
+    double rt60_smoothed;   /* exponential smoothing with alpha = 1 - exp(-dt/tau) */
+    double fit_hi_db;       /* fit window upper level (-5, -5 or 0 dB) */
+    double fit_lo_db;       /* fit window lower level (-35, -25 or -10 dB) */
+    double fit_r2;
+    double slope_db_per_s;
+    double intercept_db;
+    double i_total;         /* sum over bins of I(t) */
+    double g_reverb;        /* sqrt(i_total / (rt60 / (6 ln 10))) */
+    double e_direct;        /* direct energy of the source */
+    double drr_db;          /* 10 log10(e_direct / i_total) */
+    double predelay_s;      /* first bin non-zero in any band / rate */
+    int32_t range_kind;     /* 0 none, 1 T30 (-5..-35 dB), 2 T20 (-5..-25), 3 T10 (0..-10) */
+    int32_t n_fit;
+    int32_t fit_j0;
+    int32_t fit_j1;
+    double xbar[RP_MAX_SH]; /* sum_t X_lm(t) / sum_t I(t), k < K */
+} rp_reverb_params;
+
+/* Per-kernel device time collected while profiling is enabled. */
+typedef struct {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+} rp_kernel_time;
+
+const char *rp_status_string(int status);
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *out is owned by the caller
+ * until rp_destroy.  Fails with RP_ERR_NO_DEVICE when the device is absent. */
+int rp_create(rp_ctx **out, int device, void *cuda_stream);
+int rp_destroy(rp_ctx *ctx);
+int rp_set_stream(rp_ctx *ctx, void *cuda_stream);
+
+/* Copy the mesh to the device and build its BVH (Morton codes, radix sort,
+ * hierarchy, bottom-up bounds, all on the device).  Non-finite vertices or
+ * materials give RP_ERR_NAN_INPUT, zero triangles RP_ERR_EMPTY_SCENE, an index out
+ * of range RP_ERR_INVALID_ARG.  Synchronises the stream before returning. */
+int rp_scene_create(rp_ctx *ctx, const rp_mesh_desc *mesh, rp_scene **out);
+int rp_scene_destroy(rp_scene *scene);
+int rp_scene_info_get(const rp_scene *scene, rp_scene_info *out);
+
+/* Reserve the workspace one rp_trace of these sizes needs, so that later calls
+ * (and CUDA graph capture of them) allocate nothing. */
+int rp_trace_reserve(rp_scene *scene, const rp_trace_params *params, int32_t num_sources);
+
+/* One trace step.
+ *   listener  float[3], sources float[num_sources][3]: host memory, or device memory
+ *             with RP_FLAG_DEVICE_POSITIONS.
+ *   H         device float[S][B][K][T], overwritten: X_{b,k}(t) per source, with
+ *             I_b(t) = sqrt(4 pi) * H[s][b][0][t]; normalised per primary ray.
+ *   direct    device rp_direct[S] or NULL.
+ *   stats     device rp_trace_stats or NULL (zeroed and filled).
+ *   ray_hash  device uint64[num_rays] or NULL (with RP_FLAG_RAY_HASH): hashes of
+ *             primaries of the first wave.
+ * Allocates workspace on first use for these sizes (see rp_trace_reserve). */
+int rp_trace(rp_scene *scene, const rp_trace_params *params, const float *listener,
+             const float *sources, int32_t num_sources, float *H, rp_direct *direct,
+             rp_trace_stats *stats, uint64_t *ray_hash);
+
+/* Estimate reverb parameters from device H [S][B][K][T] (K = (n+1)^2).
+ *   direct  device rp_direct[S] or NULL (then e_direct = 0).
+ *   out     device rp_reverb_params[S][B].
+ *   state   device double[S][B] smoothing state or NULL; NaN entries mean "no
+ *           previous value".  Updated in place. */
+int rp_estimate(rp_ctx *ctx, const float *H, const rp_direct *direct, int32_t num_sources,
+                int32_t num_bands, int32_t num_sh, int32_t num_bins,
+                const rp_estimate_params *params, rp_reverb_params *out, double *state);
+
+/* Trace + estimate with HOST buffers: positions are copied in, H, parameters, direct
+ * sound and stats are copied out (any output pointer may be NULL).  state is a host
+ * double[S][B] or NULL.  Returns after the results are in host memory. */
+int rp_update(rp_scene *scene, const rp_trace_params *params,
+              const rp_estimate_params *est, const float *listener, const float *sources,
+              int32_t num_sources, float *H_host, rp_reverb_params *params_host,
+              rp_direct *direct_host, rp_trace_stats *stats_host, double *state_host);
+
+/* Synchronise the context stream and return the first device-side error (or a CUDA
+ * error).  Clears the recorded device error. */
+int rp_sync_status(rp_ctx *ctx);
+
+/* Kernel timing with CUDA events on the context stream (off by default). */
+int rp_profile_enable(rp_ctx *ctx, int enable);
+int rp_profile_reset(rp_ctx *ctx);
+int rp_profile_read(rp_ctx *ctx, rp_kernel_time *out, int32_t max_entries, int32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPR_H */

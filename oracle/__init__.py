@@ -65,6 +65,7 @@ class _TraceParams(C.Structure):
         ("seed", C.c_uint64),
         ("scene_id", C.c_uint32),
         ("budget_refill", C.c_int32),
+        ("first_ray", C.c_int64),
     ]
 
 
@@ -98,6 +99,9 @@ def _load():
                                   P(C.c_uint64), C.c_int64]
         lib.orc_trace.restype = C.c_int
         lib.orc_direct.argtypes = [C.c_void_p, P(_TraceParams), dp, dp, C.c_int, dp]
+        lib.orc_trace_ray_log.argtypes = [C.c_void_p, P(_TraceParams), dp, dp, C.c_int, C.c_uint64, dp, dp,
+                                          ip, dp, dp, dp]
+        lib.orc_trace_ray_log.restype = C.c_int
         lib.orc_next_wave.argtypes = [C.c_int64, C.c_int, C.c_double]
         lib.orc_next_wave.restype = C.c_int64
         lib.orc_estimate.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
@@ -233,13 +237,14 @@ class TraceParams:
     seed: int = 0xC0FFEE
     scene_id: int = 0
     budget_refill: int = 0
+    first_ray: int = 0
 
     def c(self) -> _TraceParams:
         return _TraceParams(int(self.num_rays), int(self.max_order), int(self.sh_order),
                             int(self.num_bins), int(self.min_order), float(self.ir_rate_hz),
                             float(self.speed_of_sound), float(self.source_radius),
                             int(self.seed) & 0xFFFFFFFFFFFFFFFF, int(self.scene_id) & 0xFFFFFFFF,
-                            int(self.budget_refill))
+                            int(self.budget_refill), int(self.first_ray))
 
 
 STAT_NAMES = {
@@ -306,7 +311,7 @@ def trace_parallel(scene: OracleScene, p: TraceParams, listener, sources, thread
     H = np.zeros((S, B, K, T))
     st = np.zeros(ST_COUNT)
     hashes = np.zeros(max(hash_cap, 1), dtype=np.uint64)
-    begin, count, waves = 0, int(p.num_rays), 0
+    begin, count, waves = int(p.first_ray), int(p.num_rays), 0
     lib = _load()
     while count > 0:
         csz = chunk or max(1, -(-count // (threads * 4)))
@@ -323,7 +328,7 @@ def trace_parallel(scene: OracleScene, p: TraceParams, listener, sources, thread
                 if i >= len(ranges):
                     return
                 a, b = ranges[i]
-                results[i] = trace_rays(scene, p, lis, src, a, b, want_hash=hash_cap > a)
+                results[i] = trace_rays(scene, p, lis, src, a, b, want_hash=hash_cap > a - int(p.first_ray))
 
         ths = [threading.Thread(target=worker) for _ in range(min(threads, len(ranges)))]
         for t in ths:
@@ -333,9 +338,10 @@ def trace_parallel(scene: OracleScene, p: TraceParams, listener, sources, thread
         for (a, b), (h, s, hh) in zip(ranges, results):
             H += h
             st += s
-            if hash_cap > a:
-                n = min(b, hash_cap) - a
-                hashes[a:a + n] = hh[:n]
+            a0 = a - int(p.first_ray)
+            if hash_cap > a0 >= 0:
+                n = min(b - int(p.first_ray), hash_cap) - a0
+                hashes[a0:a0 + n] = hh[:n]
         begin += count
         waves += 1
         count = (int(lib.orc_next_wave(int(p.num_rays), int(p.max_order), float(st[36])))
@@ -351,6 +357,24 @@ def trace_parallel(scene: OracleScene, p: TraceParams, listener, sources, thread
             if dd["visible"][s] and dd["bin"][s] < T:
                 H[s, :, :, int(dd["bin"][s])] += dd["sh"][s][None, :K]
     return H, stats_dict(st, B), hashes[:hash_cap]
+
+
+def trace_ray_log(scene: OracleScene, p: TraceParams, listener, sources, rid: int) -> dict:
+    """Segments of one primary ray: triangle, t, origin and direction per segment."""
+    lib = _load()
+    lis, src = _src_arrays(listener, sources)
+    S, B, K, T = src.shape[0], scene.B, (p.sh_order + 1) ** 2, p.num_bins
+    M = max(int(p.max_order), 1)
+    H = np.zeros((S, B, K, T))
+    st = np.zeros(ST_COUNT)
+    tri = np.zeros(M, np.int32)
+    t = np.zeros(M)
+    o = np.zeros((M, 3))
+    d = np.zeros((M, 3))
+    cp = p.c()
+    n = lib.orc_trace_ray_log(scene._h, C.byref(cp), _d(lis), _d(src), S, int(rid), _d(H), _d(st), _i(tri),
+                              _d(t), _d(o), _d(d))
+    return {"tri": tri[:n], "t": t[:n], "o": o[:n], "d": d[:n]}
 
 
 def direct(scene: OracleScene, p: TraceParams, listener, sources) -> dict:

@@ -433,6 +433,7 @@ typedef struct {
     uint64_t seed;         /* Philox key */
     uint32_t scene_id;     /* Philox counter word 1 */
     int32_t budget_refill; /* re-spend unused segments on extra primaries */
+    int64_t first_ray;     /* id of the first primary */
 } orc_trace_params;
 
 /* layout of the stats array (doubles) */
@@ -471,8 +472,17 @@ static void add_contrib(const orc_trace_params *p, int B, int K, int S_idx, cons
             H[(((size_t)S_idx * B + b) * K + k) * T + bin] += e[b] * Y[k];
 }
 
+/* optional per-segment record of one ray (debugging divergence): triangle, t,
+ * origin and direction of every segment */
+typedef struct {
+    int *tri;
+    double *t, *o, *d;
+    int n;
+} orc_ray_log;
+
 static void trace_ray(const orc_scene *sc, const orc_trace_params *p, const double lis[3],
-                      const double *src, int S, uint64_t rid, double *H, double *st, uint64_t *hash_out)
+                      const double *src, int S, uint64_t rid, double *H, double *st, uint64_t *hash_out,
+                      orc_ray_log *log)
 {
     const int B = sc->B, K = (p->sh_order + 1) * (p->sh_order + 1), M = p->max_order;
     uint32_t r[4];
@@ -498,6 +508,12 @@ static void trace_ray(const orc_scene *sc, const orc_trace_params *p, const doub
         double t = INFINITY;
         int tri = orc_closest_hit(sc, o, d, sc->tmin, INFINITY, prev, &t);
         st[ST_SEGMENTS] += 1.0;
+        if (log) {
+            log->tri[log->n] = tri;
+            log->t[log->n] = t;
+            for (int a = 0; a < 3; ++a) { log->o[3 * log->n + a] = o[a]; log->d[3 * log->n + a] = d[a]; }
+            log->n++;
+        }
         if (spec_prev && h - 1 >= p->min_order) {
             /* specularly reflected source image: the source as a sphere of radius
              * r_s on the segment after a specular choice [reading] */
@@ -604,7 +620,17 @@ void orc_trace_rays(const orc_scene *sc, const orc_trace_params *p, const double
                     double *st, uint64_t *ray_hash)
 {
     for (int64_t r = ray_begin; r < ray_end; ++r)
-        trace_ray(sc, p, lis, src, S, (uint64_t)r, H_raw, st, ray_hash ? &ray_hash[r - ray_begin] : NULL);
+        trace_ray(sc, p, lis, src, S, (uint64_t)r, H_raw, st, ray_hash ? &ray_hash[r - ray_begin] : NULL, NULL);
+}
+
+/* Debug: the segments of primary ray `rid` (at most max_order entries); returns
+ * the number of segments.  H_raw and st receive the ray's contributions. */
+int orc_trace_ray_log(const orc_scene *sc, const orc_trace_params *p, const double lis[3], const double *src,
+                      int S, uint64_t rid, double *H_raw, double *st, int *tri, double *t, double *o, double *d)
+{
+    orc_ray_log log = { tri, t, o, d, 0 };
+    trace_ray(sc, p, lis, src, S, rid, H_raw, st, NULL, &log);
+    return log.n;
 }
 
 /* Direct sound of a point source (reduction of Section 5's direct-sound step):
@@ -645,8 +671,8 @@ int64_t orc_next_wave(int64_t N, int M, double segments_used)
 
 /* The whole trace step: waves of primaries (one wave unless budget_refill),
  * normalisation by the number of primaries K, and direct sound binned into H
- * when min_order == 0.  H [S][B][K][T] is overwritten.  ray_hash[0..hash_cap)
- * receives the hash of rays with id < hash_cap. Returns the number of waves. */
+ * when min_order == 0.  H [S][B][K][T] is overwritten.  ray_hash[i] receives the
+ * hash of ray first_ray + i for i < hash_cap. Returns the number of waves. */
 int orc_trace(const orc_scene *sc, const orc_trace_params *p, const double lis[3], const double *src,
               int S, double *H, double *st, uint64_t *ray_hash, int64_t hash_cap)
 {
@@ -654,12 +680,13 @@ int orc_trace(const orc_scene *sc, const orc_trace_params *p, const double lis[3
     size_t nH = (size_t)S * B * K * T;
     memset(H, 0, sizeof(double) * nH);
     memset(st, 0, sizeof(double) * ST_COUNT);
-    int64_t begin = 0, count = p->num_rays;
+    int64_t begin = p->first_ray, count = p->num_rays;
     int waves = 0;
     while (count > 0 && waves < 4096) {
         for (int64_t r = begin; r < begin + count; ++r) {
-            uint64_t *hp = (ray_hash && r < hash_cap) ? &ray_hash[r] : NULL;
-            trace_ray(sc, p, lis, src, S, (uint64_t)r, H, st, hp);
+            const int64_t hi = r - p->first_ray;
+            uint64_t *hp = (ray_hash && hi >= 0 && hi < hash_cap) ? &ray_hash[hi] : NULL;
+            trace_ray(sc, p, lis, src, S, (uint64_t)r, H, st, hp, NULL);
         }
         begin += count;
         waves++;

@@ -1,0 +1,204 @@
+// accum.cu -- binning of contribution records into the low-rate SH energy
+// histogram H[s][b][k][t] (Section 4.2: I_b(t) with its spherical-harmonic
+// directivity X_{b,lm}(t); arrival direction = the path's first segment).
+//
+// Records (key = source * T + bin, primary ray id, e[B]) are grouped by key with a
+// counting sort (count, exclusive scan, scatter of record indices).  Then one warp
+// owns one (source, bin): its 32 lanes own the B*K cells, 32 records at a time are
+// staged in shared memory (energies, and SH of the primary direction recomputed
+// from Philox), and every cell is summed with Kahan compensation in FP32.  Each
+// cell is written by exactly one warp, so no atomics touch H.  Chunks of records
+// (when the record buffer is smaller than one step's records) are merged into a
+// running (sum, error) pair with an error-free two-sum.
+#include "internal.cuh"
+
+namespace rp {
+namespace {
+
+constexpr int ACC_THREADS = 256;
+constexpr int ACC_WARPS = ACC_THREADS / 32;
+constexpr int ACC_SLOTS = (MAXB * MAXK + 31) / 32;
+
+__global__ void k_count(TraceWork w)
+{
+    const unsigned long long n = min(w.ctr->n_records, w.rec.cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        atomicAdd(&w.cnt[w.rec.key[i]], 1u);
+}
+
+// exclusive scan of cnt[0..n) into off[0..n], off[n] = total; one block of 1024
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ cnt, uint32_t *__restrict__ off, int n)
+{
+    __shared__ uint32_t warp_sums[32];
+    const int t = threadIdx.x;
+    const int per = (n + 1023) / 1024;
+    const int b = t * per, e = min(n, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += cnt[i];
+    const int lane = t & 31, wid = t >> 5;
+    uint32_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t v = warp_sums[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += y;
+        }
+        warp_sums[lane] = v;
+    }
+    __syncthreads();
+    uint32_t run = x - s + (wid > 0 ? warp_sums[wid - 1] : 0u);
+    for (int i = b; i < e; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+    if (t == 1023) off[n] = run;
+}
+
+__global__ void k_scatter(TraceWork w)
+{
+    const unsigned long long n = min(w.ctr->n_records, w.rec.cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t key = w.rec.key[i];
+        const uint32_t pos = w.off[key] + atomicAdd(&w.cur[key], 1u);
+        w.perm[pos] = (uint32_t)i;
+    }
+}
+
+// Kahan step with the error kept as "true minus sum"
+__device__ __forceinline__ void kahan_add(float &sum, float &err, float x)
+{
+    const float y = __fadd_rn(x, err);
+    const float t = __fadd_rn(sum, y);
+    err = __fsub_rn(y, __fsub_rn(t, sum));
+    sum = t;
+}
+
+__global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first)
+{
+    __shared__ float se[ACC_WARPS][32][MAXB];
+    __shared__ float sy[ACC_WARPS][32][MAXK];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int S = w.k.S, B = w.k.B, K = w.k.K, T = w.k.T, BK = B * K;
+    const long long nkeys = (long long)S * T;
+    const long long nwarps = (long long)gridDim.x * ACC_WARPS;
+    for (long long key = (long long)blockIdx.x * ACC_WARPS + wp; key < nkeys; key += nwarps) {
+        const uint32_t begin = w.off[key], end = w.off[key + 1];
+        float sum[ACC_SLOTS], err[ACC_SLOTS];
+#pragma unroll
+        for (int i = 0; i < ACC_SLOTS; ++i) sum[i] = err[i] = 0.f;
+        for (uint32_t base = begin; base < end; base += 32) {
+            const int n = (int)min(32u, end - base);
+            if (lane < n) {
+                const uint32_t r = w.perm[base + lane];
+                const uint32_t rid = w.rec.rid[r];
+                const float *e = w.rec.e + (unsigned long long)r * B;
+#pragma unroll
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < B) se[wp][lane][b] = e[b];
+                const float3 d0 = primary_direction(rid, w.k.scene_id, w.k.key0, w.k.key1);
+                float Y[MAXK];
+                sh_eval(w.k.sh_order, d0.x, d0.y, d0.z, Y);
+#pragma unroll
+                for (int kk = 0; kk < MAXK; ++kk)
+                    if (kk < K) sy[wp][lane][kk] = Y[kk];
+            }
+            __syncwarp();
+            for (int j = 0; j < n; ++j) {
+#pragma unroll
+                for (int i = 0; i < ACC_SLOTS; ++i) {
+                    const int c = lane + 32 * i;
+                    if (c < BK) {
+                        const int b = c / K, kk = c - b * K;
+                        kahan_add(sum[i], err[i], se[wp][j][b] * sy[wp][j][kk]);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        const int s = (int)(key / T), bin = (int)(key - (long long)s * T);
+#pragma unroll
+        for (int i = 0; i < ACC_SLOTS; ++i) {
+            const int c = lane + 32 * i;
+            if (c < BK) {
+                const int b = c / K, kk = c - b * K;
+                const unsigned long long idx = (((unsigned long long)s * B + b) * K + kk) * T + bin;
+                if (first) {
+                    w.Hs[idx] = sum[i];
+                    w.He[idx] = err[i];
+                } else {
+                    // two-sum merge of the running pair with this chunk's pair
+                    const float a = w.Hs[idx], bsum = sum[i];
+                    const float s2 = __fadd_rn(a, bsum);
+                    const float bp = __fsub_rn(s2, a);
+                    const float e2 = __fadd_rn(__fsub_rn(a, __fsub_rn(s2, bp)), __fsub_rn(bsum, bp));
+                    w.Hs[idx] = s2;
+                    w.He[idx] = w.He[idx] + err[i] + e2;
+                }
+            }
+        }
+    }
+}
+
+// H = (sum + error) / K_primaries; late energy likewise; then direct sound binned
+// into H when min_order == 0
+__global__ void k_finalize(TraceWork w)
+{
+    const unsigned long long n = (unsigned long long)w.k.S * w.k.B * w.k.K * w.k.T;
+    const unsigned long long kp = w.stats->primaries;
+    const float inv = kp > 0 ? 1.0f / (float)kp : 0.f;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        w.H[i] = kp > 0 ? (w.Hs[i] + w.He[i]) / (float)kp : 0.f;
+    (void)inv;
+    if (blockIdx.x == 0 && threadIdx.x < w.k.B && kp > 0) w.stats->late[threadIdx.x] /= (double)kp;
+}
+
+__global__ void k_direct_add(TraceWork w)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int S = w.k.S, B = w.k.B, K = w.k.K, T = w.k.T;
+    if (i >= S * B * K) return;
+    const int s = i / (B * K), r = i - s * B * K, b = r / K, kk = r - b * K;
+    const rp_direct dd = w.direct[s];
+    if (!dd.visible || dd.bin < 0 || dd.bin >= T) return;
+    (void)b;
+    w.H[(unsigned long long)i * T + dd.bin] += dd.sh[kk];
+}
+
+}  // namespace
+
+void launch_count(const TraceWork &w, int blocks, cudaStream_t st) { k_count<<<blocks, 256, 0, st>>>(w); }
+
+void launch_scan(const TraceWork &w, cudaStream_t st)
+{
+    k_scan<<<1, 1024, 0, st>>>(w.cnt, w.off, w.k.S * w.k.T);
+}
+
+void launch_scatter(const TraceWork &w, int blocks, cudaStream_t st) { k_scatter<<<blocks, 256, 0, st>>>(w); }
+
+void launch_accum(const TraceWork &w, int first_chunk, int blocks, cudaStream_t st)
+{
+    k_accum<<<blocks, ACC_THREADS, 0, st>>>(w, first_chunk);
+}
+
+void launch_finalize(const TraceWork &w, cudaStream_t st)
+{
+    const unsigned long long n = (unsigned long long)w.k.S * w.k.B * w.k.K * w.k.T;
+    const unsigned long long nb = (n + 255) / 256;
+    const int blocks = (int)(nb < 4096ull ? nb : 4096ull);
+    k_finalize<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(w);
+    if (w.k.min_order == 0 && w.direct) {
+        const int m = w.k.S * w.k.B * w.k.K;
+        k_direct_add<<<(m + 255) / 256, 256, 0, st>>>(w);
+    }
+}
+
+}  // namespace rp

@@ -1,0 +1,676 @@
+// api.cu -- the C ABI (include/rpr.h): contexts, scenes, workspace, the trace step
+// orchestration, estimation, host-buffer updates and kernel timing.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace rp;
+
+namespace {
+
+// Records kept in device memory at once (one chunk of next-event work plus the
+// records of source-sphere hits).  40 bytes each at 8 bands.
+constexpr unsigned long long REC_BUDGET = 1ull << 28;
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct ProfPair {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct rp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int *d_status = nullptr;
+    int paths_blocks = 0, shadow_blocks = 0;
+    // workspace
+    Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, rec_key, rec_rid, rec_e, perm, cnt, off, cur, Hs, He, src, ctr,
+        stats, H, direct, params, state;
+    // profiling
+    bool prof = false;
+    std::vector<ProfPair> pending;
+    std::vector<cudaEvent_t> free_events;
+    std::map<std::string, std::pair<unsigned long long, double>> totals;
+};
+
+struct rp_scene {
+    rp_ctx *ctx = nullptr;
+    int num_tris = 0, num_nodes = 0, num_mats = 0, B = 0, max_depth = 0;
+    float tmin = 0.f, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, build_ms = 0.f;
+    float4 *nodes = nullptr, *tris = nullptr;
+    float *alpha = nullptr, *scat = nullptr, *wdiff = nullptr, *wspec = nullptr;
+    uint32_t *thr = nullptr;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return RP_OK;
+    if (e == cudaErrorMemoryAllocation) return RP_ERR_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInvalidDevice || e == cudaErrorNoKernelImageForDevice ||
+        e == cudaErrorInsufficientDriver)
+        return RP_ERR_NO_DEVICE;
+    return RP_ERR_CUDA;
+}
+
+#define CK(x)                                  \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+int ensure(rp_ctx *c, Buf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return RP_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    CK(cudaMalloc(&b.p, bytes));
+    b.bytes = bytes;
+    return RP_OK;
+}
+
+void free_buf(Buf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+cudaEvent_t get_event(rp_ctx *c)
+{
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    rp_ctx *c;
+    const char *name;
+    cudaEvent_t a = nullptr;
+    ProfScope(rp_ctx *c_, const char *n) : c(c_), name(n)
+    {
+        if (c->prof) {
+            a = get_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~ProfScope()
+    {
+        if (c->prof && a) {
+            cudaEvent_t b = get_event(c);
+            cudaEventRecord(b, c->stream);
+            c->pending.push_back({name, a, b});
+        }
+    }
+};
+
+void prof_collect(rp_ctx *c)
+{
+    if (c->pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto &p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto &t = c->totals[p.name];
+            t.first += 1;
+            t.second += ms;
+        }
+        c->free_events.push_back(p.a);
+        c->free_events.push_back(p.b);
+    }
+    c->pending.clear();
+}
+
+struct Sizes {
+    unsigned long long hit_cap, sph_cap, rec_cap, chunk_hits, n_chunks;
+    int S, B, K, T;
+};
+
+Sizes trace_sizes(const rp_scene *sc, const rp_trace_params *p, int S)
+{
+    Sizes z;
+    z.S = S;
+    z.B = sc->B;
+    z.K = (p->sh_order + 1) * (p->sh_order + 1);
+    z.T = p->num_bins;
+    const unsigned long long nm = p->num_rays * (unsigned long long)std::max(p->max_order, 0);
+    z.hit_cap = std::max(1ull, nm);
+    z.sph_cap = z.hit_cap / 2 + 4096;
+    const unsigned long long s = (unsigned long long)std::max(S, 1);
+    const unsigned long long room = REC_BUDGET > z.sph_cap ? REC_BUDGET - z.sph_cap : 1ull << 20;
+    z.chunk_hits = std::max(1ull, std::min(z.hit_cap, room / s));
+    z.n_chunks = (z.hit_cap + z.chunk_hits - 1) / z.chunk_hits;
+    z.rec_cap = z.sph_cap + z.chunk_hits * s;
+    return z;
+}
+
+int reserve(rp_ctx *c, const Sizes &z)
+{
+    int r;
+    const size_t keys = (size_t)z.S * z.T;
+    const size_t cells = (size_t)z.S * z.B * z.K * z.T;
+    if ((r = ensure(c, c->hit_p, z.hit_cap * sizeof(float4)))) return r;
+    if ((r = ensure(c, c->hit_plo, z.hit_cap * sizeof(float4)))) return r;
+    if ((r = ensure(c, c->hit_n, z.hit_cap * sizeof(float4)))) return r;
+    if ((r = ensure(c, c->hit_ws, z.hit_cap * z.B * sizeof(float)))) return r;
+    if ((r = ensure(c, c->hit_rid, z.hit_cap * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->rec_key, z.rec_cap * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->rec_rid, z.rec_cap * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->rec_e, z.rec_cap * z.B * sizeof(float)))) return r;
+    if ((r = ensure(c, c->perm, z.rec_cap * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->cnt, keys * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->cur, keys * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->off, (keys + 1) * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->Hs, cells * sizeof(float)))) return r;
+    if ((r = ensure(c, c->He, cells * sizeof(float)))) return r;
+    if ((r = ensure(c, c->src, (z.S + 1) * sizeof(float4)))) return r;
+    if ((r = ensure(c, c->ctr, sizeof(TraceCounters)))) return r;
+    if ((r = ensure(c, c->stats, sizeof(rp_trace_stats)))) return r;
+    return RP_OK;
+}
+
+int check_params(const rp_scene *sc, const rp_trace_params *p, int S)
+{
+    if (!sc || !p) return RP_ERR_INVALID_ARG;
+    if (S < 0 || S > RP_MAX_SOURCES) return RP_ERR_INVALID_ARG;
+    if (p->max_order < 0 || p->sh_order < 0 || p->sh_order > RP_MAX_SH_ORDER) return RP_ERR_INVALID_ARG;
+    if (p->num_bins < 1 || p->min_order < 0) return RP_ERR_INVALID_ARG;
+    if ((unsigned long long)S * (unsigned long long)p->num_bins >= (1ull << 31)) return RP_ERR_INVALID_ARG;
+    if (p->num_rays > 0xffffffffull || p->first_ray + p->num_rays > 0x100000000ull) return RP_ERR_INVALID_ARG;
+    if (p->num_rays * (unsigned long long)std::max(p->max_order, 1) >= (1ull << 40)) return RP_ERR_INVALID_ARG;
+    if (!(p->ir_rate_hz > 0.f) || !(p->speed_of_sound > 0.f) || !(p->source_radius > 0.f))
+        return RP_ERR_INVALID_ARG;
+    if (!std::isfinite(p->ir_rate_hz) || !std::isfinite(p->speed_of_sound) || !std::isfinite(p->source_radius))
+        return RP_ERR_NAN_INPUT;
+    return RP_OK;
+}
+
+__global__ void k_pack_positions(const float *lis, const float *src, int S, float4 *out, int *status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > S) return;
+    const float *p = i < S ? src + 3 * i : lis;
+    const float x = p[0], y = p[1], z = p[2];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) raise_error(status, RP_ERR_NAN_INPUT);
+    out[i] = make_float4(x, y, z, 0.f);
+}
+
+__global__ void k_copy_status(const int *status, const TraceCounters *ctr, rp_trace_stats *st)
+{
+    st->error = *status;
+    st->hits_stored = ctr->n_hits;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rp_status_string(int s)
+{
+    switch (s) {
+    case RP_OK: return "ok";
+    case RP_ERR_INVALID_ARG: return "invalid argument";
+    case RP_ERR_CUDA: return "CUDA error";
+    case RP_ERR_OOM: return "out of device memory";
+    case RP_ERR_CAPACITY: return "internal buffer capacity exceeded";
+    case RP_ERR_STACK_OVERFLOW: return "BVH traversal stack overflow";
+    case RP_ERR_TIMEOUT: return "traversal iteration cap reached";
+    case RP_ERR_NAN_INPUT: return "non-finite input";
+    case RP_ERR_EMPTY_SCENE: return "scene has no triangles";
+    case RP_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+    }
+}
+
+int rp_create(rp_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return RP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0 || device < 0 || device >= n) return RP_ERR_NO_DEVICE;
+    CK(cudaSetDevice(device));
+    rp_ctx *c = new (std::nothrow) rp_ctx();
+    if (!c) return RP_ERR_OOM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_status(e);
+    }
+    cudaMemset(c->d_status, 0, sizeof(int));
+    c->paths_blocks = c->num_sms * paths_occupancy(0);
+    c->shadow_blocks = c->num_sms * shadow_occupancy(0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return cuda_status(e);
+    }
+    *out = c;
+    return RP_OK;
+}
+
+int rp_destroy(rp_ctx *c)
+{
+    if (!c) return RP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (Buf *b : {&c->hit_p, &c->hit_plo, &c->hit_n, &c->hit_ws, &c->hit_rid, &c->rec_key, &c->rec_rid, &c->rec_e, &c->perm,
+                   &c->cnt, &c->off, &c->cur, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H, &c->direct,
+                   &c->params, &c->state})
+        free_buf(*b);
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->free_events) cudaEventDestroy(e);
+    cudaFree(c->d_status);
+    delete c;
+    return RP_OK;
+}
+
+int rp_set_stream(rp_ctx *c, void *cuda_stream)
+{
+    if (!c) return RP_ERR_INVALID_ARG;
+    c->stream = (cudaStream_t)cuda_stream;
+    return RP_OK;
+}
+
+int rp_sync_status(rp_ctx *c)
+{
+    if (!c) return RP_ERR_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    int h = 0;
+    CK(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) CK(cudaMemset(c->d_status, 0, sizeof(int)));
+    return h;
+}
+
+int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
+{
+    if (!c || !m || !out) return RP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (m->num_tris == 0) return RP_ERR_EMPTY_SCENE;
+    if (m->num_tris < 0 || m->num_verts <= 0 || m->num_materials <= 0 || m->num_bands < 1 ||
+        m->num_bands > RP_MAX_BANDS || !m->verts || !m->tris || !m->tri_material || !m->absorption ||
+        !m->scattering || (m->memory != RP_MEM_HOST && m->memory != RP_MEM_DEVICE))
+        return RP_ERR_INVALID_ARG;
+    if (!std::isfinite(m->ray_epsilon) || m->ray_epsilon < 0.f) return RP_ERR_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    const int nv = m->num_verts, nt = m->num_tris, nm = m->num_materials, B = m->num_bands;
+    const float *dv = m->verts, *da = m->absorption, *ds = m->scattering;
+    const int32_t *dt = m->tris, *dm = m->tri_material;
+    void *tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int rc = RP_OK;
+    rp_scene *sc = new (std::nothrow) rp_scene();
+    if (!sc) return RP_ERR_OOM;
+    sc->ctx = c;
+    sc->num_tris = nt;
+    sc->num_nodes = nt - 1;
+    sc->num_mats = nm;
+    sc->B = B;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BvhBuildArgs a;
+    BvhOut o;
+    cudaError_t err;
+    if (m->memory == RP_MEM_HOST) {
+        const size_t sz[5] = {sizeof(float) * 3 * nv, sizeof(int32_t) * 3 * nt, sizeof(int32_t) * nt,
+                              sizeof(float) * nm * B, sizeof(float) * nm * B};
+        const void *src[5] = {m->verts, m->tris, m->tri_material, m->absorption, m->scattering};
+        for (int i = 0; i < 5; ++i) {
+            if ((err = cudaMalloc(&tmp[i], sz[i])) != cudaSuccess) { rc = cuda_status(err); goto fail; }
+            if ((err = cudaMemcpyAsync(tmp[i], src[i], sz[i], cudaMemcpyHostToDevice, c->stream)) != cudaSuccess) {
+                rc = cuda_status(err);
+                goto fail;
+            }
+        }
+        dv = (const float *)tmp[0];
+        dt = (const int32_t *)tmp[1];
+        dm = (const int32_t *)tmp[2];
+        da = (const float *)tmp[3];
+        ds = (const float *)tmp[4];
+    }
+    if ((err = cudaMalloc(&sc->nodes, sizeof(float4) * 4 * (size_t)std::max(nt - 1, 1))) != cudaSuccess ||
+        (err = cudaMalloc(&sc->tris, sizeof(float4) * 3 * (size_t)nt)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->alpha, sizeof(float) * nm * B)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->scat, sizeof(float) * nm * B)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->wdiff, sizeof(float) * nm * B)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->wspec, sizeof(float) * nm * B)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->thr, sizeof(uint32_t) * nm)) != cudaSuccess) {
+        rc = cuda_status(err);
+        goto fail;
+    }
+    a = {dv, dt, dm, da, ds, nv, nt, nm, B, m->ray_epsilon};
+    o.nodes = sc->nodes;
+    o.tris = sc->tris;
+    o.alpha = sc->alpha;
+    o.scat = sc->scat;
+    o.wdiff = sc->wdiff;
+    o.wspec = sc->wspec;
+    o.thr = sc->thr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    cudaEventRecord(e0, c->stream);
+    err = build_bvh(a, o, c->d_status, c->stream);
+    cudaEventRecord(e1, c->stream);
+    if (err != cudaSuccess) {
+        rc = cuda_status(err);
+        goto fail;
+    }
+    if ((rc = rp_sync_status(c)) != RP_OK) goto fail;
+    cudaEventElapsedTime(&sc->build_ms, e0, e1);
+    sc->tmin = o.tmin;
+    sc->max_depth = o.max_depth;
+    for (int k = 0; k < 3; ++k) {
+        sc->lo[k] = o.lo[k];
+        sc->hi[k] = o.hi[k];
+    }
+    for (void *p : tmp) cudaFree(p);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *out = sc;
+    return RP_OK;
+fail:
+    cudaStreamSynchronize(c->stream);
+    for (void *p : tmp) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    rp_scene_destroy(sc);
+    return rc;
+}
+
+int rp_scene_destroy(rp_scene *sc)
+{
+    if (!sc) return RP_ERR_INVALID_ARG;
+    cudaSetDevice(sc->ctx->device);
+    cudaStreamSynchronize(sc->ctx->stream);
+    cudaFree(sc->nodes);
+    cudaFree(sc->tris);
+    cudaFree(sc->alpha);
+    cudaFree(sc->scat);
+    cudaFree(sc->wdiff);
+    cudaFree(sc->wspec);
+    cudaFree(sc->thr);
+    delete sc;
+    return RP_OK;
+}
+
+int rp_scene_info_get(const rp_scene *sc, rp_scene_info *out)
+{
+    if (!sc || !out) return RP_ERR_INVALID_ARG;
+    out->num_tris = sc->num_tris;
+    out->num_nodes = sc->num_nodes;
+    out->max_depth = sc->max_depth;
+    out->num_bands = sc->B;
+    for (int k = 0; k < 3; ++k) {
+        out->bounds_lo[k] = sc->lo[k];
+        out->bounds_hi[k] = sc->hi[k];
+    }
+    out->ray_epsilon = sc->tmin;
+    out->build_ms = sc->build_ms;
+    return RP_OK;
+}
+
+int rp_trace_reserve(rp_scene *sc, const rp_trace_params *p, int32_t S)
+{
+    int rc = check_params(sc, p, S);
+    if (rc) return rc;
+    CK(cudaSetDevice(sc->ctx->device));
+    return reserve(sc->ctx, trace_sizes(sc, p, S));
+}
+
+int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, const float *sources, int32_t S,
+             float *H, rp_direct *direct, rp_trace_stats *stats, uint64_t *ray_hash)
+{
+    int rc = check_params(sc, p, S);
+    if (rc) return rc;
+    if (!listener || (S > 0 && !sources) || (!H && S > 0)) return RP_ERR_INVALID_ARG;
+    rp_ctx *c = sc->ctx;
+    CK(cudaSetDevice(c->device));
+    const Sizes z = trace_sizes(sc, p, S);
+    if ((rc = reserve(c, z))) return rc;
+    cudaStream_t st = c->stream;
+
+    // positions: sources then the listener, packed as float4 on the device
+    float4 *dsrc = (float4 *)c->src.p;
+    if (p->flags & RP_FLAG_DEVICE_POSITIONS) {
+        ProfScope ps(c, "pack_positions");
+        k_pack_positions<<<(S + 1 + 127) / 128, 128, 0, st>>>(listener, sources, S, dsrc, c->d_status);
+    } else {
+        std::vector<float4> hp(S + 1);
+        for (int i = 0; i <= S; ++i) {
+            const float *q = i < S ? sources + 3 * i : listener;
+            if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2])) return RP_ERR_NAN_INPUT;
+            hp[i] = make_float4(q[0], q[1], q[2], 0.f);
+        }
+        // from pageable memory the copy is staged before the call returns
+        CK(cudaMemcpyAsync(dsrc, hp.data(), sizeof(float4) * (S + 1), cudaMemcpyHostToDevice, st));
+    }
+
+    TraceWork w;
+    w.sc = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris, sc->num_nodes,
+            sc->B, sc->tmin};
+    w.k.S = S;
+    w.k.B = sc->B;
+    w.k.K = z.K;
+    w.k.T = z.T;
+    w.k.M = p->max_order;
+    w.k.min_order = p->min_order;
+    w.k.sh_order = p->sh_order;
+    w.k.rate = p->ir_rate_hz;
+    w.k.c = p->speed_of_sound;
+    w.k.rs = p->source_radius;
+    w.k.scene_id = p->scene_id;
+    w.k.key0 = (uint32_t)p->seed;
+    w.k.key1 = (uint32_t)(p->seed >> 32);
+    w.k.num_rays = p->num_rays;
+    w.k.first_ray = p->first_ray;
+    w.k.flags = p->flags;
+    w.src = dsrc;
+    w.ctr = (TraceCounters *)c->ctr.p;
+    w.hits = {(float4 *)c->hit_p.p, (float4 *)c->hit_plo.p, (float4 *)c->hit_n.p, (float *)c->hit_ws.p, (uint32_t *)c->hit_rid.p,
+              z.hit_cap};
+    w.rec = {(uint32_t *)c->rec_key.p, (uint32_t *)c->rec_rid.p, (float *)c->rec_e.p, z.rec_cap};
+    w.stats = (rp_trace_stats *)c->stats.p;
+    w.ray_hash = (p->flags & RP_FLAG_RAY_HASH) ? ray_hash : nullptr;
+    w.status = c->d_status;
+    w.cnt = (uint32_t *)c->cnt.p;
+    w.off = (uint32_t *)c->off.p;
+    w.cur = (uint32_t *)c->cur.p;
+    w.perm = (uint32_t *)c->perm.p;
+    w.Hs = (float *)c->Hs.p;
+    w.He = (float *)c->He.p;
+    w.H = H;
+    w.direct = direct;
+    w.hits_per_chunk = z.chunk_hits;
+    w.num_sms = c->num_sms;
+
+    CK(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
+    CK(cudaMemsetAsync(w.stats, 0, sizeof(rp_trace_stats), st));
+    {
+        ProfScope ps(c, "wave_setup");
+        launch_wave_setup(w, 0, st);
+    }
+    if (p->max_order > 0) {
+        ProfScope ps(c, "paths");
+        launch_paths(w, c->paths_blocks, st);
+    }
+    if (p->budget_refill && p->max_order > 0) {
+        for (int wave = 1; wave < 4096; ++wave) {
+            {
+                ProfScope ps(c, "wave_setup");
+                launch_wave_setup(w, wave, st);
+            }
+            unsigned long long cnt = 0;
+            CK(cudaMemcpyAsync(&cnt, &w.ctr->wave_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (cnt == 0) break;
+            ProfScope ps(c, "paths");
+            launch_paths(w, c->paths_blocks, st);
+        }
+    }
+    {
+        ProfScope ps(c, "direct");
+        launch_direct(w, st);
+    }
+    const int grid_flat = c->num_sms * 8;
+    const long long nkeys = (long long)S * z.T;
+    const int acc_blocks = (int)std::max(1ll, std::min<long long>((nkeys + 7) / 8, (long long)c->num_sms * 8));
+    for (unsigned long long ch = 0; ch < z.n_chunks && S > 0; ++ch) {
+        if (ch > 0) CK(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(&w.ctr->next_item, 0, sizeof(unsigned long long), st));
+        if (p->max_order > 0) {
+            ProfScope ps(c, "shadow");
+            launch_shadow(w, ch, c->shadow_blocks, st);
+        }
+        CK(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nkeys, st));
+        CK(cudaMemsetAsync(w.cur, 0, sizeof(uint32_t) * nkeys, st));
+        {
+            ProfScope ps(c, "count");
+            launch_count(w, grid_flat, st);
+        }
+        {
+            ProfScope ps(c, "scan");
+            launch_scan(w, st);
+        }
+        {
+            ProfScope ps(c, "scatter");
+            launch_scatter(w, grid_flat, st);
+        }
+        {
+            ProfScope ps(c, "accum");
+            launch_accum(w, ch == 0 ? 1 : 0, acc_blocks, st);
+        }
+    }
+    if (S > 0) {
+        ProfScope ps(c, "finalize");
+        launch_finalize(w, st);
+    }
+    {
+        ProfScope ps(c, "copy_status");
+        k_copy_status<<<1, 1, 0, st>>>(c->d_status, w.ctr, w.stats);
+    }
+    CK(cudaGetLastError());
+    if (stats) CK(cudaMemcpyAsync(stats, w.stats, sizeof(rp_trace_stats), cudaMemcpyDeviceToDevice, st));
+    return RP_OK;
+}
+
+int rp_estimate(rp_ctx *c, const float *H, const rp_direct *direct, int32_t S, int32_t B, int32_t K, int32_t T,
+                const rp_estimate_params *ep, rp_reverb_params *out, double *state)
+{
+    if (!c || !ep || (S > 0 && (!H || !out))) return RP_ERR_INVALID_ARG;
+    if (S < 0 || B < 1 || B > RP_MAX_BANDS || K < 1 || K > RP_MAX_SH || T < 1) return RP_ERR_INVALID_ARG;
+    const int n = (int)std::lround(std::sqrt((double)K));
+    if (n * n != K) return RP_ERR_INVALID_ARG;
+    if (!(ep->ir_rate_hz > 0.0) || ep->tau < 0.0 || ep->dt_update < 0.0) return RP_ERR_INVALID_ARG;
+    CK(cudaSetDevice(c->device));
+    EstimateWork w{H, direct, S, B, K, T, ep->ir_rate_hz, ep->dt_update, ep->tau, out, state};
+    {
+        ProfScope ps(c, "estimate");
+        launch_estimate(w, c->stream);
+    }
+    CK(cudaGetLastError());
+    return RP_OK;
+}
+
+int rp_update(rp_scene *sc, const rp_trace_params *p, const rp_estimate_params *ep, const float *listener,
+              const float *sources, int32_t S, float *H_host, rp_reverb_params *params_host, rp_direct *direct_host,
+              rp_trace_stats *stats_host, double *state_host)
+{
+    int rc = check_params(sc, p, S);
+    if (rc) return rc;
+    if (!ep || (p->flags & RP_FLAG_DEVICE_POSITIONS)) return RP_ERR_INVALID_ARG;
+    rp_ctx *c = sc->ctx;
+    CK(cudaSetDevice(c->device));
+    const int K = (p->sh_order + 1) * (p->sh_order + 1);
+    const size_t cells = (size_t)S * sc->B * K * p->num_bins;
+    if ((rc = ensure(c, c->H, cells * sizeof(float)))) return rc;
+    if ((rc = ensure(c, c->direct, (size_t)std::max(S, 1) * sizeof(rp_direct)))) return rc;
+    if ((rc = ensure(c, c->params, (size_t)std::max(S, 1) * sc->B * sizeof(rp_reverb_params)))) return rc;
+    if ((rc = ensure(c, c->state, (size_t)std::max(S, 1) * sc->B * sizeof(double)))) return rc;
+    cudaStream_t st = c->stream;
+    double *dstate = nullptr;
+    if (state_host) {
+        dstate = (double *)c->state.p;
+        CK(cudaMemcpyAsync(dstate, state_host, sizeof(double) * S * sc->B, cudaMemcpyHostToDevice, st));
+    }
+    rp_trace_params q = *p;
+    q.flags &= ~RP_FLAG_RAY_HASH;
+    if ((rc = rp_trace(sc, &q, listener, sources, S, (float *)c->H.p, (rp_direct *)c->direct.p, nullptr, nullptr)))
+        return rc;
+    if ((rc = rp_estimate(c, (float *)c->H.p, (rp_direct *)c->direct.p, S, sc->B, K, p->num_bins, ep,
+                          (rp_reverb_params *)c->params.p, dstate)))
+        return rc;
+    if (H_host) CK(cudaMemcpyAsync(H_host, c->H.p, cells * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (params_host)
+        CK(cudaMemcpyAsync(params_host, c->params.p, sizeof(rp_reverb_params) * S * sc->B, cudaMemcpyDeviceToHost,
+                           st));
+    if (direct_host) CK(cudaMemcpyAsync(direct_host, c->direct.p, sizeof(rp_direct) * S, cudaMemcpyDeviceToHost, st));
+    if (stats_host)
+        CK(cudaMemcpyAsync(stats_host, c->stats.p, sizeof(rp_trace_stats), cudaMemcpyDeviceToHost, st));
+    if (state_host) CK(cudaMemcpyAsync(state_host, dstate, sizeof(double) * S * sc->B, cudaMemcpyDeviceToHost, st));
+    return rp_sync_status(c);
+}
+
+int rp_profile_enable(rp_ctx *c, int enable)
+{
+    if (!c) return RP_ERR_INVALID_ARG;
+    c->prof = enable != 0;
+    return RP_OK;
+}
+
+int rp_profile_reset(rp_ctx *c)
+{
+    if (!c) return RP_ERR_INVALID_ARG;
+    prof_collect(c);
+    c->totals.clear();
+    return RP_OK;
+}
+
+int rp_profile_read(rp_ctx *c, rp_kernel_time *out, int32_t max_entries, int32_t *count)
+{
+    if (!c || !count || (max_entries > 0 && !out)) return RP_ERR_INVALID_ARG;
+    prof_collect(c);
+    int i = 0;
+    for (auto &kv : c->totals) {
+        if (i < max_entries) {
+            std::memset(out[i].name, 0, sizeof(out[i].name));
+            std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = kv.second.first;
+            out[i].total_ms = kv.second.second;
+        }
+        ++i;
+    }
+    *count = i;
+    return RP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,589 @@
+// trace.cu -- backward path tracing from the listener with diffuse rain
+// (Section 5, "Sound Propagation"), direct sound, and the segment-budget waves.
+//
+// Kernels of one trace step:
+//   k_wave_setup  sets the ray range of the next wave of primaries; with budget
+//                 refill the unused part of the N*M segment budget buys
+//                 floor(unused / M) extra primaries (Section 5).
+//   k_paths       persistent: each warp takes 32 primaries at a time from a global
+//                 counter; each thread follows its path bounce by bounce: closest
+//                 hit, absorption, storage of the reflection for next-event
+//                 estimation, then a diffuse (cosine lobe, probability mean(s)) or
+//                 specular continuation drawn from Philox(ray, scene, bounce).
+//                 Path state in FP64 (default) or FP32 (RP_FLAG_FP32_PATHS).
+//                 After a specular choice the next segment also tests the sources
+//                 as spheres (the specular image of the source).
+//   k_shadow      persistent over (reflection, source) pairs: the diffuse-rain
+//                 shadow ray of each stored reflection to each source; a visible
+//                 source emits a contribution record w_b s_b cos / (pi d^2) at
+//                 arrival time (L + d) / c.
+//   k_direct      visibility and closed-form direct sound per source.
+#include "traverse.cuh"
+
+namespace rp {
+namespace {
+
+constexpr int PATH_THREADS = 128;
+constexpr int SHADOW_THREADS = 128;
+// an FP32 arrival time within this many bins of a bin boundary is re-decided in FP64
+constexpr float BIN_GUARD = 2e-3f;
+
+struct BlockAcc {
+    double esc[MAXB], absb[MAXB], rem[MAXB], late[MAXB];
+    double mfp, mfp_np;
+    unsigned long long mfp_cnt, mfp_cnt_np, segs, shadow, contrib, sphere, nodes, tris;
+};
+
+__device__ __forceinline__ void acc_init(BlockAcc &a)
+{
+    const int t = threadIdx.x;
+    if (t < MAXB) {
+        a.esc[t] = 0.0;
+        a.absb[t] = 0.0;
+        a.rem[t] = 0.0;
+        a.late[t] = 0.0;
+    }
+    if (t == 0) {
+        a.mfp = a.mfp_np = 0.0;
+        a.mfp_cnt = a.mfp_cnt_np = a.segs = a.shadow = a.contrib = a.sphere = a.nodes = a.tris = 0ull;
+    }
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void acc_flush(BlockAcc &a, rp_trace_stats *st, int B, int which)
+{
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < B) {
+        if (a.esc[t] != 0.0) atomicAdd(&st->escaped[t], a.esc[t]);
+        if (a.absb[t] != 0.0) atomicAdd(&st->absorbed[t], a.absb[t]);
+        if (a.rem[t] != 0.0) atomicAdd(&st->remaining[t], a.rem[t]);
+        if (a.late[t] != 0.0) atomicAdd(&st->late[t], a.late[t]);
+    }
+    if (t == 0) {
+        if (a.mfp != 0.0) atomicAdd(&st->mfp_sum, a.mfp);
+        if (a.mfp_np != 0.0) atomicAdd(&st->mfp_sum_np, a.mfp_np);
+        atomicAdd((unsigned long long *)&st->mfp_count, a.mfp_cnt);
+        atomicAdd((unsigned long long *)&st->mfp_count_np, a.mfp_cnt_np);
+        atomicAdd((unsigned long long *)&st->segments, a.segs);
+        atomicAdd((unsigned long long *)&st->shadow_rays, a.shadow);
+        atomicAdd((unsigned long long *)&st->contributions, a.contrib);
+        atomicAdd((unsigned long long *)&st->sphere_hits, a.sphere);
+        atomicAdd((unsigned long long *)&st->node_visits[which], a.nodes);
+        atomicAdd((unsigned long long *)&st->tri_tests[which], a.tris);
+    }
+}
+
+// warp-reduce per-thread counters into the block accumulator
+__device__ __forceinline__ void acc_counters(BlockAcc &a, double mfp, double mfp_np, unsigned long long mc,
+                                             unsigned long long mcnp, unsigned long long segs,
+                                             unsigned long long shadow, unsigned long long contrib,
+                                             unsigned long long sphere, const TravStats &ts)
+{
+    mfp = warp_sum_d(mfp);
+    mfp_np = warp_sum_d(mfp_np);
+    mc = warp_sum_u(mc);
+    mcnp = warp_sum_u(mcnp);
+    segs = warp_sum_u(segs);
+    shadow = warp_sum_u(shadow);
+    contrib = warp_sum_u(contrib);
+    sphere = warp_sum_u(sphere);
+    const unsigned long long nodes = warp_sum_u(ts.nodes), tris = warp_sum_u(ts.tris);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&a.mfp, mfp);
+        atomicAdd(&a.mfp_np, mfp_np);
+        atomicAdd(&a.mfp_cnt, mc);
+        atomicAdd(&a.mfp_cnt_np, mcnp);
+        atomicAdd(&a.segs, segs);
+        atomicAdd(&a.shadow, shadow);
+        atomicAdd(&a.contrib, contrib);
+        atomicAdd(&a.sphere, sphere);
+        atomicAdd(&a.nodes, nodes);
+        atomicAdd(&a.tris, tris);
+    }
+}
+
+__device__ __forceinline__ void emit_record(const TraceWork &w, uint32_t key, uint32_t rid, const float *e,
+                                            int B)
+{
+    const unsigned long long idx = warp_append(&w.ctr->n_records);
+    if (idx < w.rec.cap) {
+        w.rec.key[idx] = key;
+        w.rec.rid[idx] = rid;
+        float *dst = w.rec.e + idx * (unsigned long long)B;
+#pragma unroll
+        for (int b = 0; b < MAXB; ++b)
+            if (b < B) dst[b] = e[b];
+    } else {
+        raise_error(w.status, RP_ERR_CAPACITY);
+    }
+}
+
+__global__ void k_wave_setup(TraceWork w, int wave)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    TraceCounters *c = w.ctr;
+    unsigned long long count;
+    if (wave == 0) {
+        c->wave_begin = w.k.first_ray;
+        count = w.k.num_rays;
+    } else {
+        c->wave_begin += c->wave_count;
+        const unsigned long long budget = w.k.num_rays * (unsigned long long)w.k.M;
+        const unsigned long long used = w.stats->segments;
+        const unsigned long long unused = budget > used ? budget - used : 0ull;
+        count = (w.k.M > 0 && unused >= (unsigned long long)w.k.M) ? unused / (unsigned long long)w.k.M : 0ull;
+    }
+    c->wave_count = count;
+    c->next_ray = 0;
+    if (count > 0) {
+        w.stats->waves += 1;
+        w.stats->primaries += count;
+    }
+}
+
+// Path state in precision R.  The default carries the origin, direction and path
+// length of each path in FP64 while BVH traversal and the triangle choice stay in
+// FP32: the hit distance is re-computed in FP64 on the chosen triangle, so that a
+// path keeps FP64 accuracy over many reflections (in FP32 the position error grows
+// with every oblique reflection until late reflections pick different triangles).
+// With RP_FLAG_FP32_PATHS the whole path is FP32.
+template <typename R>
+struct V3 {
+    R x, y, z;
+    // hidden friends: found by argument-dependent lookup only, so they do not hide
+    // the float3 operators of the enclosing namespace
+    friend __device__ __forceinline__ V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+    friend __device__ __forceinline__ V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+    friend __device__ __forceinline__ V3 operator*(V3 a, R s) { return {a.x * s, a.y * s, a.z * s}; }
+};
+template <typename R>
+__device__ __forceinline__ V3<R> v3(R x, R y, R z)
+{
+    return {x, y, z};
+}
+template <typename R>
+__device__ __forceinline__ R dot3(V3<R> a, V3<R> b)
+{
+    return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename R>
+__device__ __forceinline__ V3<R> cross3(V3<R> a, V3<R> b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ V3<R> from4(float4 v)
+{
+    return {(R)v.x, (R)v.y, (R)v.z};
+}
+template <typename R>
+__device__ __forceinline__ float3 to_f3(V3<R> v)
+{
+    return mk3((float)v.x, (float)v.y, (float)v.z);
+}
+__device__ __forceinline__ void sincospi_r(float x, float *s, float *c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_r(double x, double *s, double *c) { sincospi(x, s, c); }
+template <typename R>
+__device__ __forceinline__ R u01r(uint32_t x)
+{
+    return (R)(x >> 8) * (R)(1.0 / 16777216.0);
+}
+
+template <typename R>
+__device__ __forceinline__ V3<R> primary_dir_r(uint32_t rid, uint32_t scene_id, uint32_t k0, uint32_t k1)
+{
+    const U4 r = philox4x32_10(rid, scene_id, 0u, 0u, k0, k1);
+    const R z = (R)1 - (R)2 * u01r<R>(r.x);
+    const R rad = sqrt(max((R)0, (R)1 - z * z));
+    R s, c;
+    sincospi_r((R)2 * u01r<R>(r.y), &s, &c);
+    return v3<R>(rad * c, rad * s, z);
+}
+
+template <typename R, bool HASH, bool COUNT>
+__global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
+{
+    __shared__ int sstack[SMEM_STACK * PATH_THREADS];
+    __shared__ BlockAcc acc;
+    acc_init(acc);
+    __syncthreads();
+
+    const SceneView &sc = w.sc;
+    const TraceConsts &k = w.k;
+    const int B = k.B, S = k.S, T = k.T, M = k.M;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long wave_begin = w.ctr->wave_begin, wave_count = w.ctr->wave_count;
+    const float inv_pi_rs2 = 1.0f / (PI_F * k.rs * k.rs);
+    const V3<R> lis = from4<R>(__ldg(w.src + S));  // the listener follows the S sources
+
+    double mfp = 0.0, mfp_np = 0.0;
+    unsigned long long mc = 0, mcnp = 0, segs = 0, sphere = 0, contrib = 0;
+    TravStats ts = {0u, 0u};
+
+    // path state
+    bool have = false, done = wave_count == 0;
+    uint32_t rid = 0;
+    V3<R> o = v3<R>(0, 0, 0), d = o;
+    R L = 0;
+    float wgt[MAXB], absorbed[MAXB];
+    int prev = -1, h = 1;
+    bool spec_prev = false;
+    uint64_t hash = FNV_OFFSET;
+
+    while (true) {
+        const unsigned need = __ballot_sync(FULL, !have && !done);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&w.ctr->next_ray, (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (!have && !done) {
+                const unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
+                if (my < wave_count) {
+                    rid = (uint32_t)(wave_begin + my);
+                    have = true;
+                    o = lis;
+                    d = primary_dir_r<R>(rid, k.scene_id, k.key0, k.key1);
+                    L = 0;
+#pragma unroll
+                    for (int b = 0; b < MAXB; ++b) {
+                        wgt[b] = 1.0f;
+                        absorbed[b] = 0.0f;
+                    }
+                    prev = -1;
+                    h = 1;
+                    spec_prev = false;
+                    hash = FNV_OFFSET;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, have)) break;
+        if (!have) continue;
+
+        // ---- one segment: closest hit (FP32 traversal) ----
+        const float3 of = to_f3(o), df = to_f3(d);
+        const float Lf = (float)L;
+        float tf;
+        const int tri = traverse<false, COUNT>(sc, of, df, sc.tmin, INFINITY, prev, sstack + threadIdx.x, tf, ts,
+                                               w.status);
+        ++segs;
+        if (spec_prev && h - 1 >= k.min_order) {
+            // the source as a sphere of radius r_s, seen through the specular bounce
+            for (int s = 0; s < S; ++s) {
+                const float4 cs = __ldg(w.src + s);
+                const float3 oc = of - xyz(cs);
+                const float bq = dot(oc, df);
+                const float cq = dot(oc, oc) - k.rs * k.rs;
+                const float disc = bq * bq - cq;
+                if (disc < 0.f) continue;
+                const float tsph = -bq - sqrtf(disc);
+                if (!(tsph > sc.tmin) || (tri >= 0 && !(tsph < tf))) continue;
+                ++sphere;
+                ++contrib;
+                float e[MAXB];
+#pragma unroll
+                for (int b = 0; b < MAXB; ++b) e[b] = wgt[b] * inv_pi_rs2;
+                float binf;
+                const float x = ((Lf + tsph) / k.c) * k.rate;
+                if (fabsf(x - rintf(x)) < BIN_GUARD) {
+                    // close to a bin boundary: decide with the path-precision state
+                    const V3<R> oc2 = o - from4<R>(cs);
+                    const R b2 = dot3(oc2, d);
+                    const R c2 = dot3(oc2, oc2) - (R)k.rs * (R)k.rs;
+                    const R t2 = -b2 - sqrt(max((R)0, b2 * b2 - c2));
+                    binf = (float)floor(((L + t2) / (R)k.c) * (R)k.rate);
+                } else {
+                    binf = floorf(x);
+                }
+                if (binf < (float)T) {
+                    emit_record(w, (uint32_t)s * (uint32_t)T + (uint32_t)binf, rid, e, B);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < MAXB; ++b)
+                        if (b < B) atomicAdd(&acc.late[b], (double)e[b]);
+                }
+            }
+        }
+        if (HASH) {
+            const uint32_t v = tri < 0 ? 0xffffffffu : __float_as_uint(__ldg(sc.tris + 3 * tri + 1).w);
+            hash = fnv_u32(hash, v);
+        }
+        bool end_ray = false;
+        if (tri < 0) {
+#pragma unroll
+            for (int b = 0; b < MAXB; ++b)
+                if (b < B) atomicAdd(&acc.esc[b], (double)wgt[b]);
+            end_ray = true;
+        } else {
+            const float4 ta = __ldg(sc.tris + 3 * tri), tb = __ldg(sc.tris + 3 * tri + 1),
+                         tc = __ldg(sc.tris + 3 * tri + 2);
+            const V3<R> v0 = from4<R>(ta), e1 = from4<R>(tb) - v0, e2 = from4<R>(tc) - v0;
+            // hit distance on the chosen triangle in the path precision
+            R t = (R)tf;
+            if (sizeof(R) == 8) {
+                const V3<R> pv = cross3(d, e2);
+                const R det = dot3(e1, pv);
+                if (det != (R)0) t = dot3(e2, cross3(o - v0, e1)) / det;
+            }
+            L += t;
+            const V3<R> p = o + d * t;
+            mfp += (double)t;
+            ++mc;
+            if (h > 1) {
+                mfp_np += (double)t;
+                ++mcnp;
+            }
+            V3<R> n = cross3(e1, e2);
+            n = n * ((R)1 / sqrt(dot3(n, n)));
+            if (dot3(n, d) > (R)0) n = n * (R)-1;
+            const int mat = __float_as_int(ta.w);
+            const float *al = sc.alpha + mat * B;
+#pragma unroll
+            for (int b = 0; b < MAXB; ++b) {
+                if (b < B) {
+                    const float a = __ldg(al + b);
+                    absorbed[b] += wgt[b] * a;
+                    wgt[b] *= (1.0f - a);
+                }
+            }
+            if (h >= k.min_order && S > 0) {
+                const unsigned long long j = warp_append(&w.ctr->n_hits);
+                if (j < w.hits.cap) {
+                    const float4 phi = make_float4((float)p.x, (float)p.y, (float)p.z, (float)L);
+                    w.hits.p[j] = phi;
+                    w.hits.plo[j] = make_float4((float)(p.x - (R)phi.x), (float)(p.y - (R)phi.y),
+                                                (float)(p.z - (R)phi.z), (float)(L - (R)phi.w));
+                    w.hits.n[j] = make_float4((float)n.x, (float)n.y, (float)n.z, __int_as_float(tri));
+                    const float *sb = sc.scat + mat * B;
+#pragma unroll
+                    for (int b = 0; b < MAXB; ++b)
+                        if (b < B) w.hits.ws[(unsigned long long)b * w.hits.cap + j] = wgt[b] * __ldg(sb + b);
+                    w.hits.rid[j] = rid;
+                } else {
+                    raise_error(w.status, RP_ERR_CAPACITY);
+                }
+            }
+            if (h == M) {
+#pragma unroll
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < B) atomicAdd(&acc.rem[b], (double)wgt[b]);
+                end_ray = true;
+            } else {
+                const U4 r = philox4x32_10(rid, k.scene_id, (uint32_t)h, 0u, k.key0, k.key1);
+                if ((r.z >> 8) < __ldg(sc.thr + mat)) {
+                    // cosine-weighted hemisphere about n (Malley), frame of Duff et al. 2017
+                    const R u0 = u01r<R>(r.x), u1 = u01r<R>(r.y);
+                    const R rr = sqrt(u1);
+                    R sn, cn;
+                    sincospi_r((R)2 * u0, &sn, &cn);
+                    const R lx = rr * cn, ly = rr * sn, lz = sqrt(max((R)0, (R)1 - u1));
+                    const R sg = n.z >= (R)0 ? (R)1 : (R)-1;
+                    const R aa = (R)-1 / (sg + n.z);
+                    const R bb = n.x * n.y * aa;
+                    const V3<R> b1 = v3<R>((R)1 + sg * n.x * n.x * aa, sg * bb, -sg * n.x);
+                    const V3<R> b2 = v3<R>(bb, sg + n.y * n.y * aa, -n.y);
+                    d = b1 * lx + b2 * ly + n * lz;
+                    const float *wd = sc.wdiff + mat * B;
+#pragma unroll
+                    for (int b = 0; b < MAXB; ++b)
+                        if (b < B) wgt[b] *= __ldg(wd + b);
+                    spec_prev = false;
+                } else {
+                    d = d - n * ((R)2 * dot3(d, n));
+                    d = d * ((R)1 / sqrt(dot3(d, d)));
+                    const float *wsp = sc.wspec + mat * B;
+#pragma unroll
+                    for (int b = 0; b < MAXB; ++b)
+                        if (b < B) wgt[b] *= __ldg(wsp + b);
+                    spec_prev = true;
+                }
+                o = p;
+                prev = tri;
+                ++h;
+            }
+        }
+        if (end_ray) {
+#pragma unroll
+            for (int b = 0; b < MAXB; ++b)
+                if (b < B) atomicAdd(&acc.absb[b], (double)absorbed[b]);
+            if (HASH && w.ray_hash && rid >= k.first_ray && rid - k.first_ray < k.num_rays)
+                w.ray_hash[rid - k.first_ray] = hash;
+            have = false;
+        }
+    }
+    acc_counters(acc, mfp, mfp_np, mc, mcnp, segs, 0ull, contrib, sphere, ts);
+    acc_flush(acc, w.stats, B, 0);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned long long chunk)
+{
+    __shared__ int sstack[SMEM_STACK * SHADOW_THREADS];
+    __shared__ BlockAcc acc;
+    acc_init(acc);
+    __syncthreads();
+
+    const SceneView &sc = w.sc;
+    const TraceConsts &k = w.k;
+    const int B = k.B, S = k.S, T = k.T;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nh = min(w.ctr->n_hits, w.hits.cap);
+    const unsigned long long j0 = chunk * w.hits_per_chunk;
+    const unsigned long long j1 = min(j0 + w.hits_per_chunk, nh);
+    const unsigned long long items = j1 > j0 ? (j1 - j0) * (unsigned long long)S : 0ull;
+    const float inv_pi = 1.0f / PI_F;
+
+    unsigned long long shadow = 0, contrib = 0;
+    TravStats ts = {0u, 0u};
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&w.ctr->next_item, 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= items) break;
+        const unsigned long long q = base + lane;
+        if (q < items) {
+            const unsigned long long jj = q / (unsigned long long)S;
+            const int s = (int)(q - jj * (unsigned long long)S);
+            const unsigned long long j = j0 + jj;
+            const float4 P = w.hits.p[j], N = w.hits.n[j];
+            const float3 p = xyz(P), n = xyz(N);
+            const float4 cs = __ldg(w.src + s);
+            const float3 v = xyz(cs) - p;
+            const float dist2 = dot(v, v);
+            const float dist = sqrtf(dist2);
+            const float cth = dot(n, v) / dist;
+            if (cth > 0.f) {
+                ++shadow;
+                const float3 dir = v * (1.0f / dist);
+                float tt;
+                const int blk = traverse<true, COUNT>(sc, p, dir, sc.tmin, dist, __float_as_int(N.w),
+                                                      sstack + threadIdx.x, tt, ts, w.status);
+                if (blk < 0) {
+                    ++contrib;
+                    const float f = cth * inv_pi / dist2;
+                    float e[MAXB];
+#pragma unroll
+                    for (int b = 0; b < MAXB; ++b)
+                        e[b] = b < B ? w.hits.ws[(unsigned long long)b * w.hits.cap + j] * f : 0.f;
+                    float binf;
+                    const float x = ((P.w + dist) / k.c) * k.rate;
+                    if (fabsf(x - rintf(x)) < BIN_GUARD) {
+                        // close to a bin boundary: decide in FP64 from the stored residuals
+                        const float4 lo = w.hits.plo[j];
+                        const double dx = (double)cs.x - ((double)P.x + (double)lo.x);
+                        const double dy = (double)cs.y - ((double)P.y + (double)lo.y);
+                        const double dz = (double)cs.z - ((double)P.z + (double)lo.z);
+                        const double dd = sqrt(dx * dx + dy * dy + dz * dz);
+                        const double tt = ((double)P.w + (double)lo.w + dd) / (double)k.c;
+                        binf = (float)floor(tt * (double)k.rate);
+                    } else {
+                        binf = floorf(x);
+                    }
+                    if (binf < (float)T) {
+                        emit_record(w, (uint32_t)s * (uint32_t)T + (uint32_t)binf, w.hits.rid[j], e, B);
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < MAXB; ++b)
+                            if (b < B) atomicAdd(&acc.late[b], (double)e[b]);
+                    }
+                }
+            }
+        }
+    }
+    acc_counters(acc, 0.0, 0.0, 0ull, 0ull, 0ull, shadow, contrib, 0ull, ts);
+    acc_flush(acc, w.stats, B, 1);
+}
+
+__global__ void __launch_bounds__(128) k_direct(TraceWork w)
+{
+    __shared__ int sstack[SMEM_STACK * 128];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= w.k.S) return;
+    const float4 l4 = __ldg(w.src + w.k.S), s4 = __ldg(w.src + s);
+    // distance, time and bin in FP64; the visibility ray in FP32
+    const double vx = (double)s4.x - l4.x, vy = (double)s4.y - l4.y, vz = (double)s4.z - l4.z;
+    const double dist = sqrt(vx * vx + vy * vy + vz * vz);
+    const float3 dir = mk3((float)(vx / dist), (float)(vy / dist), (float)(vz / dist));
+    TravStats ts = {0u, 0u};
+    float tt;
+    const int blk = traverse<true, false>(w.sc, xyz(l4), dir, w.sc.tmin, (float)dist, -1, sstack + threadIdx.x, tt,
+                                          ts, w.status);
+    rp_direct out;
+    out.visible = blk < 0 ? 1 : 0;
+    out.dist = (float)dist;
+    const double time = dist / (double)w.k.c;
+    out.time = (float)time;
+    out.energy = blk < 0 ? (float)(1.0 / (4.0 * 3.14159265358979323846 * dist * dist)) : 0.0f;
+    const double binf = floor(time * (double)w.k.rate);
+    out.bin = binf < 2147483520.0 ? (int)binf : 0x7fffffff;
+    float Y[MAXK];
+    sh_eval(w.k.sh_order, dir.x, dir.y, dir.z, Y);
+    for (int kk = 0; kk < MAXK; ++kk) out.sh[kk] = kk < w.k.K ? out.energy * Y[kk] : 0.f;
+    w.direct[s] = out;
+}
+
+}  // namespace
+
+void launch_wave_setup(const TraceWork &w, int wave, cudaStream_t st) { k_wave_setup<<<1, 32, 0, st>>>(w, wave); }
+
+template <typename R>
+void launch_paths_r(const TraceWork &w, int blocks, cudaStream_t st)
+{
+    const bool hash = (w.k.flags & RP_FLAG_RAY_HASH) && w.ray_hash;
+    const bool count = (w.k.flags & RP_FLAG_COUNT_VISITS) != 0;
+    if (hash && count) k_paths<R, true, true><<<blocks, PATH_THREADS, 0, st>>>(w);
+    else if (hash) k_paths<R, true, false><<<blocks, PATH_THREADS, 0, st>>>(w);
+    else if (count) k_paths<R, false, true><<<blocks, PATH_THREADS, 0, st>>>(w);
+    else k_paths<R, false, false><<<blocks, PATH_THREADS, 0, st>>>(w);
+}
+
+void launch_paths(const TraceWork &w, int blocks, cudaStream_t st)
+{
+    if (w.k.flags & RP_FLAG_FP32_PATHS) launch_paths_r<float>(w, blocks, st);
+    else launch_paths_r<double>(w, blocks, st);
+}
+
+void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
+{
+    if (w.k.flags & RP_FLAG_COUNT_VISITS) k_shadow<true><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    else k_shadow<false><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+}
+
+void launch_direct(const TraceWork &w, cudaStream_t st)
+{
+    if (w.k.S > 0 && w.direct) k_direct<<<(w.k.S + 127) / 128, 128, 0, st>>>(w);
+}
+
+int paths_occupancy(int flags)
+{
+    int n = 0;
+    if (flags & RP_FLAG_FP32_PATHS)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_paths<float, false, false>, PATH_THREADS, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_paths<double, false, false>, PATH_THREADS, 0);
+    return n > 0 ? n : 1;
+}
+
+int shadow_occupancy(int flags)
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false>, SHADOW_THREADS, 0);
+    (void)flags;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace rp

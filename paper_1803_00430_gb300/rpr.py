@@ -1,0 +1,427 @@
+"""ctypes binding of the C ABI declared in include/rpr.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA library
+(``_build/librpr.so``, built by ``paper_1803_00430_gb300.build``).  Loading fails
+loudly when the library is missing; there is no CPU fallback.
+
+The raw entry points keep their C names (``rp_create``, ``rp_trace`` ...).  The
+small classes below pass torch CUDA tensors (device memory) or numpy arrays (host
+memory) through them.
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes as C
+import os
+import weakref
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MAX_BANDS = 8
+MAX_SH_ORDER = 3
+MAX_SH = 16
+MAX_SOURCES = 4096
+
+RP_OK = 0
+STATUS = {
+    0: "RP_OK", -1: "RP_ERR_INVALID_ARG", -2: "RP_ERR_CUDA", -3: "RP_ERR_OOM", -4: "RP_ERR_CAPACITY",
+    -5: "RP_ERR_STACK_OVERFLOW", -6: "RP_ERR_TIMEOUT", -7: "RP_ERR_NAN_INPUT", -8: "RP_ERR_EMPTY_SCENE",
+    -9: "RP_ERR_NO_DEVICE",
+}
+RP_ERR = {v: k for k, v in STATUS.items()}
+RP_MEM_HOST, RP_MEM_DEVICE = 0, 1
+RP_FLAG_RAY_HASH, RP_FLAG_COUNT_VISITS, RP_FLAG_DEVICE_POSITIONS, RP_FLAG_FP32_PATHS = 1, 2, 4, 8
+
+
+class rp_mesh_desc(C.Structure):
+    _fields_ = [("verts", C.c_void_p), ("tris", C.c_void_p), ("tri_material", C.c_void_p),
+                ("absorption", C.c_void_p), ("scattering", C.c_void_p), ("num_verts", C.c_int32),
+                ("num_tris", C.c_int32), ("num_materials", C.c_int32), ("num_bands", C.c_int32),
+                ("memory", C.c_int32), ("ray_epsilon", C.c_float)]
+
+
+class rp_scene_info(C.Structure):
+    _fields_ = [("num_tris", C.c_int32), ("num_nodes", C.c_int32), ("max_depth", C.c_int32),
+                ("num_bands", C.c_int32), ("bounds_lo", C.c_float * 3), ("bounds_hi", C.c_float * 3),
+                ("ray_epsilon", C.c_float), ("build_ms", C.c_float)]
+
+
+class rp_trace_params(C.Structure):
+    _fields_ = [("num_rays", C.c_uint64), ("seed", C.c_uint64), ("first_ray", C.c_uint64), ("max_order", C.c_int32),
+                ("sh_order", C.c_int32), ("num_bins", C.c_int32), ("min_order", C.c_int32),
+                ("ir_rate_hz", C.c_float), ("speed_of_sound", C.c_float), ("source_radius", C.c_float),
+                ("scene_id", C.c_uint32), ("budget_refill", C.c_int32), ("flags", C.c_int32)]
+
+
+class rp_direct(C.Structure):
+    _fields_ = [("visible", C.c_int32), ("bin", C.c_int32), ("dist", C.c_float), ("time", C.c_float),
+                ("energy", C.c_float), ("sh", C.c_float * MAX_SH)]
+
+
+class rp_trace_stats(C.Structure):
+    _fields_ = [("escaped", C.c_double * MAX_BANDS), ("absorbed", C.c_double * MAX_BANDS),
+                ("remaining", C.c_double * MAX_BANDS), ("late", C.c_double * MAX_BANDS),
+                ("mfp_sum", C.c_double), ("mfp_sum_np", C.c_double), ("mfp_count", C.c_uint64),
+                ("mfp_count_np", C.c_uint64), ("segments", C.c_uint64), ("shadow_rays", C.c_uint64),
+                ("primaries", C.c_uint64), ("contributions", C.c_uint64), ("sphere_hits", C.c_uint64),
+                ("waves", C.c_uint64), ("node_visits", C.c_uint64 * 2), ("tri_tests", C.c_uint64 * 2),
+                ("hits_stored", C.c_uint64), ("error", C.c_int32), ("reserved", C.c_int32)]
+
+
+class rp_estimate_params(C.Structure):
+    _fields_ = [("ir_rate_hz", C.c_double), ("dt_update", C.c_double), ("tau", C.c_double)]
+
+
+class rp_reverb_params(C.Structure):
+    _fields_ = [("rt60_raw", C.c_double), ("rt60_smoothed", C.c_double), ("fit_hi_db", C.c_double),
+                ("fit_lo_db", C.c_double), ("fit_r2", C.c_double), ("slope_db_per_s", C.c_double),
+                ("intercept_db", C.c_double), ("i_total", C.c_double), ("g_reverb", C.c_double),
+                ("e_direct", C.c_double), ("drr_db", C.c_double), ("predelay_s", C.c_double),
+                ("range_kind", C.c_int32), ("n_fit", C.c_int32), ("fit_j0", C.c_int32),
+                ("fit_j1", C.c_int32), ("xbar", C.c_double * MAX_SH)]
+
+
+class rp_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
+# (name, argtypes) of every exported entry point, in header order
+_SIGS = {
+    "rp_status_string": ([C.c_int], C.c_char_p),
+    "rp_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p], C.c_int),
+    "rp_destroy": ([C.c_void_p], C.c_int),
+    "rp_set_stream": ([C.c_void_p, C.c_void_p], C.c_int),
+    "rp_scene_create": ([C.c_void_p, C.POINTER(rp_mesh_desc), C.POINTER(C.c_void_p)], C.c_int),
+    "rp_scene_destroy": ([C.c_void_p], C.c_int),
+    "rp_scene_info_get": ([C.c_void_p, C.POINTER(rp_scene_info)], C.c_int),
+    "rp_trace_reserve": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_int32], C.c_int),
+    "rp_trace": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                  C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "rp_estimate": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                     C.POINTER(rp_estimate_params), C.c_void_p, C.c_void_p], C.c_int),
+    "rp_update": ([C.c_void_p, C.POINTER(rp_trace_params), C.POINTER(rp_estimate_params), C.c_void_p,
+                   C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+                  C.c_int),
+    "rp_sync_status": ([C.c_void_p], C.c_int),
+    "rp_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
+    "rp_profile_reset": ([C.c_void_p], C.c_int),
+    "rp_profile_read": ([C.c_void_p, C.POINTER(rp_kernel_time), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+}
+
+_lib = None
+_live = weakref.WeakSet()   # contexts and scenes still holding library objects
+_closed = False
+
+
+def _close_all():
+    """Release library objects while the CUDA runtime is still alive (interpreter
+    exit runs Python's atexit handlers before the C runtime's)."""
+    global _closed
+    for obj in sorted(list(_live), key=lambda o: 0 if isinstance(o, Scene) else 1):
+        try:
+            obj.close()
+        except Exception:
+            pass
+    _closed = True
+
+
+atexit.register(_close_all)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load librpr.so (optionally building it).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB} is missing "
+                           "(run python -m paper_1803_00430_gb300.build)")
+    lib = C.CDLL(_build.LIB)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+class RprError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({load().rp_status_string(status).decode()})")
+
+
+def check(status: int, what: str = "rp call"):
+    if status != RP_OK:
+        raise RprError(status, what)
+    return status
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (or None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+@dataclass
+class TraceParams:
+    num_rays: int = 10000
+    max_order: int = 20
+    sh_order: int = 1
+    num_bins: int = 1000
+    min_order: int = 1
+    ir_rate_hz: float = 1000.0
+    speed_of_sound: float = 343.0
+    source_radius: float = 0.5
+    seed: int = 0xC0FFEE
+    scene_id: int = 0
+    budget_refill: int = 0
+    flags: int = 0
+    first_ray: int = 0
+
+    def c(self) -> rp_trace_params:
+        return rp_trace_params(int(self.num_rays), int(self.seed) & 0xFFFFFFFFFFFFFFFF, int(self.first_ray),
+                               int(self.max_order),
+                               int(self.sh_order), int(self.num_bins), int(self.min_order),
+                               float(self.ir_rate_hz), float(self.speed_of_sound), float(self.source_radius),
+                               int(self.scene_id) & 0xFFFFFFFF, int(self.budget_refill), int(self.flags))
+
+    @property
+    def K(self) -> int:
+        return (self.sh_order + 1) ** 2
+
+
+class Context:
+    """rp_ctx on one device and stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        h = C.c_void_p()
+        check(self.lib.rp_create(C.byref(h), int(device), _stream_handle(stream)), "rp_create")
+        self.h = h
+        self.device = device
+        self.scenes = weakref.WeakSet()
+        _live.add(self)
+
+    def set_stream(self, stream):
+        check(self.lib.rp_set_stream(self.h, _stream_handle(stream)), "rp_set_stream")
+
+    def sync_status(self) -> int:
+        return self.lib.rp_sync_status(self.h)
+
+    def profile(self, enable: bool = True):
+        check(self.lib.rp_profile_enable(self.h, int(enable)), "rp_profile_enable")
+
+    def profile_reset(self):
+        check(self.lib.rp_profile_reset(self.h), "rp_profile_reset")
+
+    def profile_read(self) -> dict:
+        n = C.c_int32()
+        buf = (rp_kernel_time * 64)()
+        check(self.lib.rp_profile_read(self.h, buf, 64, C.byref(n)), "rp_profile_read")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+                for i in range(min(n.value, 64))}
+
+    def close(self):
+        if getattr(self, "h", None) and not _closed:
+            for sc in list(self.scenes):
+                sc.close()
+            self.lib.rp_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """rp_scene: the mesh and its device BVH.  Arrays may be numpy (host) or torch
+    CUDA tensors (device)."""
+
+    def __init__(self, ctx: Context, verts, tris, tri_material, absorption, scattering,
+                 ray_epsilon: float = 0.0):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        on_dev = hasattr(verts, "is_cuda") and verts.is_cuda
+        if on_dev:
+            import torch
+            arrs = [verts.float().contiguous(), tris.int().contiguous(), tri_material.int().contiguous(),
+                    absorption.float().contiguous(), scattering.float().contiguous()]
+            assert all(isinstance(a, torch.Tensor) and a.is_cuda for a in arrs)
+        else:
+            arrs = [np.ascontiguousarray(verts, np.float32), np.ascontiguousarray(tris, np.int32),
+                    np.ascontiguousarray(tri_material, np.int32), np.ascontiguousarray(absorption, np.float32),
+                    np.ascontiguousarray(scattering, np.float32)]
+        self._keep = arrs
+        v, t, m, a, s = arrs
+        B = int(a.shape[1]) if len(a.shape) == 2 else 1
+        d = rp_mesh_desc(_ptr(v), _ptr(t), _ptr(m), _ptr(a), _ptr(s), int(v.shape[0]), int(t.shape[0]),
+                         int(a.shape[0]), B, RP_MEM_DEVICE if on_dev else RP_MEM_HOST, float(ray_epsilon))
+        self.B = B
+        h = C.c_void_p()
+        check(self.lib.rp_scene_create(ctx.h, C.byref(d), C.byref(h)), "rp_scene_create")
+        self.h = h
+        self._keep = None
+        ctx.scenes.add(self)
+        _live.add(self)
+
+    @classmethod
+    def from_scene(cls, ctx: Context, sc, **kw):
+        return cls(ctx, sc.verts, sc.tris, sc.tri_material, sc.absorption, sc.scattering, **kw)
+
+    def info(self) -> rp_scene_info:
+        out = rp_scene_info()
+        check(self.lib.rp_scene_info_get(self.h, C.byref(out)), "rp_scene_info_get")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) and not _closed and getattr(self.ctx, "h", None):
+            self.lib.rp_scene_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _struct_array(raw: bytes, ctype, n: int):
+    arr = (ctype * n).from_buffer_copy(raw)
+    return arr
+
+
+def stats_to_dict(st: rp_trace_stats, B: int) -> dict:
+    out = {k: np.array(getattr(st, k)[:B]) for k in ("escaped", "absorbed", "remaining", "late")}
+    for k in ("mfp_sum", "mfp_sum_np", "mfp_count", "mfp_count_np", "segments", "shadow_rays", "primaries",
+              "contributions", "sphere_hits", "waves", "hits_stored", "error"):
+        out[k] = getattr(st, k)
+    out["node_visits"] = list(st.node_visits)
+    out["tri_tests"] = list(st.tri_tests)
+    out["mean_free_path"] = st.mfp_sum / st.mfp_count if st.mfp_count else float("nan")
+    out["mean_free_path_np"] = st.mfp_sum_np / st.mfp_count_np if st.mfp_count_np else float("nan")
+    return out
+
+
+def direct_to_dict(raw, S: int, K: int) -> dict:
+    arr = _struct_array(bytes(raw), rp_direct, S)
+    return {"visible": np.array([a.visible for a in arr], bool), "bin": np.array([a.bin for a in arr]),
+            "dist": np.array([a.dist for a in arr]), "time": np.array([a.time for a in arr]),
+            "energy": np.array([a.energy for a in arr]),
+            "sh": np.array([list(a.sh)[:K] for a in arr]).reshape(S, K)}
+
+
+EP_FIELDS = ["rt60_raw", "rt60_smoothed", "fit_hi_db", "fit_lo_db", "fit_r2", "slope_db_per_s",
+             "intercept_db", "i_total", "g_reverb", "e_direct", "drr_db", "predelay_s", "range_kind",
+             "n_fit", "fit_j0", "fit_j1"]
+
+
+def params_to_dict(raw, S: int, B: int, K: int) -> dict:
+    arr = _struct_array(bytes(raw), rp_reverb_params, S * B)
+    out = {f: np.array([getattr(a, f) for a in arr]).reshape(S, B) for f in EP_FIELDS}
+    out["xbar"] = np.array([list(a.xbar)[:K] for a in arr]).reshape(S, B, K)
+    return out
+
+
+class DeviceTrace:
+    """Device outputs of rp_trace: H (torch float32 [S,B,K,T] on cuda), direct
+    (rp_direct[S] bytes), stats (rp_trace_stats bytes), optional ray hashes."""
+
+    def __init__(self, S, B, K, T, want_hash=0, device="cuda"):
+        import torch
+        self.S, self.B, self.K, self.T = S, B, K, T
+        self.H = torch.empty((S, B, K, T), dtype=torch.float32, device=device)
+        self.direct = torch.zeros(max(S, 1) * C.sizeof(rp_direct), dtype=torch.uint8, device=device)
+        self.stats = torch.zeros(C.sizeof(rp_trace_stats), dtype=torch.uint8, device=device)
+        self.ray_hash = torch.zeros(max(want_hash, 1), dtype=torch.int64, device=device) if want_hash else None
+
+    def stats_dict(self) -> dict:
+        st = rp_trace_stats.from_buffer_copy(bytes(self.stats.cpu().numpy()))
+        return stats_to_dict(st, self.B)
+
+    def direct_dict(self) -> dict:
+        return direct_to_dict(self.direct.cpu().numpy()[: self.S * C.sizeof(rp_direct)], self.S, self.K)
+
+    def hashes(self) -> np.ndarray:
+        return self.ray_hash.cpu().numpy().view(np.uint64)
+
+
+def trace(scene: Scene, p: TraceParams, listener, sources, out: DeviceTrace | None = None,
+          sync: bool = True) -> DeviceTrace:
+    """One rp_trace with host positions; returns the device outputs."""
+    lis = np.ascontiguousarray(listener, np.float32).reshape(3)
+    src = np.ascontiguousarray(sources, np.float32).reshape(-1, 3)
+    S = src.shape[0]
+    if out is None:
+        out = DeviceTrace(S, scene.B, p.K, p.num_bins,
+                          want_hash=p.num_rays if p.flags & RP_FLAG_RAY_HASH else 0)
+    cp = p.c()
+    check(scene.lib.rp_trace(scene.h, C.byref(cp), _ptr(lis), _ptr(src), S, _ptr(out.H), _ptr(out.direct),
+                             _ptr(out.stats), _ptr(out.ray_hash)), "rp_trace")
+    if sync:
+        check(scene.ctx.sync_status(), "rp_trace (device)")
+    return out
+
+
+def estimate(ctx: Context, H, direct, ir_rate_hz: float, dt_update: float = 0.0, tau: float = 0.0,
+             state=None, out=None, sync: bool = True):
+    """rp_estimate on device H [S,B,K,T]; returns (raw rp_reverb_params bytes tensor)."""
+    import torch
+    S, B, K, T = H.shape
+    if out is None:
+        out = torch.empty(max(S * B, 1) * C.sizeof(rp_reverb_params), dtype=torch.uint8, device=H.device)
+    ep = rp_estimate_params(float(ir_rate_hz), float(dt_update), float(tau))
+    check(ctx.lib.rp_estimate(ctx.h, _ptr(H), _ptr(direct), S, B, K, T, C.byref(ep), _ptr(out), _ptr(state)),
+          "rp_estimate")
+    if sync:
+        check(ctx.sync_status(), "rp_estimate (device)")
+    return out
+
+
+def update(scene: Scene, p: TraceParams, ir_rate_hz: float, listener, sources, dt_update: float = 0.0,
+           tau: float = 0.0, state=None, H_host=None, want=("H", "params", "direct", "stats")):
+    """rp_update: host buffers in and out (copies inside the call)."""
+    lis = np.ascontiguousarray(listener, np.float32).reshape(3)
+    src = np.ascontiguousarray(sources, np.float32).reshape(-1, 3)
+    S, B, K, T = src.shape[0], scene.B, p.K, p.num_bins
+    H = H_host if H_host is not None else (np.empty((S, B, K, T), np.float32) if "H" in want else None)
+    prm = (rp_reverb_params * max(S * B, 1))() if "params" in want else None
+    dr = (rp_direct * max(S, 1))() if "direct" in want else None
+    st = rp_trace_stats() if "stats" in want else None
+    cp = p.c()
+    ep = rp_estimate_params(float(ir_rate_hz), float(dt_update), float(tau))
+    check(scene.lib.rp_update(scene.h, C.byref(cp), C.byref(ep), _ptr(lis), _ptr(src), S, _ptr(H),
+                              prm, dr, C.byref(st) if st is not None else None, _ptr(state)), "rp_update")
+    res = {"H": H}
+    if prm is not None:
+        res["params"] = params_to_dict(bytes(prm), S, B, K)
+    if dr is not None:
+        res["direct"] = direct_to_dict(bytes(dr), S, K)
+    if st is not None:
+        res["stats"] = stats_to_dict(st, B)
+    return res

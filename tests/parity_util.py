@@ -1,0 +1,111 @@
+"""Helpers of the GPU-vs-oracle parity tests: run one configuration through the C
+ABI and through the FP64 oracle on the same seeded inputs, and compare.
+
+Bars (from the method's stated tolerances):
+  * per-band relative L1 of the intensity histogram, sum_t |H_gpu - H_ora| over
+    sum_t |H_ora| per (source, band, k = 0): <= 1e-3; the k > 0 coefficients are
+    measured against the same denominator;
+  * fraction of primary rays whose triangle sequence differs (64-bit hash): <= 1e-4;
+  * RT60 and g_reverb within 0.5 % relative, DRR within 10 log10(1.005) dB.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+import oracle
+from paper_1803_00430_gb300 import rpr
+
+L1_BAR = 1e-3
+DIVERGENCE_BAR = 1e-4
+PARAM_BAR = 5e-3
+DRR_BAR_DB = 10 * np.log10(1.005)
+
+
+def oracle_params(p: rpr.TraceParams) -> oracle.TraceParams:
+    return oracle.TraceParams(num_rays=p.num_rays, max_order=p.max_order, sh_order=p.sh_order,
+                              num_bins=p.num_bins, min_order=p.min_order, ir_rate_hz=p.ir_rate_hz,
+                              speed_of_sound=p.speed_of_sound, source_radius=p.source_radius, seed=p.seed,
+                              scene_id=p.scene_id, budget_refill=p.budget_refill, first_ray=p.first_ray)
+
+
+def run_gpu(ctx, sc, p: rpr.TraceParams, want_hash=True, scene=None):
+    scene = scene or rpr.Scene.from_scene(ctx, sc)
+    q = rpr.TraceParams(**{**p.__dict__})
+    if want_hash:
+        q.flags |= rpr.RP_FLAG_RAY_HASH
+    out = rpr.trace(scene, q, sc.listener, sc.sources)
+    prm = rpr.estimate(ctx, out.H, out.direct, p.ir_rate_hz)
+    return {
+        "H": out.H.double().cpu().numpy(),
+        "stats": out.stats_dict(),
+        "direct": out.direct_dict(),
+        "hash": out.hashes()[: p.num_rays] if want_hash else None,
+        "params": rpr.params_to_dict(prm.cpu().numpy().tobytes(), sc.num_sources, sc.num_bands, p.K),
+        "scene": scene,
+        "out": out,
+    }
+
+
+def run_oracle(sc, p: rpr.TraceParams, want_hash=True, threads=None):
+    osc = oracle.OracleScene.from_scene(sc)
+    op = oracle_params(p)
+    H, st, hh = oracle.trace_parallel(osc, op, sc.listener, sc.sources, threads=threads or os.cpu_count(),
+                                      hash_cap=p.num_rays if want_hash else 0)
+    dd = oracle.direct(osc, op, sc.listener, sc.sources)
+    ep = oracle.estimate(H, dd["energy"], p.ir_rate_hz)
+    return {"H": H, "stats": st, "direct": dd, "hash": hh, "params": ep, "scene": osc}
+
+
+def band_l1(Hg, Ho):
+    """Per (source, band): L1 of k = 0 and the largest L1 of k > 0, both relative to
+    sum_t |H_ora[k = 0]|."""
+    den = np.abs(Ho[:, :, 0]).sum(-1)
+    den = np.where(den > 0, den, 1.0)
+    l1_0 = np.abs(Hg[:, :, 0] - Ho[:, :, 0]).sum(-1) / den
+    l1_k = (np.abs(Hg[:, :, 1:] - Ho[:, :, 1:]).sum(-1).max(-1) / den) if Hg.shape[2] > 1 else l1_0 * 0
+    return l1_0, l1_k
+
+
+def divergence(hg, ho):
+    return float(np.mean(hg != ho)) if len(hg) else 0.0
+
+
+def param_errors(pg, po):
+    ok = (po["range_kind"] > 0) & (pg["range_kind"] > 0)
+    rt = np.abs(pg["rt60_raw"] - po["rt60_raw"]) / po["rt60_raw"]
+    gr = np.abs(pg["g_reverb"] - po["g_reverb"]) / po["g_reverb"]
+    fin = np.isfinite(po["drr_db"]) & np.isfinite(pg["drr_db"])
+    drr = np.abs(pg["drr_db"] - po["drr_db"])
+    return {
+        "rt60": float(np.max(rt[ok])) if ok.any() else 0.0,
+        "g_reverb": float(np.max(gr[ok])) if ok.any() else 0.0,
+        "drr_db": float(np.max(drr[fin])) if fin.any() else 0.0,
+        "range_kind_equal": bool(np.all(pg["range_kind"] == po["range_kind"])),
+        "drr_inf_equal": bool(np.all(np.isfinite(po["drr_db"]) == np.isfinite(pg["drr_db"]))),
+    }
+
+
+def assert_parity(g, o, n_rays, l1_bar=L1_BAR, div_bar=DIVERGENCE_BAR, check_params=True):
+    l1_0, l1_k = band_l1(g["H"], o["H"])
+    report = {"l1_k0_max": float(l1_0.max()), "l1_kpos_max": float(l1_k.max())}
+    if g["hash"] is not None:
+        report["divergence"] = divergence(g["hash"], o["hash"])
+    if check_params:
+        report.update(param_errors(g["params"], o["params"]))
+    assert report["l1_k0_max"] <= l1_bar, report
+    assert report["l1_kpos_max"] <= 2 * l1_bar, report
+    if "divergence" in report:
+        assert report["divergence"] <= max(div_bar, 1.0 / n_rays), report
+    if check_params:
+        assert report["rt60"] <= PARAM_BAR, report
+        assert report["g_reverb"] <= PARAM_BAR, report
+        assert report["drr_db"] <= DRR_BAR_DB, report
+        assert report["drr_inf_equal"], report
+    return report
+
+
+def sizeof(t):
+    return C.sizeof(t)
