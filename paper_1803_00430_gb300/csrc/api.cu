@@ -52,6 +52,7 @@ struct rp_scene {
     rp_ctx *ctx = nullptr;
     int num_tris = 0, num_nodes = 0, num_mats = 0, B = 0, max_depth = 0;
     float tmin = 0.f, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, build_ms = 0.f;
+    double tmin_d = 0.0;
     float4 *nodes = nullptr, *tris = nullptr;
     float *alpha = nullptr, *scat = nullptr, *wdiff = nullptr, *wspec = nullptr;
     uint32_t *thr = nullptr;
@@ -388,6 +389,7 @@ int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
     if ((rc = rp_sync_status(c)) != RP_OK) goto fail;
     cudaEventElapsedTime(&sc->build_ms, e0, e1);
     sc->tmin = o.tmin;
+    sc->tmin_d = o.tmin_d;
     sc->max_depth = o.max_depth;
     for (int k = 0; k < 3; ++k) {
         sc->lo[k] = o.lo[k];
@@ -477,7 +479,7 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
 
     TraceWork w;
     w.sc = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris, sc->num_nodes,
-            sc->B, sc->tmin};
+            sc->B, sc->tmin, sc->tmin_d};
     w.k.S = S;
     w.k.B = sc->B;
     w.k.K = z.K;

@@ -472,7 +472,10 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
             amax = fmaxf(amax, fmaxf(fabsf(hb[6 + k]), fabsf(hb[9 + k])));
         }
         const float diag = sqrtf(diag2);
-        out.tmin = a.ray_eps > 0.f ? a.ray_eps : 1e-6f * diag;
+        double dd2 = 0.0;
+        for (int k = 0; k < 3; ++k) dd2 += ((double)hb[9 + k] - hb[6 + k]) * ((double)hb[9 + k] - hb[6 + k]);
+        out.tmin_d = a.ray_eps > 0.f ? (double)a.ray_eps : 1e-6 * sqrt(dd2);
+        out.tmin = a.ray_eps > 0.f ? a.ray_eps : (float)out.tmin_d;
         out.max_depth = nt > 1 ? hdepth : 0;
         const float pad = 1e-6f * (amax + diag) + 1e-30f;
         if (nt > 1)

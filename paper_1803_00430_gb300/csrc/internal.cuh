@@ -35,7 +35,8 @@ struct SceneView {
     int num_tris;
     int num_nodes;
     int B;
-    float tmin;
+    float tmin;     // self-intersection guard used by FP32 queries
+    double tmin_d;  // the same guard for FP64 re-decisions
 };
 
 // Counters and accumulators of one trace step (device memory, zeroed per step).
@@ -95,6 +96,7 @@ struct BvhOut {
     float *alpha, *scat, *wdiff, *wspec;
     uint32_t *thr;
     float tmin;
+    double tmin_d;
     float lo[3], hi[3];
     int max_depth;
 };

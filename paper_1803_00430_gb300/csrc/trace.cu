@@ -278,8 +278,26 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
         const float3 of = to_f3(o), df = to_f3(d);
         const float Lf = (float)L;
         float tf;
-        const int tri = traverse<false, COUNT>(sc, of, df, sc.tmin, INFINITY, prev, sstack + threadIdx.x, tf, ts,
-                                               w.status);
+        bool amb = false, exact = false;
+        int tri;
+        R t_exact = 0;
+        if (sizeof(R) == 8) {
+            tri = traverse<false, COUNT, true>(sc, of, df, sc.tmin, INFINITY, prev, sstack + threadIdx.x, tf, ts,
+                                               w.status, &amb);
+            if (amb) {
+                // the FP32 answer may depend on rounding: decide it in FP64
+                double te;
+                tri = traverse_exact<false>(sc, D3{(double)o.x, (double)o.y, (double)o.z},
+                                            D3{(double)d.x, (double)d.y, (double)d.z}, sc.tmin_d, INFINITY, prev,
+                                            sstack + threadIdx.x, te, w.status);
+                exact = true;
+                t_exact = (R)te;
+                tf = (float)te;
+            }
+        } else {
+            tri = traverse<false, COUNT, false>(sc, of, df, sc.tmin, INFINITY, prev, sstack + threadIdx.x, tf, ts,
+                                                w.status);
+        }
         ++segs;
         if (spec_prev && h - 1 >= k.min_order) {
             // the source as a sphere of radius r_s, seen through the specular bounce
@@ -333,8 +351,8 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
                          tc = __ldg(sc.tris + 3 * tri + 2);
             const V3<R> v0 = from4<R>(ta), e1 = from4<R>(tb) - v0, e2 = from4<R>(tc) - v0;
             // hit distance on the chosen triangle in the path precision
-            R t = (R)tf;
-            if (sizeof(R) == 8) {
+            R t = exact ? t_exact : (R)tf;
+            if (sizeof(R) == 8 && !exact) {
                 const V3<R> pv = cross3(d, e2);
                 const R det = dot3(e1, pv);
                 if (det != (R)0) t = dot3(e2, cross3(o - v0, e1)) / det;
@@ -429,7 +447,7 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
     acc_flush(acc, w.stats, B, 0);
 }
 
-template <bool COUNT>
+template <bool COUNT, bool EXACT>
 __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned long long chunk)
 {
     __shared__ int sstack[SMEM_STACK * SHADOW_THREADS];
@@ -470,8 +488,19 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
                 ++shadow;
                 const float3 dir = v * (1.0f / dist);
                 float tt;
-                const int blk = traverse<true, COUNT>(sc, p, dir, sc.tmin, dist, __float_as_int(N.w),
-                                                      sstack + threadIdx.x, tt, ts, w.status);
+                bool amb = false;
+                int blk = traverse<true, COUNT, EXACT>(sc, p, dir, sc.tmin, dist, __float_as_int(N.w),
+                                                       sstack + threadIdx.x, tt, ts, w.status, &amb);
+                if (EXACT && amb) {
+                    // visibility may depend on rounding: decide it in FP64 from the stored residuals
+                    const float4 lo = w.hits.plo[j];
+                    const D3 pd = {(double)P.x + lo.x, (double)P.y + lo.y, (double)P.z + lo.z};
+                    const double vx = (double)cs.x - pd.x, vy = (double)cs.y - pd.y, vz = (double)cs.z - pd.z;
+                    const double dd = sqrt(vx * vx + vy * vy + vz * vz);
+                    double te;
+                    blk = traverse_exact<true>(sc, pd, D3{vx / dd, vy / dd, vz / dd}, sc.tmin_d, dd,
+                                               __float_as_int(N.w), sstack + threadIdx.x, te, w.status);
+                }
                 if (blk < 0) {
                     ++contrib;
                     const float f = cth * inv_pi / dist2;
@@ -520,8 +549,15 @@ __global__ void __launch_bounds__(128) k_direct(TraceWork w)
     const float3 dir = mk3((float)(vx / dist), (float)(vy / dist), (float)(vz / dist));
     TravStats ts = {0u, 0u};
     float tt;
-    const int blk = traverse<true, false>(w.sc, xyz(l4), dir, w.sc.tmin, (float)dist, -1, sstack + threadIdx.x, tt,
-                                          ts, w.status);
+    bool amb = false;
+    int blk = traverse<true, false, true>(w.sc, xyz(l4), dir, w.sc.tmin, (float)dist, -1, sstack + threadIdx.x, tt,
+                                          ts, w.status, &amb);
+    if (amb) {
+        double te;
+        blk = traverse_exact<true>(w.sc, D3{(double)l4.x, (double)l4.y, (double)l4.z},
+                                   D3{vx / dist, vy / dist, vz / dist}, w.sc.tmin_d, dist, -1, sstack + threadIdx.x,
+                                   te, w.status);
+    }
     rp_direct out;
     out.visible = blk < 0 ? 1 : 0;
     out.dist = (float)dist;
@@ -559,8 +595,12 @@ void launch_paths(const TraceWork &w, int blocks, cudaStream_t st)
 
 void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
 {
-    if (w.k.flags & RP_FLAG_COUNT_VISITS) k_shadow<true><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
-    else k_shadow<false><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    const bool count = (w.k.flags & RP_FLAG_COUNT_VISITS) != 0;
+    const bool exact = (w.k.flags & RP_FLAG_FP32_PATHS) == 0;
+    if (count && exact) k_shadow<true, true><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    else if (count) k_shadow<true, false><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    else if (exact) k_shadow<false, true><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    else k_shadow<false, false><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
 }
 
 void launch_direct(const TraceWork &w, cudaStream_t st)
@@ -581,8 +621,10 @@ int paths_occupancy(int flags)
 int shadow_occupancy(int flags)
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false>, SHADOW_THREADS, 0);
-    (void)flags;
+    if (flags & RP_FLAG_FP32_PATHS)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false, false>, SHADOW_THREADS, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false, true>, SHADOW_THREADS, 0);
     return n > 0 ? n : 1;
 }
 

@@ -10,7 +10,14 @@
 // Closest hit: the nearest t in (tmin, tmax); equal t goes to the smaller original
 // triangle index.  Any hit: some triangle with tmin < t < tmax.  The triangle
 // `exclude` (leaf order) is skipped, which keeps a ray from re-hitting the surface
-// it leaves.  Triangle test: Moller-Trumbore, two-sided, in FP32.
+// it leaves.  Triangle test: Moller-Trumbore, two-sided.
+//
+// Precision: boxes and triangles are tested in FP32.  A query can ask to be told
+// when its answer may depend on FP32 rounding -- a tested triangle lay within
+// AMBIG_BARY (barycentric) of an edge at a distance that could decide the answer,
+// or a hit lay within a relative AMBIG_T of t_min.  Such queries are re-run by
+// traverse_exact(), whose triangle tests are FP64 on the FP64 ray; its box tests stay
+// FP32 on the rounded ray, which the padding of the boxes keeps conservative.
 #pragma once
 
 #include "internal.cuh"
@@ -21,36 +28,71 @@ constexpr int SMEM_STACK = 24;
 constexpr int LOCAL_STACK = 40;
 constexpr int STACK_DEPTH = SMEM_STACK + LOCAL_STACK;
 constexpr int ITER_CAP_MULT = 4;  // node visits per query are capped at 4 x nodes + 64
+constexpr float AMBIG_BARY = 2e-4f;
+constexpr float AMBIG_T = 2e-4f;
 
 struct TravStats {
     uint32_t nodes;
     uint32_t tris;
 };
 
+struct D3 {
+    double x, y, z;
+};
+
+// FP32 Moller-Trumbore: t, the signed barycentric margin min(u, v, 1-u-v)
+// (negative outside), and whether the ray passes inside the triangle.
 __device__ __forceinline__ bool tri_intersect(const float4 *__restrict__ tris, int i, float3 o, float3 d,
-                                              float &t, uint32_t &orig)
+                                              float &t, uint32_t &orig, float &margin)
 {
     const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
     const float3 e1 = xyz(b) - xyz(a), e2 = xyz(c) - xyz(a);
     const float3 p = cross(d, e2);
     const float det = dot(e1, p);
-    if (det == 0.0f) return false;
+    if (det == 0.0f) {
+        margin = -1.0f;
+        t = -1.0f;
+        return false;
+    }
     const float inv = 1.0f / det;
     const float3 s = o - xyz(a);
     const float u = dot(s, p) * inv;
-    if (u < 0.0f || u > 1.0f) return false;
     const float3 q = cross(s, e1);
     const float v = dot(d, q) * inv;
-    if (v < 0.0f || u + v > 1.0f) return false;
     t = dot(e2, q) * inv;
+    orig = __float_as_uint(b.w);
+    margin = fminf(fminf(u, v), 1.0f - u - v);
+    return u >= 0.0f && u <= 1.0f && v >= 0.0f && u + v <= 1.0f;
+}
+
+// FP64 Moller-Trumbore on the exact input vertices (the FP64 reference test)
+__device__ __forceinline__ bool tri_intersect_d(const float4 *__restrict__ tris, int i, D3 o, D3 d, double &t,
+                                                uint32_t &orig)
+{
+    const float4 a = __ldg(tris + 3 * i), b = __ldg(tris + 3 * i + 1), c = __ldg(tris + 3 * i + 2);
+    const double e1x = (double)b.x - a.x, e1y = (double)b.y - a.y, e1z = (double)b.z - a.z;
+    const double e2x = (double)c.x - a.x, e2y = (double)c.y - a.y, e2z = (double)c.z - a.z;
+    const double px = d.y * e2z - d.z * e2y, py = d.z * e2x - d.x * e2z, pz = d.x * e2y - d.y * e2x;
+    const double det = e1x * px + e1y * py + e1z * pz;
+    if (det == 0.0) return false;
+    const double inv = 1.0 / det;
+    const double sx = o.x - a.x, sy = o.y - a.y, sz = o.z - a.z;
+    const double u = (sx * px + sy * py + sz * pz) * inv;
+    if (u < 0.0 || u > 1.0) return false;
+    const double qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+    const double v = (d.x * qx + d.y * qy + d.z * qz) * inv;
+    if (v < 0.0 || u + v > 1.0) return false;
+    t = (e2x * qx + e2y * qy + e2z * qz) * inv;
     orig = __float_as_uint(b.w);
     return true;
 }
 
-template <bool ANY, bool COUNT>
-__device__ __forceinline__ int traverse(const SceneView &sc, float3 o, float3 d, float tmin, float tmax,
-                                        int exclude, int *__restrict__ sstack, float &t_out, TravStats &ts,
-                                        int *status)
+// Shared traversal loop.  `bound` is the current far limit of the query (the best
+// hit so far, or tmax); leaf(tri) tests one triangle, may lower `bound`, and returns
+// true to stop the query.
+template <bool COUNT, typename Leaf>
+__device__ __forceinline__ void traverse_core(const SceneView &sc, float3 o, float3 d, float tmin, float &bound,
+                                              int *__restrict__ sstack, TravStats &ts, int *status, Leaf leaf)
 {
     const int stride = blockDim.x;
     int lstack[LOCAL_STACK];
@@ -60,51 +102,24 @@ __device__ __forceinline__ int traverse(const SceneView &sc, float3 o, float3 d,
     const float3 idir = mk3(1.0f / ex, 1.0f / ey, 1.0f / ez);
     const float3 ood = mk3(o.x * idir.x, o.y * idir.y, o.z * idir.z);
 
-    int best = -1;
-    uint32_t best_orig = 0xffffffffu;
-    float best_t = tmax;
-
-    auto leaf = [&](int tri) -> bool {
-        if (COUNT) ts.tris++;
-        if ((unsigned)tri >= (unsigned)sc.num_tris) {  // corrupt structure: record, skip
-            raise_error(status, RP_ERR_INVALID_ARG);
-            return false;
-        }
-        float t;
-        uint32_t orig;
-        if (tri != exclude && tri_intersect(sc.tris, tri, o, d, t, orig) && t > tmin) {
-            if (ANY) {
-                if (t < tmax) {
-                    best = tri;
-                    best_t = t;
-                    return true;
-                }
-            } else if (t < best_t || (t == best_t && best >= 0 && orig < best_orig)) {
-                best = tri;
-                best_t = t;
-                best_orig = orig;
-            }
-        }
-        return false;
-    };
-
     if (sc.num_nodes == 0) {
-        if (sc.num_tris > 0) leaf(0);
-        t_out = best_t;
-        return best;
+        if (sc.num_tris > 0) {
+            if (COUNT) ts.tris++;
+            leaf(0);
+        }
+        return;
     }
-
     const int iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
     int node = 0, sp = 0, iters = 0;
     while (true) {
         if (COUNT) ts.nodes++;
         if (++iters > iter_cap) {
             raise_error(status, RP_ERR_TIMEOUT);
-            break;
+            return;
         }
         if ((unsigned)node >= (unsigned)sc.num_nodes) {  // corrupt structure: record, stop
             raise_error(status, RP_ERR_INVALID_ARG);
-            break;
+            return;
         }
         const float4 *np = sc.nodes + 4 * node;
         const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
@@ -112,20 +127,32 @@ __device__ __forceinline__ int traverse(const SceneView &sc, float3 o, float3 d,
         const float a1 = n0.z * idir.y - ood.y, b1 = n0.w * idir.y - ood.y;
         const float a2 = n2.x * idir.z - ood.z, b2 = n2.y * idir.z - ood.z;
         const float c0min = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), tmin));
-        const float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), best_t));
+        const float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), bound));
         const float a3 = n1.x * idir.x - ood.x, b3 = n1.y * idir.x - ood.x;
         const float a4 = n1.z * idir.y - ood.y, b4 = n1.w * idir.y - ood.y;
         const float a5 = n2.z * idir.z - ood.z, b5 = n2.w * idir.z - ood.z;
         const float c1min = fmaxf(fmaxf(fminf(a3, b3), fminf(a4, b4)), fmaxf(fminf(a5, b5), tmin));
-        const float c1max = fminf(fminf(fmaxf(a3, b3), fmaxf(a4, b4)), fminf(fmaxf(a5, b5), best_t));
+        const float c1max = fminf(fminf(fmaxf(a3, b3), fmaxf(a4, b4)), fminf(fmaxf(a5, b5), bound));
         bool h0 = c0min <= c0max, h1 = c1min <= c1max;
         const int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
         if (h0 && ch0 < 0) {
-            if (leaf(~ch0)) break;
+            const int tri = ~ch0;
+            if (COUNT) ts.tris++;
+            if ((unsigned)tri >= (unsigned)sc.num_tris) {
+                raise_error(status, RP_ERR_INVALID_ARG);
+                return;
+            }
+            if (leaf(tri)) return;
             h0 = false;
         }
         if (h1 && ch1 < 0) {
-            if (leaf(~ch1)) break;
+            const int tri = ~ch1;
+            if (COUNT) ts.tris++;
+            if ((unsigned)tri >= (unsigned)sc.num_tris) {
+                raise_error(status, RP_ERR_INVALID_ARG);
+                return;
+            }
+            if (leaf(tri)) return;
             h1 = false;
         }
         if (h0 && h1) {
@@ -137,7 +164,7 @@ __device__ __forceinline__ int traverse(const SceneView &sc, float3 o, float3 d,
                 lstack[sp - SMEM_STACK] = farc;
             } else {
                 raise_error(status, RP_ERR_STACK_OVERFLOW);
-                break;
+                return;
             }
             ++sp;
             node = nearc;
@@ -146,11 +173,100 @@ __device__ __forceinline__ int traverse(const SceneView &sc, float3 o, float3 d,
         } else if (h1) {
             node = ch1;
         } else {
-            if (sp == 0) break;
+            if (sp == 0) return;
             --sp;
             node = sp < SMEM_STACK ? sstack[sp * stride] : lstack[sp - SMEM_STACK];
         }
     }
+}
+
+// FP32 query.  With FLAG, *ambiguous tells whether the answer may depend on rounding
+// (then the caller re-runs it with traverse_exact).
+template <bool ANY, bool COUNT, bool FLAG>
+__device__ __forceinline__ int traverse(const SceneView &sc, float3 o, float3 d, float tmin, float tmax,
+                                        int exclude, int *__restrict__ sstack, float &t_out, TravStats &ts,
+                                        int *status, bool *ambiguous = nullptr)
+{
+    int best = -1;
+    uint32_t best_orig = 0xffffffffu;
+    float bound = tmax;
+    float amb_t = INFINITY;  // nearest distance of a rounding-sensitive triangle test
+    float second = INFINITY; // closest hit: the runner-up distance (near-ties are sensitive)
+    bool clear = false;      // any-hit: a blocker whose test is not rounding-sensitive
+    const float tlo = tmin * (1.0f - AMBIG_T), tnear = tmin * (1.0f + AMBIG_T);
+    traverse_core<COUNT>(sc, o, d, tmin, bound, sstack, ts, status, [&](int tri) -> bool {
+        if (tri == exclude) return false;
+        float t, margin;
+        uint32_t orig;
+        const bool inside = tri_intersect(sc.tris, tri, o, d, t, orig, margin);
+        if (FLAG && t > tlo && t < tmax * (1.0f + AMBIG_T) &&
+            (fabsf(margin) < AMBIG_BARY || (inside && t < tnear)))
+            amb_t = fminf(amb_t, t);
+        if (!inside || !(t > tmin)) return false;
+        if (ANY) {
+            if (t < tmax) {
+                best = tri;
+                if (!FLAG || (fabsf(margin) >= AMBIG_BARY && t >= tnear)) {
+                    clear = true;
+                    return true;
+                }
+            }
+            return false;
+        }
+        if (t < bound || (t == bound && best >= 0 && orig < best_orig)) {
+            if (FLAG && best >= 0) second = fminf(second, bound);
+            best = tri;
+            bound = t;
+            best_orig = orig;
+        } else if (FLAG) {
+            second = fminf(second, t);
+        }
+        return false;
+    });
+    if (FLAG && ambiguous) {
+        if (ANY) *ambiguous = !clear && amb_t < INFINITY;
+        else *ambiguous = fminf(amb_t, second) <= bound * (1.0f + AMBIG_T) + tmin;
+    }
+    t_out = bound;
+    return best;
+}
+
+// FP64 re-run of a query whose FP32 answer was rounding-sensitive: the same
+// traversal, FP64 triangle tests on the FP64 ray, decisions as in the FP64
+// reference.
+template <bool ANY>
+__device__ __noinline__ int traverse_exact(const SceneView &sc, D3 o, D3 d, double tmin, double tmax, int exclude,
+                                           int *__restrict__ sstack, double &t_out, int *status)
+{
+    int best = -1;
+    uint32_t best_orig = 0xffffffffu;
+    double best_t = tmax;
+    // culling in FP32: bound just above best_t, t_min halved (boxes are padded)
+    float bound = tmax < 3.0e38 ? __double2float_ru(tmax) : INFINITY;
+    TravStats ts = {0u, 0u};
+    const float3 of = mk3((float)o.x, (float)o.y, (float)o.z), df = mk3((float)d.x, (float)d.y, (float)d.z);
+    const float tminf = __double2float_rd(tmin) * 0.5f;
+    traverse_core<false>(sc, of, df, tminf, bound, sstack, ts, status, [&](int tri) -> bool {
+        if (tri == exclude) return false;
+        double t;
+        uint32_t orig;
+        if (!tri_intersect_d(sc.tris, tri, o, d, t, orig) || !(t > tmin)) return false;
+        if (ANY) {
+            if (t < tmax) {
+                best = tri;
+                best_t = t;
+                return true;
+            }
+            return false;
+        }
+        if (t < best_t || (t == best_t && best >= 0 && orig < best_orig)) {
+            best = tri;
+            best_t = t;
+            best_orig = orig;
+            bound = __double2float_ru(t);
+        }
+        return false;
+    });
     t_out = best_t;
     return best;
 }
