@@ -63,7 +63,9 @@ enum {
     RP_ERR_TIMEOUT = -6,        /* a traversal exceeded its iteration cap */
     RP_ERR_NAN_INPUT = -7,      /* a vertex, material or position is not finite */
     RP_ERR_EMPTY_SCENE = -8,    /* zero triangles */
-    RP_ERR_NO_DEVICE = -9       /* no CUDA device or wrong architecture */
+    RP_ERR_NO_DEVICE = -9,      /* no CUDA device or wrong architecture */
+    RP_ERR_TOO_LARGE = -10      /* the problem does not fit the fixed scratch of
+                                   rp_trace_noalloc (RP_NOALLOC_SCRATCH_BYTES) */
 };
 
 /* Where an input array lives. */
@@ -258,6 +260,30 @@ int rp_update(rp_scene *scene, const rp_trace_params *params,
               const rp_estimate_params *est, const float *listener, const float *sources,
               int32_t num_sources, float *H_host, rp_reverb_params *params_host,
               rp_direct *direct_host, rp_trace_stats *stats_host, double *state_host);
+
+/* Size of the fixed device scratch array used by rp_trace_noalloc: 64 MiB, held by
+ * every GPU that loads the library for the life of the process. */
+#define RP_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* rp_trace without any memory allocation.  The paper has no counterpart: it exists
+ * for callers that must not allocate device memory during an update -- a real-time
+ * audio or game thread that cannot block on the driver's allocator mid-frame, code
+ * running while a stream is captured into a CUDA graph (cudaMalloc is not allowed
+ * there), or applications that hand out all device memory from their own pool.
+ * Same arguments and outputs as rp_trace (no ray hashes); the scene and context are
+ * created beforehand with rp_create / rp_scene_create.  All temporaries come from
+ * one static __device__ array of RP_NOALLOC_SCRATCH_BYTES; no cudaMalloc, cudaFree or
+ * other allocating call is made.  Problems whose temporaries do not fit return
+ * RP_ERR_TOO_LARGE (roughly: 68 + 4B bytes per ray x reflection for the stored
+ * reflections, 8 B per (source, bin) and 8 B per histogram cell, the rest holds
+ * contribution records).
+ * The first call on a device looks up the array's device address with that device
+ * current: make it before any stream capture.  Every call shares the array and
+ * overwrites the previous call's temporaries, so calls that may overlap on the GPU
+ * (several streams or host threads) race and must be serialised by the caller. */
+int rp_trace_noalloc(rp_scene *scene, const rp_trace_params *params, const float *listener,
+                     const float *sources, int32_t num_sources, float *H, rp_direct *direct,
+                     rp_trace_stats *stats);
 
 /* Synchronise the context stream and return the first device-side error (or a CUDA
  * error).  Clears the recorded device error. */

@@ -10,53 +10,9 @@
 #include <string>
 #include <vector>
 
-#include "internal.cuh"
+#include "handles.cuh"
 
 using namespace rp;
-
-namespace {
-
-// Records kept in device memory at once (one chunk of next-event work plus the
-// records of source-sphere hits).  40 bytes each at 8 bands.
-constexpr unsigned long long REC_BUDGET = 1ull << 28;
-
-struct Buf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-struct ProfPair {
-    const char *name;
-    cudaEvent_t a, b;
-};
-
-}  // namespace
-
-struct rp_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int num_sms = 0;
-    int *d_status = nullptr;
-    int paths_blocks = 0, shadow_blocks = 0;
-    // workspace
-    Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, rec_key, rec_rid, rec_e, perm, cnt, off, cur, Hs, He, src, ctr,
-        stats, H, direct, params, state;
-    // profiling
-    bool prof = false;
-    std::vector<ProfPair> pending;
-    std::vector<cudaEvent_t> free_events;
-    std::map<std::string, std::pair<unsigned long long, double>> totals;
-};
-
-struct rp_scene {
-    rp_ctx *ctx = nullptr;
-    int num_tris = 0, num_nodes = 0, num_mats = 0, B = 0, max_depth = 0;
-    float tmin = 0.f, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, build_ms = 0.f;
-    double tmin_d = 0.0;
-    float4 *nodes = nullptr, *tris = nullptr;
-    float *alpha = nullptr, *scat = nullptr, *wdiff = nullptr, *wspec = nullptr;
-    uint32_t *thr = nullptr;
-};
 
 namespace {
 
@@ -243,6 +199,7 @@ const char *rp_status_string(int s)
     case RP_ERR_NAN_INPUT: return "non-finite input";
     case RP_ERR_EMPTY_SCENE: return "scene has no triangles";
     case RP_ERR_NO_DEVICE: return "no usable CUDA device";
+    case RP_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of rp_trace_noalloc";
     default: return "unknown status";
     }
 }

@@ -1,0 +1,225 @@
+// noalloc.cu -- rp_trace_noalloc: the trace step with its scratch memory in a fixed,
+// statically allocated device array instead of library-allocated workspace.
+//
+// rp_trace allocates (and grows) device workspace with cudaMalloc the first time a
+// problem size is seen.  Some callers cannot allow that: a real-time audio or game
+// thread that must never block on the driver's allocator mid-frame, code that runs
+// while a CUDA stream is being captured into a graph (cudaMalloc is not permitted
+// there), or a host application that owns all device memory through its own pool.
+// rp_trace_noalloc runs the same kernels on the same inputs and writes the same
+// outputs, but takes every temporary buffer (counters, stored reflections,
+// contribution records, the counting sort, the compensated sums) from one
+// file-scope __device__ array of RP_NOALLOC_SCRATCH_BYTES.  It calls no cudaMalloc,
+// cudaFree or allocating routine, on the device or the host.
+//
+// Consequences of a shared static array:
+//   - every GPU that loads the library holds RP_NOALLOC_SCRATCH_BYTES until exit;
+//   - all calls on a device share the one array, which keeps the previous call's
+//     contents (this file clears what must start at zero); calls that overlap on
+//     the GPU (other streams, other host threads) race on it and must be ordered
+//     by the caller;
+//   - the device address of the array is looked up once per device, with that
+//     device current, on the first call there: make that first call before any
+//     stream capture begins.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "handles.cuh"
+
+using namespace rp;
+
+// the scratch array of the allocation-free entry point (see above)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void *g_scratch_ptr[MAX_DEVICES] = {};
+
+// device address of g_noalloc_scratch on the current device `dev`, looked up once
+int scratch_address(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= MAX_DEVICES) return RP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return RP_ERR_CUDA;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = (unsigned char *)g_scratch_ptr[dev];
+    return RP_OK;
+}
+
+struct Carve {
+    unsigned long long off = 0;
+    template <typename T>
+    unsigned long long take(unsigned long long count)
+    {
+        const unsigned long long at = off;
+        off += (sizeof(T) * std::max(count, 1ull) + 255ull) & ~255ull;
+        return at;
+    }
+};
+
+__global__ void k_pack_positions_na(const float *lis, const float *src, int S, float4 *out, int *status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > S) return;
+    const float *p = i < S ? src + 3 * i : lis;
+    const float x = p[0], y = p[1], z = p[2];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) raise_error(status, RP_ERR_NAN_INPUT);
+    out[i] = make_float4(x, y, z, 0.f);
+}
+
+__global__ void k_copy_status_na(const int *status, const TraceCounters *ctr, rp_trace_stats *st)
+{
+    st->error = *status;
+    st->hits_stored = ctr->n_hits;
+}
+
+#define CKN(x)                                        \
+    do {                                              \
+        const cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return RP_ERR_CUDA;    \
+    } while (0)
+
+}  // namespace
+
+extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const float *listener, const float *sources,
+                                int32_t S, float *H, rp_direct *direct, rp_trace_stats *stats)
+{
+    if (!sc || !p || !listener || (S > 0 && (!sources || !H))) return RP_ERR_INVALID_ARG;
+    if (S < 0 || S > RP_MAX_SOURCES) return RP_ERR_INVALID_ARG;
+    if (p->max_order < 0 || p->sh_order < 0 || p->sh_order > RP_MAX_SH_ORDER || p->num_bins < 1 || p->min_order < 0)
+        return RP_ERR_INVALID_ARG;
+    if (p->num_rays > 0xffffffffull || p->first_ray + p->num_rays > 0x100000000ull) return RP_ERR_INVALID_ARG;
+    if (!(p->ir_rate_hz > 0.f) || !(p->speed_of_sound > 0.f) || !(p->source_radius > 0.f)) return RP_ERR_INVALID_ARG;
+    if (!std::isfinite(p->ir_rate_hz) || !std::isfinite(p->speed_of_sound) || !std::isfinite(p->source_radius))
+        return RP_ERR_NAN_INPUT;
+    rp_ctx *c = sc->ctx;
+    const int B = sc->B, K = (p->sh_order + 1) * (p->sh_order + 1), T = p->num_bins, M = p->max_order;
+    const unsigned long long keys = (unsigned long long)S * T, cells = keys * B * K;
+    const unsigned long long hit_cap = std::max(1ull, p->num_rays * (unsigned long long)M);
+    const unsigned long long sph_cap = hit_cap / 2 + 4096;
+    const unsigned long long s1 = (unsigned long long)std::max(S, 1);
+
+    // fixed part of the layout
+    Carve cv;
+    const unsigned long long o_ctr = cv.take<TraceCounters>(1), o_st = cv.take<rp_trace_stats>(1);
+    const unsigned long long o_src = cv.take<float4>(S + 1), o_raw = cv.take<float>(3ull * (S + 1));
+    const unsigned long long o_hp = cv.take<float4>(hit_cap), o_hl = cv.take<float4>(hit_cap),
+                             o_hn = cv.take<float4>(hit_cap), o_hw = cv.take<float>(hit_cap * B),
+                             o_hr = cv.take<uint32_t>(hit_cap);
+    const unsigned long long o_cnt = cv.take<uint32_t>(keys), o_off = cv.take<uint32_t>(keys + 1),
+                             o_cur = cv.take<uint32_t>(keys);
+    const unsigned long long o_hs = cv.take<float>(cells), o_he = cv.take<float>(cells);
+    if (cv.off >= RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
+    // the rest holds contribution records: key, ray, energies, sort index
+    const unsigned long long per_rec = 4ull + 4ull + 4ull * B + 4ull + 16ull;  // + alignment slack
+    const unsigned long long rec_room = (RP_NOALLOC_SCRATCH_BYTES - cv.off) / per_rec;
+    if (rec_room < sph_cap + s1) return RP_ERR_TOO_LARGE;
+    const unsigned long long chunk_hits = std::max(1ull, std::min(hit_cap, (rec_room - sph_cap) / s1));
+    const unsigned long long n_chunks = (hit_cap + chunk_hits - 1) / chunk_hits;
+    const unsigned long long rec_cap = sph_cap + chunk_hits * s1;
+    const unsigned long long o_rk = cv.take<uint32_t>(rec_cap), o_rr = cv.take<uint32_t>(rec_cap),
+                             o_re = cv.take<float>(rec_cap * B), o_pm = cv.take<uint32_t>(rec_cap);
+    if (cv.off > RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
+
+    CKN(cudaSetDevice(c->device));
+    unsigned char *base = nullptr;
+    int rc = scratch_address(c->device, &base);
+    if (rc) return rc;
+    cudaStream_t st = c->stream;
+
+    float4 *dsrc = (float4 *)(base + o_src);
+    const float *lis = listener, *srcs = sources;
+    if (!(p->flags & RP_FLAG_DEVICE_POSITIONS)) {
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(listener[i])) return RP_ERR_NAN_INPUT;
+        for (long long i = 0; i < 3ll * S; ++i)
+            if (!std::isfinite(sources[i])) return RP_ERR_NAN_INPUT;
+        float *raw = (float *)(base + o_raw);
+        if (S > 0) CKN(cudaMemcpyAsync(raw, sources, sizeof(float) * 3 * S, cudaMemcpyHostToDevice, st));
+        CKN(cudaMemcpyAsync(raw + 3 * S, listener, sizeof(float) * 3, cudaMemcpyHostToDevice, st));
+        lis = raw + 3 * S;
+        srcs = raw;
+    }
+    k_pack_positions_na<<<(S + 1 + 127) / 128, 128, 0, st>>>(lis, srcs, S, dsrc, c->d_status);
+
+    TraceWork w;
+    w.sc = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris, sc->num_nodes,
+            sc->B, sc->tmin, sc->tmin_d};
+    w.k.S = S;
+    w.k.B = B;
+    w.k.K = K;
+    w.k.T = T;
+    w.k.M = M;
+    w.k.min_order = p->min_order;
+    w.k.sh_order = p->sh_order;
+    w.k.rate = p->ir_rate_hz;
+    w.k.c = p->speed_of_sound;
+    w.k.rs = p->source_radius;
+    w.k.scene_id = p->scene_id;
+    w.k.key0 = (uint32_t)p->seed;
+    w.k.key1 = (uint32_t)(p->seed >> 32);
+    w.k.num_rays = p->num_rays;
+    w.k.first_ray = p->first_ray;
+    w.k.flags = p->flags & ~RP_FLAG_RAY_HASH;
+    w.src = dsrc;
+    w.ctr = (TraceCounters *)(base + o_ctr);
+    w.hits = {(float4 *)(base + o_hp), (float4 *)(base + o_hl), (float4 *)(base + o_hn), (float *)(base + o_hw),
+              (uint32_t *)(base + o_hr), hit_cap};
+    w.rec = {(uint32_t *)(base + o_rk), (uint32_t *)(base + o_rr), (float *)(base + o_re), rec_cap};
+    w.stats = (rp_trace_stats *)(base + o_st);
+    w.ray_hash = nullptr;
+    w.status = c->d_status;
+    w.cnt = (uint32_t *)(base + o_cnt);
+    w.off = (uint32_t *)(base + o_off);
+    w.cur = (uint32_t *)(base + o_cur);
+    w.perm = (uint32_t *)(base + o_pm);
+    w.Hs = (float *)(base + o_hs);
+    w.He = (float *)(base + o_he);
+    w.H = H;
+    w.direct = direct;
+    w.hits_per_chunk = chunk_hits;
+    w.num_sms = c->num_sms;
+
+    // what must start at zero: the counters and the statistics of this step
+    CKN(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
+    CKN(cudaMemsetAsync(w.stats, 0, sizeof(rp_trace_stats), st));
+    launch_wave_setup(w, 0, st);
+    if (M > 0) launch_paths(w, c->paths_blocks, st);
+    if (p->budget_refill && M > 0) {
+        for (int wave = 1; wave < 4096; ++wave) {
+            launch_wave_setup(w, wave, st);
+            unsigned long long cnt = 0;
+            CKN(cudaMemcpyAsync(&cnt, &w.ctr->wave_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+            CKN(cudaStreamSynchronize(st));
+            if (cnt == 0) break;
+            launch_paths(w, c->paths_blocks, st);
+        }
+    }
+    launch_direct(w, st);
+    const int grid_flat = c->num_sms * 8;
+    const int acc_blocks =
+        (int)std::max(1ll, std::min<long long>(((long long)keys + 7) / 8, (long long)c->num_sms * 8));
+    for (unsigned long long ch = 0; ch < n_chunks && S > 0; ++ch) {
+        if (ch > 0) CKN(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
+        CKN(cudaMemsetAsync(&w.ctr->next_item, 0, sizeof(unsigned long long), st));
+        if (M > 0) launch_shadow(w, ch, c->shadow_blocks, st);
+        CKN(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * keys, st));
+        CKN(cudaMemsetAsync(w.cur, 0, sizeof(uint32_t) * keys, st));
+        launch_count(w, grid_flat, st);
+        launch_scan(w, st);
+        launch_scatter(w, grid_flat, st);
+        launch_accum(w, ch == 0 ? 1 : 0, acc_blocks, st);
+    }
+    if (S > 0) launch_finalize(w, st);
+    k_copy_status_na<<<1, 1, 0, st>>>(c->d_status, w.ctr, w.stats);
+    CKN(cudaGetLastError());
+    if (stats) CKN(cudaMemcpyAsync(stats, w.stats, sizeof(rp_trace_stats), cudaMemcpyDeviceToDevice, st));
+    return RP_OK;
+}

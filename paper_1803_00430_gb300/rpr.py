@@ -29,7 +29,7 @@ RP_OK = 0
 STATUS = {
     0: "RP_OK", -1: "RP_ERR_INVALID_ARG", -2: "RP_ERR_CUDA", -3: "RP_ERR_OOM", -4: "RP_ERR_CAPACITY",
     -5: "RP_ERR_STACK_OVERFLOW", -6: "RP_ERR_TIMEOUT", -7: "RP_ERR_NAN_INPUT", -8: "RP_ERR_EMPTY_SCENE",
-    -9: "RP_ERR_NO_DEVICE",
+    -9: "RP_ERR_NO_DEVICE", -10: "RP_ERR_TOO_LARGE",
 }
 RP_ERR = {v: k for k, v in STATUS.items()}
 RP_MEM_HOST, RP_MEM_DEVICE = 0, 1
@@ -105,6 +105,8 @@ _SIGS = {
     "rp_update": ([C.c_void_p, C.POINTER(rp_trace_params), C.POINTER(rp_estimate_params), C.c_void_p,
                    C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                   C.c_int),
+    "rp_trace_noalloc": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                          C.c_void_p, C.c_void_p], C.c_int),
     "rp_sync_status": ([C.c_void_p], C.c_int),
     "rp_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
     "rp_profile_reset": ([C.c_void_p], C.c_int),
@@ -385,6 +387,22 @@ def trace(scene: Scene, p: TraceParams, listener, sources, out: DeviceTrace | No
                              _ptr(out.stats), _ptr(out.ray_hash)), "rp_trace")
     if sync:
         check(scene.ctx.sync_status(), "rp_trace (device)")
+    return out
+
+
+def trace_noalloc(scene: Scene, p: TraceParams, listener, sources, out: DeviceTrace | None = None,
+                  sync: bool = True) -> DeviceTrace:
+    """rp_trace_noalloc (no memory allocation inside the call); host positions."""
+    lis = np.ascontiguousarray(listener, np.float32).reshape(3)
+    src = np.ascontiguousarray(sources, np.float32).reshape(-1, 3)
+    S = src.shape[0]
+    if out is None:
+        out = DeviceTrace(S, scene.B, p.K, p.num_bins)
+    cp = p.c()
+    check(scene.lib.rp_trace_noalloc(scene.h, C.byref(cp), _ptr(lis), _ptr(src), S, _ptr(out.H),
+                                     _ptr(out.direct), _ptr(out.stats)), "rp_trace_noalloc")
+    if sync:
+        check(scene.ctx.sync_status(), "rp_trace_noalloc (device)")
     return out
 
 
