@@ -170,7 +170,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp32-paths", action="store_true", help="time the all-FP32 path precision form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--rays", type=int, default=0, help="primaries per update (default: the workload's 200k; "
+                    "smaller values make a small case for profilers)")
     args = ap.parse_args()
+    if args.rays:
+        WORKLOAD["num_rays"] = args.rays
     if args.impl == "reference":
         return run_reference(args)
 
@@ -264,23 +269,23 @@ def main():
     stc = out.stats_dict()
 
     # e2e: the public host-buffer entry point, H2D of positions and D2H of H + parameters
+    e2e_total, e2e_steps = 0.0, 1
     Hh = torch.empty((S, B, K, T), dtype=torch.float32).pin_memory().numpy()
     lis_h = torch.tensor(sc.listener).pin_memory().numpy()
     src_h = torch.tensor(sc.sources).pin_memory().numpy()
     e2e_p = rpr.TraceParams(**WORKLOAD, flags=flags & ~rpr.RP_FLAG_DEVICE_POSITIONS, scene_id=rank)
-    for i in range(max(1, args.warmup)):
+    for i in range(0 if args.no_e2e else max(1, args.warmup)):
         e2e_p.seed = scenes.PHILOX_KEY_BASE + i
         rpr.update(scene, e2e_p, e2e_p.ir_rate_hz, lis_h, src_h, H_host=Hh, want=("H", "params"))
-    e2e_steps = max(3, min(args.steps, 10))
-    e2e_total = 0.0
-    for i in range(e2e_steps):
+    e2e_steps = 1 if args.no_e2e else max(3, min(args.steps, 10))
+    for i in range(0 if args.no_e2e else e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         ta = time.perf_counter()
         e2e_p.seed = scenes.PHILOX_KEY_BASE + 200 + i
         rpr.update(scene, e2e_p, e2e_p.ir_rate_hz, lis_h, src_h, H_host=Hh, want=("H", "params"))
         e2e_total += time.perf_counter() - ta
-    e2e_value = work * e2e_steps / e2e_total * (ws if ws > 1 else 1)
+    e2e_value = work * e2e_steps / e2e_total * (ws if ws > 1 else 1) if e2e_total > 0 else None
     h2d = (S + 1) * 3 * 4
     d2h = Hh.nbytes + S * B * C_sizeof("rp_reverb_params")
 
@@ -319,7 +324,7 @@ def main():
         "kernel_share": shares,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": 1000 * e2e_total / e2e_steps},
+                "ms_per_step": 1000 * e2e_total / e2e_steps if e2e_total > 0 else None},
         "clocks": clocks,
     }
     if cpu:

@@ -170,6 +170,8 @@ typedef struct {
                                         [0] closest-hit segments, [1] shadow rays */
     uint64_t tri_tests[2];           /* with RP_FLAG_COUNT_VISITS: triangle tests, same split */
     uint64_t hits_stored;            /* reflections kept for next-event estimation */
+    uint64_t fp64_reruns;            /* queries whose FP32 answer was rounding-sensitive and
+                                        were decided again in FP64 */
     int32_t error;                   /* first RP_ERR_* raised by a kernel, or 0 */
     int32_t reserved;
 } rp_trace_stats;

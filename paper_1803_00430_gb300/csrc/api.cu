@@ -139,6 +139,7 @@ int reserve(rp_ctx *c, const Sizes &z)
     if ((r = ensure(c, c->rec_rid, z.rec_cap * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->rec_e, z.rec_cap * z.B * sizeof(float)))) return r;
     if ((r = ensure(c, c->perm, z.rec_cap * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->rerun, (z.rec_cap / 8 + 4096) * sizeof(unsigned long long)))) return r;
     if ((r = ensure(c, c->cnt, keys * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->cur, keys * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->off, (keys + 1) * sizeof(uint32_t)))) return r;
@@ -239,7 +240,7 @@ int rp_destroy(rp_ctx *c)
     if (!c) return RP_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    for (Buf *b : {&c->hit_p, &c->hit_plo, &c->hit_n, &c->hit_ws, &c->hit_rid, &c->rec_key, &c->rec_rid, &c->rec_e, &c->perm,
+    for (Buf *b : {&c->hit_p, &c->hit_plo, &c->hit_n, &c->hit_ws, &c->hit_rid, &c->rec_key, &c->rec_rid, &c->rec_e, &c->perm, &c->rerun,
                    &c->cnt, &c->off, &c->cur, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H, &c->direct,
                    &c->params, &c->state})
         free_buf(*b);
@@ -470,6 +471,8 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
     w.H = H;
     w.direct = direct;
     w.hits_per_chunk = z.chunk_hits;
+    w.rerun = (unsigned long long *)c->rerun.p;
+    w.rerun_cap = z.rec_cap / 8 + 4096;
     w.num_sms = c->num_sms;
 
     CK(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
@@ -505,10 +508,14 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
     const int acc_blocks = (int)std::max(1ll, std::min<long long>((nkeys + 7) / 8, (long long)c->num_sms * 8));
     for (unsigned long long ch = 0; ch < z.n_chunks && S > 0; ++ch) {
         if (ch > 0) CK(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(&w.ctr->next_item, 0, sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(&w.ctr->next_item, 0, 2 * sizeof(unsigned long long), st));  // + n_rerun
         if (p->max_order > 0) {
-            ProfScope ps(c, "shadow");
-            launch_shadow(w, ch, c->shadow_blocks, st);
+            {
+                ProfScope ps(c, "shadow");
+                launch_shadow(w, ch, c->shadow_blocks, st);
+            }
+            ProfScope ps(c, "shadow_exact");
+            launch_shadow_exact(w, ch, c->num_sms * 2, st);
         }
         CK(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nkeys, st));
         CK(cudaMemsetAsync(w.cur, 0, sizeof(uint32_t) * nkeys, st));

@@ -36,7 +36,7 @@ struct rp_ctx {
     int *d_status = nullptr;
     int paths_blocks = 0, shadow_blocks = 0;
     // workspace
-    Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, rec_key, rec_rid, rec_e, perm, cnt, off, cur, Hs, He, src, ctr,
+    Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, Hs, He, src, ctr,
         stats, H, direct, params, state;
     // profiling
     bool prof = false;

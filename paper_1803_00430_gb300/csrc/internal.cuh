@@ -48,7 +48,7 @@ struct TraceCounters {
     unsigned long long n_records;    // contribution records in the current chunk
     unsigned long long n_sphere;     // records written by the path kernel
     unsigned long long next_item;    // shadow work fetched in the current chunk
-    unsigned long long pad;
+    unsigned long long n_rerun;      // shadow items queued for an FP64 decision (current chunk)
 };
 
 // Contribution records: key = source * T + bin, ray id, e[B] (row of B floats).
@@ -121,12 +121,15 @@ struct TraceWork {
     float *H;        // output
     rp_direct *direct;
     unsigned long long hits_per_chunk;
+    unsigned long long *rerun;  // queue of rounding-sensitive shadow items
+    unsigned long long rerun_cap;
     int num_sms;
 };
 
 void launch_wave_setup(const TraceWork &w, int wave, cudaStream_t st);
 void launch_paths(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
+void launch_shadow_exact(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_direct(const TraceWork &w, cudaStream_t st);
 void launch_count(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_scan(const TraceWork &w, cudaStream_t st);

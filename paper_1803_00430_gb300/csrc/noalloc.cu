@@ -118,7 +118,7 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     const unsigned long long o_hs = cv.take<float>(cells), o_he = cv.take<float>(cells);
     if (cv.off >= RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
     // the rest holds contribution records: key, ray, energies, sort index
-    const unsigned long long per_rec = 4ull + 4ull + 4ull * B + 4ull + 16ull;  // + alignment slack
+    const unsigned long long per_rec = 4ull + 4ull + 4ull * B + 4ull + 1ull + 16ull;  // + FP64 queue, slack
     const unsigned long long rec_room = (RP_NOALLOC_SCRATCH_BYTES - cv.off) / per_rec;
     if (rec_room < sph_cap + s1) return RP_ERR_TOO_LARGE;
     const unsigned long long chunk_hits = std::max(1ull, std::min(hit_cap, (rec_room - sph_cap) / s1));
@@ -126,6 +126,8 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     const unsigned long long rec_cap = sph_cap + chunk_hits * s1;
     const unsigned long long o_rk = cv.take<uint32_t>(rec_cap), o_rr = cv.take<uint32_t>(rec_cap),
                              o_re = cv.take<float>(rec_cap * B), o_pm = cv.take<uint32_t>(rec_cap);
+    const unsigned long long rerun_cap = rec_cap / 8 + 4096;
+    const unsigned long long o_rq = cv.take<unsigned long long>(rerun_cap);
     if (cv.off > RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
 
     CKN(cudaSetDevice(c->device));
@@ -185,6 +187,8 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.H = H;
     w.direct = direct;
     w.hits_per_chunk = chunk_hits;
+    w.rerun = (unsigned long long *)(base + o_rq);
+    w.rerun_cap = rerun_cap;
     w.num_sms = c->num_sms;
 
     // what must start at zero: the counters and the statistics of this step
@@ -208,8 +212,11 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
         (int)std::max(1ll, std::min<long long>(((long long)keys + 7) / 8, (long long)c->num_sms * 8));
     for (unsigned long long ch = 0; ch < n_chunks && S > 0; ++ch) {
         if (ch > 0) CKN(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
-        CKN(cudaMemsetAsync(&w.ctr->next_item, 0, sizeof(unsigned long long), st));
-        if (M > 0) launch_shadow(w, ch, c->shadow_blocks, st);
+        CKN(cudaMemsetAsync(&w.ctr->next_item, 0, 2 * sizeof(unsigned long long), st));  // + n_rerun
+        if (M > 0) {
+            launch_shadow(w, ch, c->shadow_blocks, st);
+            launch_shadow_exact(w, ch, c->num_sms * 2, st);
+        }
         CKN(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * keys, st));
         CKN(cudaMemsetAsync(w.cur, 0, sizeof(uint32_t) * keys, st));
         launch_count(w, grid_flat, st);

@@ -27,6 +27,8 @@ constexpr int PATH_THREADS = 128;
 constexpr int SHADOW_THREADS = 128;
 // an FP32 arrival time within this many bins of a bin boundary is re-decided in FP64
 constexpr float BIN_GUARD = 2e-3f;
+// node visits a shadow-ray lane makes before the warp refills finished lanes
+constexpr int SHADOW_STEPS = 8;
 
 struct BlockAcc {
     double esc[MAXB], absb[MAXB], rem[MAXB], late[MAXB];
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
     const V3<R> lis = from4<R>(__ldg(w.src + S));  // the listener follows the S sources
 
     double mfp = 0.0, mfp_np = 0.0;
-    unsigned long long mc = 0, mcnp = 0, segs = 0, sphere = 0, contrib = 0;
+    unsigned long long mc = 0, mcnp = 0, segs = 0, sphere = 0, contrib = 0, reruns = 0;
     TravStats ts = {0u, 0u};
 
     // path state
@@ -293,6 +295,7 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
                 exact = true;
                 t_exact = (R)te;
                 tf = (float)te;
+                ++reruns;
             }
         } else {
             tri = traverse<false, COUNT, false>(sc, of, df, sc.tmin, INFINITY, prev, sstack + threadIdx.x, tf, ts,
@@ -444,9 +447,53 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
         }
     }
     acc_counters(acc, mfp, mfp_np, mc, mcnp, segs, 0ull, contrib, sphere, ts);
+    for (int o = 16; o > 0; o >>= 1) reruns += __shfl_xor_sync(FULL, reruns, o);
+    if (lane == 0 && reruns) atomicAdd((unsigned long long *)&w.stats->fp64_reruns, reruns);
     acc_flush(acc, w.stats, B, 0);
 }
 
+// Emit the contribution of a visible (reflection j, source s) pair: energy
+// w_b s_b cos(theta) / (pi d^2), arrival (L + d) / c.  An FP32 arrival time that
+// lands within BIN_GUARD of a bin boundary is re-decided in FP64 from the stored
+// residuals.
+__device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc &acc, unsigned long long j, int s,
+                                                    float f, float dist)
+{
+    const TraceConsts &k = w.k;
+    const int B = k.B, T = k.T;
+    const float4 P = w.hits.p[j];
+    float e[MAXB];
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) e[b] = b < B ? w.hits.ws[(unsigned long long)b * w.hits.cap + j] * f : 0.f;
+    float binf;
+    const float x = ((P.w + dist) / k.c) * k.rate;
+    if (fabsf(x - rintf(x)) < BIN_GUARD) {
+        const float4 lo = w.hits.plo[j];
+        const float4 cs = __ldg(w.src + s);
+        const double dx = (double)cs.x - ((double)P.x + (double)lo.x);
+        const double dy = (double)cs.y - ((double)P.y + (double)lo.y);
+        const double dz = (double)cs.z - ((double)P.z + (double)lo.z);
+        const double dd = sqrt(dx * dx + dy * dy + dz * dz);
+        const double tt = ((double)P.w + (double)lo.w + dd) / (double)k.c;
+        binf = (float)floor(tt * (double)k.rate);
+    } else {
+        binf = floorf(x);
+    }
+    if (binf < (float)T) {
+        emit_record(w, (uint32_t)s * (uint32_t)T + (uint32_t)binf, w.hits.rid[j], e, B);
+    } else {
+#pragma unroll
+        for (int b = 0; b < MAXB; ++b)
+            if (b < B) atomicAdd(&acc.late[b], (double)e[b]);
+    }
+}
+
+// Shadow rays of one chunk of stored reflections: items q = (reflection, source)
+// pairs, reflection-major.  Persistent threads with per-lane refill: each lane
+// advances its any-hit query SHADOW_STEPS nodes at a time; a lane whose query ends
+// takes the next item at once, so lanes of a warp do not idle behind its longest
+// ray.  Queries whose FP32 answer is rounding-sensitive are queued for the FP64
+// kernel below (EXACT); when the queue is full the FP32 answer stands.
 template <bool COUNT, bool EXACT>
 __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned long long chunk)
 {
@@ -457,84 +504,125 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
 
     const SceneView &sc = w.sc;
     const TraceConsts &k = w.k;
-    const int B = k.B, S = k.S, T = k.T;
+    const int S = k.S;
     const int lane = threadIdx.x & 31;
     const unsigned long long nh = min(w.ctr->n_hits, w.hits.cap);
     const unsigned long long j0 = chunk * w.hits_per_chunk;
     const unsigned long long j1 = min(j0 + w.hits_per_chunk, nh);
     const unsigned long long items = j1 > j0 ? (j1 - j0) * (unsigned long long)S : 0ull;
+    const int iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
     const float inv_pi = 1.0f / PI_F;
+    int lstack[LOCAL_STACK];
 
     unsigned long long shadow = 0, contrib = 0;
     TravStats ts = {0u, 0u};
+    bool busy = false, exhausted = items == 0;
+    unsigned long long item = 0;
+    AnyRay ray;
+    float3 dir = mk3(0.f, 0.f, 0.f);
+    AnyState st = {-1, 0, INFINITY, false, false};
+    int steps = 0;
+    float f = 0.f, dist = 0.f;
     while (true) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&w.ctr->next_item, 32ull);
-        base = __shfl_sync(FULL, base, 0);
-        if (base >= items) break;
-        const unsigned long long q = base + lane;
-        if (q < items) {
-            const unsigned long long jj = q / (unsigned long long)S;
-            const int s = (int)(q - jj * (unsigned long long)S);
-            const unsigned long long j = j0 + jj;
-            const float4 P = w.hits.p[j], N = w.hits.n[j];
-            const float3 p = xyz(P), n = xyz(N);
-            const float4 cs = __ldg(w.src + s);
-            const float3 v = xyz(cs) - p;
-            const float dist2 = dot(v, v);
-            const float dist = sqrtf(dist2);
-            const float cth = dot(n, v) / dist;
-            if (cth > 0.f) {
-                ++shadow;
-                const float3 dir = v * (1.0f / dist);
-                float tt;
-                bool amb = false;
-                int blk = traverse<true, COUNT, EXACT>(sc, p, dir, sc.tmin, dist, __float_as_int(N.w),
-                                                       sstack + threadIdx.x, tt, ts, w.status, &amb);
-                if (EXACT && amb) {
-                    // visibility may depend on rounding: decide it in FP64 from the stored residuals
-                    const float4 lo = w.hits.plo[j];
-                    const D3 pd = {(double)P.x + lo.x, (double)P.y + lo.y, (double)P.z + lo.z};
-                    const double vx = (double)cs.x - pd.x, vy = (double)cs.y - pd.y, vz = (double)cs.z - pd.z;
-                    const double dd = sqrt(vx * vx + vy * vy + vz * vz);
-                    double te;
-                    blk = traverse_exact<true>(sc, pd, D3{vx / dd, vy / dd, vz / dd}, sc.tmin_d, dd,
-                                               __float_as_int(N.w), sstack + threadIdx.x, te, w.status);
-                }
-                if (blk < 0) {
-                    ++contrib;
-                    const float f = cth * inv_pi / dist2;
-                    float e[MAXB];
-#pragma unroll
-                    for (int b = 0; b < MAXB; ++b)
-                        e[b] = b < B ? w.hits.ws[(unsigned long long)b * w.hits.cap + j] * f : 0.f;
-                    float binf;
-                    const float x = ((P.w + dist) / k.c) * k.rate;
-                    if (fabsf(x - rintf(x)) < BIN_GUARD) {
-                        // close to a bin boundary: decide in FP64 from the stored residuals
-                        const float4 lo = w.hits.plo[j];
-                        const double dx = (double)cs.x - ((double)P.x + (double)lo.x);
-                        const double dy = (double)cs.y - ((double)P.y + (double)lo.y);
-                        const double dz = (double)cs.z - ((double)P.z + (double)lo.z);
-                        const double dd = sqrt(dx * dx + dy * dy + dz * dz);
-                        const double tt = ((double)P.w + (double)lo.w + dd) / (double)k.c;
-                        binf = (float)floor(tt * (double)k.rate);
-                    } else {
-                        binf = floorf(x);
-                    }
-                    if (binf < (float)T) {
-                        emit_record(w, (uint32_t)s * (uint32_t)T + (uint32_t)binf, w.hits.rid[j], e, B);
-                    } else {
-#pragma unroll
-                        for (int b = 0; b < MAXB; ++b)
-                            if (b < B) atomicAdd(&acc.late[b], (double)e[b]);
+        const unsigned need = __ballot_sync(FULL, !busy && !exhausted);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&w.ctr->next_item, (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (!busy && !exhausted) {
+                const unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
+                if (my >= items) {
+                    exhausted = true;
+                } else {
+                    item = my;
+                    const unsigned long long jj = my / (unsigned long long)S;
+                    const int s = (int)(my - jj * (unsigned long long)S);
+                    const unsigned long long j = j0 + jj;
+                    const float4 P = w.hits.p[j], N = w.hits.n[j];
+                    const float3 p = xyz(P);
+                    const float3 v = xyz(__ldg(w.src + s)) - p;
+                    const float dist2 = dot(v, v);
+                    dist = sqrtf(dist2);
+                    const float cth = dot(xyz(N), v) / dist;
+                    if (cth > 0.f) {
+                        ++shadow;
+                        dir = v * (1.0f / dist);
+                        ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
+                        st = {0, 0, INFINITY, false, false};
+                        steps = 0;
+                        f = cth * inv_pi / dist2;
+                        busy = true;
                     }
                 }
             }
         }
+        if (__all_sync(FULL, !busy && exhausted)) break;
+        if (!busy) continue;
+        bool done = any_hit_steps<COUNT, EXACT>(sc, ray, dir, st, sstack + threadIdx.x, lstack, SHADOW_STEPS, ts,
+                                                 w.status);
+        steps += SHADOW_STEPS;
+        if (!done && steps > iter_cap) {
+            raise_error(w.status, RP_ERR_TIMEOUT);
+            done = true;
+        }
+        if (!done) continue;
+        busy = false;
+        const bool amb = EXACT && !st.clear && st.amb_t < INFINITY;
+        if (amb) {
+            const unsigned long long r = warp_append(&w.ctr->n_rerun);
+            if (r < w.rerun_cap) {
+                w.rerun[r] = item;
+                continue;
+            }
+        }
+        if (!st.blocked) {
+            const unsigned long long jj = item / (unsigned long long)S;
+            ++contrib;
+            shadow_contribution(w, acc, j0 + jj, (int)(item - jj * (unsigned long long)S), f, dist);
+        }
     }
     acc_counters(acc, 0.0, 0.0, 0ull, 0ull, 0ull, shadow, contrib, 0ull, ts);
-    acc_flush(acc, w.stats, B, 1);
+    acc_flush(acc, w.stats, k.B, 1);
+}
+
+// FP64 decisions for the shadow rays whose FP32 visibility was rounding-sensitive
+__global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_exact(TraceWork w, unsigned long long chunk)
+{
+    __shared__ int sstack[SMEM_STACK * SHADOW_THREADS];
+    __shared__ BlockAcc acc;
+    acc_init(acc);
+    __syncthreads();
+    const int S = w.k.S;
+    const unsigned long long n = min(w.ctr->n_rerun, w.rerun_cap);
+    const unsigned long long j0 = chunk * w.hits_per_chunk;
+    unsigned long long contrib = 0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long item = w.rerun[i];
+        const unsigned long long jj = item / (unsigned long long)S;
+        const int s = (int)(item - jj * (unsigned long long)S);
+        const unsigned long long j = j0 + jj;
+        const float4 P = w.hits.p[j], N = w.hits.n[j], lo = w.hits.plo[j];
+        const float4 cs = __ldg(w.src + s);
+        const D3 pd = {(double)P.x + lo.x, (double)P.y + lo.y, (double)P.z + lo.z};
+        const double vx = (double)cs.x - pd.x, vy = (double)cs.y - pd.y, vz = (double)cs.z - pd.z;
+        const double dd = sqrt(vx * vx + vy * vy + vz * vz);
+        double te;
+        const int blk = traverse_exact<true>(w.sc, pd, D3{vx / dd, vy / dd, vz / dd}, w.sc.tmin_d, dd,
+                                             __float_as_int(N.w), sstack + threadIdx.x, te, w.status);
+        if (blk < 0) {
+            const float3 v = xyz(cs) - xyz(P);
+            const float dist2 = dot(v, v), dist = sqrtf(dist2);
+            const float cth = dot(xyz(N), v) / dist;
+            ++contrib;
+            shadow_contribution(w, acc, j, s, cth * (1.0f / PI_F) / dist2, dist);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd((unsigned long long *)&w.stats->fp64_reruns, n);
+    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(FULL, contrib, o);
+    if ((threadIdx.x & 31) == 0 && contrib) atomicAdd(&acc.contrib, contrib);
+    acc_flush(acc, w.stats, w.k.B, 1);
 }
 
 __global__ void __launch_bounds__(128) k_direct(TraceWork w)
@@ -601,6 +689,11 @@ void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cud
     else if (count) k_shadow<true, false><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
     else if (exact) k_shadow<false, true><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
     else k_shadow<false, false><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+}
+
+void launch_shadow_exact(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
+{
+    if ((w.k.flags & RP_FLAG_FP32_PATHS) == 0) k_shadow_exact<<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
 }
 
 void launch_direct(const TraceWork &w, cudaStream_t st)

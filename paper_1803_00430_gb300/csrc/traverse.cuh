@@ -272,3 +272,133 @@ __device__ __noinline__ int traverse_exact(const SceneView &sc, D3 o, D3 d, doub
 }
 
 }  // namespace rp
+
+namespace rp {
+
+// ---------------------------------------------------------------------------
+// Resumable any-hit query: the traversal state lives in registers and the
+// caller's stack columns between calls, so that a warp can advance each lane's
+// query a few nodes at a time and give a finished lane a new ray immediately
+// (persistent threads with per-lane refill).  Same decisions as
+// traverse<true, COUNT, FLAG>.
+// ---------------------------------------------------------------------------
+struct AnyRay {
+    float3 o, idir, ood;
+    float tmin, tmax;
+    int exclude;
+};
+
+struct AnyState {
+    int node;      // next node to visit, -1 when the stack is empty
+    int sp;        // stack depth
+    float amb_t;   // nearest rounding-sensitive triangle distance
+    bool blocked;  // a blocker was found
+    bool clear;    // ... and its test was not rounding-sensitive
+};
+
+__device__ __forceinline__ AnyRay make_any_ray(float3 o, float3 d, float tmin, float tmax, int exclude)
+{
+    AnyRay r;
+    const float ex = fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x);
+    const float ey = fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y);
+    const float ez = fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z);
+    r.o = o;
+    r.idir = mk3(1.0f / ex, 1.0f / ey, 1.0f / ez);
+    r.ood = mk3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
+    r.tmin = tmin;
+    r.tmax = tmax;
+    r.exclude = exclude;
+    return r;
+}
+
+// advance the query by at most `budget` node visits; returns true when it is done
+template <bool COUNT, bool FLAG>
+__device__ __forceinline__ bool any_hit_steps(const SceneView &sc, const AnyRay &r, float3 d, AnyState &q,
+                                              int *__restrict__ sstack, int *lstack, int budget, TravStats &ts,
+                                              int *status)
+{
+    const int stride = blockDim.x;
+    const float tlo = r.tmin * (1.0f - AMBIG_T), tnear = r.tmin * (1.0f + AMBIG_T);
+    auto leaf = [&](int tri) -> bool {  // true: query finished
+        if (COUNT) ts.tris++;
+        if ((unsigned)tri >= (unsigned)sc.num_tris) {
+            raise_error(status, RP_ERR_INVALID_ARG);
+            return true;
+        }
+        if (tri == r.exclude) return false;
+        float t, margin;
+        uint32_t orig;
+        const bool inside = tri_intersect(sc.tris, tri, r.o, d, t, orig, margin);
+        if (FLAG && t > tlo && t < r.tmax * (1.0f + AMBIG_T) &&
+            (fabsf(margin) < AMBIG_BARY || (inside && t < tnear)))
+            q.amb_t = fminf(q.amb_t, t);
+        if (!inside || !(t > r.tmin) || !(t < r.tmax)) return false;
+        q.blocked = true;
+        if (!FLAG || (fabsf(margin) >= AMBIG_BARY && t >= tnear)) {
+            q.clear = true;
+            return true;
+        }
+        return false;
+    };
+    if (sc.num_nodes == 0) {
+        if (sc.num_tris > 0) leaf(0);
+        return true;
+    }
+    for (int it = 0; it < budget; ++it) {
+        if (q.node < 0) return true;
+        if (COUNT) ts.nodes++;
+        if ((unsigned)q.node >= (unsigned)sc.num_nodes) {
+            raise_error(status, RP_ERR_INVALID_ARG);
+            return true;
+        }
+        const float4 *np = sc.nodes + 4 * q.node;
+        const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+        const float a0 = n0.x * r.idir.x - r.ood.x, b0 = n0.y * r.idir.x - r.ood.x;
+        const float a1 = n0.z * r.idir.y - r.ood.y, b1 = n0.w * r.idir.y - r.ood.y;
+        const float a2 = n2.x * r.idir.z - r.ood.z, b2 = n2.y * r.idir.z - r.ood.z;
+        const float c0min = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), r.tmin));
+        const float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), r.tmax));
+        const float a3 = n1.x * r.idir.x - r.ood.x, b3 = n1.y * r.idir.x - r.ood.x;
+        const float a4 = n1.z * r.idir.y - r.ood.y, b4 = n1.w * r.idir.y - r.ood.y;
+        const float a5 = n2.z * r.idir.z - r.ood.z, b5 = n2.w * r.idir.z - r.ood.z;
+        const float c1min = fmaxf(fmaxf(fminf(a3, b3), fminf(a4, b4)), fmaxf(fminf(a5, b5), r.tmin));
+        const float c1max = fminf(fminf(fmaxf(a3, b3), fmaxf(a4, b4)), fminf(fmaxf(a5, b5), r.tmax));
+        bool h0 = c0min <= c0max, h1 = c1min <= c1max;
+        const int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
+        if (h0 && ch0 < 0) {
+            if (leaf(~ch0)) return true;
+            h0 = false;
+        }
+        if (h1 && ch1 < 0) {
+            if (leaf(~ch1)) return true;
+            h1 = false;
+        }
+        if (h0 && h1) {
+            const bool swap = c1min < c0min;
+            const int nearc = swap ? ch1 : ch0, farc = swap ? ch0 : ch1;
+            if (q.sp < SMEM_STACK) {
+                sstack[q.sp * stride] = farc;
+            } else if (q.sp < STACK_DEPTH) {
+                lstack[q.sp - SMEM_STACK] = farc;
+            } else {
+                raise_error(status, RP_ERR_STACK_OVERFLOW);
+                return true;
+            }
+            ++q.sp;
+            q.node = nearc;
+        } else if (h0) {
+            q.node = ch0;
+        } else if (h1) {
+            q.node = ch1;
+        } else if (q.sp == 0) {
+            q.node = -1;
+            return true;
+        } else {
+            --q.sp;
+            q.node = q.sp < SMEM_STACK ? sstack[q.sp * stride] : lstack[q.sp - SMEM_STACK];
+        }
+    }
+    return q.node < 0;
+}
+
+}  // namespace rp
