@@ -263,6 +263,77 @@ int rp_update(rp_scene *scene, const rp_trace_params *params,
               int32_t num_sources, float *H_host, rp_reverb_params *params_host,
               rp_direct *direct_host, rp_trace_stats *stats_host, double *state_host);
 
+/* ---------------------------------------------------------------------------
+ * Batched updates: many independent scenes, each with its own sources, listener and
+ * ray budget, traced in the same persistent launches and estimated together; the
+ * whole update can be captured once in a CUDA graph and replayed per update.
+ * --------------------------------------------------------------------------- */
+typedef struct rp_batch rp_batch;
+
+typedef struct {
+    rp_scene *scene;        /* created on the batch's context; same band count for all items */
+    const float *listener;  /* host float[3] */
+    const float *sources;   /* host float[num_sources][3] */
+    int32_t num_sources;
+    uint32_t scene_id;      /* Philox counter word 1 of this item */
+    uint64_t num_rays;
+    uint64_t first_ray;
+} rp_batch_item;
+
+/* Launch shape of a batch, chosen by rp_batch_autotune or set by hand. */
+typedef struct {
+    int32_t chunk_rays;            /* primaries per work chunk of the paths kernel, 32..65536 */
+    int32_t shadow_steps;          /* BVH nodes a shadow-ray lane visits between refills, 1..64 */
+    int32_t paths_blocks_per_sm;   /* persistent grid of the paths kernel, 1..occupancy */
+    int32_t shadow_blocks_per_sm;  /* persistent grid of the shadow-ray kernel, 1..occupancy */
+} rp_batch_tuning;
+
+typedef struct {
+    int32_t num_items;
+    int32_t total_sources;
+    int32_t num_groups;                  /* steps the update is split into (memory budget) */
+    int32_t reserved;
+    uint64_t total_rays;
+    uint64_t max_group_reflections;
+} rp_batch_info;
+
+/* Create a batch of num_items items sharing `params` (max_order, sh_order, num_bins,
+ * min_order, ir_rate_hz, speed_of_sound, source_radius, flags; num_rays, first_ray,
+ * scene_id and seed are per item / per run; budget_refill, RP_FLAG_RAY_HASH and
+ * RP_FLAG_DEVICE_POSITIONS are rejected).  Item i's sources take global indices
+ * sum_{i'<i} num_sources(i') ... in the outputs, all device memory owned by the caller:
+ *   H       float[total sources][B][K][T], each item normalised by its own primaries
+ *   direct  rp_direct[total sources]
+ *   params  rp_reverb_params[total sources][B] or NULL (no estimation); est must be set
+ *   stats   rp_trace_stats (aggregate over the batch) or NULL
+ * Positions are copied at creation.  Workspace is reserved here; later calls on the
+ * context that grow it make the next graph run re-capture.  Items are traced in
+ * groups whose stored reflections fit 2^27 slots (about 11 GB at 8 bands); the
+ * environment variable RP_BATCH_HIT_BUDGET can lower that budget. */
+int rp_batch_create(rp_ctx *ctx, const rp_batch_item *items, int32_t num_items,
+                    const rp_trace_params *params, const rp_estimate_params *est, float *H,
+                    rp_direct *direct, rp_reverb_params *params_out, rp_trace_stats *stats,
+                    rp_batch **out);
+int rp_batch_destroy(rp_batch *batch);
+
+/* Enqueue one batched update with Philox key `seed`.  use_graph = 1 captures the
+ * launch sequence into a CUDA graph on first use (or after a tuning or workspace
+ * change) and replays it; the key is read from device memory, so replays take new
+ * keys.  Asynchronous: rp_sync_status(ctx) waits and reports device errors. */
+int rp_batch_run(rp_batch *batch, uint64_t seed, int use_graph);
+
+int rp_batch_set_tuning(rp_batch *batch, const rp_batch_tuning *tuning);
+int rp_batch_get_tuning(const rp_batch *batch, rp_batch_tuning *tuning);
+int rp_batch_info_get(const rp_batch *batch, rp_batch_info *out);
+
+/* Time launch shapes on this batch (coordinate descent over shadow_steps {4,8,16},
+ * chunk_rays {64,256,1024} and full or half persistent grids, two runs each) and
+ * apply the fastest.  cache_path (or NULL) is a text file of
+ * "key chunk steps paths_blocks shadow_blocks ms" lines keyed by device, SM count
+ * and batch shape; a cached entry is applied without timing. */
+int rp_batch_autotune(rp_batch *batch, uint64_t seed, const char *cache_path,
+                      rp_batch_tuning *best, double *best_ms);
+
 /* Size of the fixed device scratch array used by rp_trace_noalloc: 64 MiB, held by
  * every GPU that loads the library for the life of the process. */
 #define RP_NOALLOC_SCRATCH_BYTES (64ull << 20)

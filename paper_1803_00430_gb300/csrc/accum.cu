@@ -89,8 +89,12 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first)
     const int S = w.k.S, B = w.k.B, K = w.k.K, T = w.k.T, BK = B * K;
     const long long nkeys = (long long)S * T;
     const long long nwarps = (long long)gridDim.x * ACC_WARPS;
+    const unsigned long long seed = w.seed ? w.seed[0] : w.seed_val;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
     for (long long key = (long long)blockIdx.x * ACC_WARPS + wp; key < nkeys; key += nwarps) {
         const uint32_t begin = w.off[key], end = w.off[key + 1];
+        const int gs = w.src_base + (int)(key / T);
+        const uint32_t scene_id = w.njobs > 1 ? w.jobs[w.src_job[gs]].scene_id : w.job0.scene_id;
         float sum[ACC_SLOTS], err[ACC_SLOTS];
 #pragma unroll
         for (int i = 0; i < ACC_SLOTS; ++i) sum[i] = err[i] = 0.f;
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first)
 #pragma unroll
                 for (int b = 0; b < MAXB; ++b)
                     if (b < B) se[wp][lane][b] = e[b];
-                const float3 d0 = primary_direction(rid, w.k.scene_id, w.k.key0, w.k.key1);
+                const float3 d0 = primary_direction(rid, scene_id, key0, key1);
                 float Y[MAXK];
                 sh_eval(w.k.sh_order, d0.x, d0.y, d0.z, Y);
 #pragma unroll
@@ -147,18 +151,21 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first)
     }
 }
 
-// H = (sum + error) / K_primaries; late energy likewise; then direct sound binned
-// into H when min_order == 0
+// H = (sum + error) / K_primaries of the source's job; late energy likewise (one
+// job); then direct sound binned into H when min_order == 0
 __global__ void k_finalize(TraceWork w)
 {
-    const unsigned long long n = (unsigned long long)w.k.S * w.k.B * w.k.K * w.k.T;
-    const unsigned long long kp = w.stats->primaries;
-    const float inv = kp > 0 ? 1.0f / (float)kp : 0.f;
+    const unsigned long long per_src = (unsigned long long)w.k.B * w.k.K * w.k.T;
+    const unsigned long long n = (unsigned long long)w.k.S * per_src;
+    float *Hg = w.H + (unsigned long long)w.src_base * per_src;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        w.H[i] = kp > 0 ? (w.Hs[i] + w.He[i]) / (float)kp : 0.f;
-    (void)inv;
-    if (blockIdx.x == 0 && threadIdx.x < w.k.B && kp > 0) w.stats->late[threadIdx.x] /= (double)kp;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int gs = w.src_base + (int)(i / per_src);
+        const unsigned long long kp = w.njobs > 1 ? w.js[w.src_job[gs]].primaries : w.js[0].primaries;
+        Hg[i] = kp > 0 ? (w.Hs[i] + w.He[i]) / (float)kp : 0.f;
+    }
+    if (w.njobs == 1 && blockIdx.x == 0 && threadIdx.x < w.k.B && w.js[0].primaries > 0)
+        w.stats->late[threadIdx.x] /= (double)w.js[0].primaries;
 }
 
 __global__ void k_direct_add(TraceWork w)
@@ -166,11 +173,11 @@ __global__ void k_direct_add(TraceWork w)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int S = w.k.S, B = w.k.B, K = w.k.K, T = w.k.T;
     if (i >= S * B * K) return;
-    const int s = i / (B * K), r = i - s * B * K, b = r / K, kk = r - b * K;
-    const rp_direct dd = w.direct[s];
+    const int s = i / (B * K), r = i - s * B * K, kk = r - (r / K) * K;
+    const int gs = w.src_base + s;
+    const rp_direct dd = w.direct[gs];
     if (!dd.visible || dd.bin < 0 || dd.bin >= T) return;
-    (void)b;
-    w.H[(unsigned long long)i * T + dd.bin] += dd.sh[kk];
+    w.H[((unsigned long long)w.src_base * B * K + i) * T + dd.bin] += dd.sh[kk];
 }
 
 }  // namespace

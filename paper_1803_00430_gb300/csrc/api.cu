@@ -42,6 +42,7 @@ int ensure(rp_ctx *c, Buf &b, size_t bytes)
     b.bytes = 0;
     CK(cudaMalloc(&b.p, bytes));
     b.bytes = bytes;
+    c->ws_gen++;
     return RP_OK;
 }
 
@@ -102,53 +103,103 @@ void prof_collect(rp_ctx *c)
     c->pending.clear();
 }
 
-struct Sizes {
-    unsigned long long hit_cap, sph_cap, rec_cap, chunk_hits, n_chunks;
-    int S, B, K, T;
-};
-
-Sizes trace_sizes(const rp_scene *sc, const rp_trace_params *p, int S)
+StepSizes trace_sizes(const rp_scene *sc, const rp_trace_params *p, int S)
 {
-    Sizes z;
-    z.S = S;
-    z.B = sc->B;
-    z.K = (p->sh_order + 1) * (p->sh_order + 1);
-    z.T = p->num_bins;
-    const unsigned long long nm = p->num_rays * (unsigned long long)std::max(p->max_order, 0);
-    z.hit_cap = std::max(1ull, nm);
-    z.sph_cap = z.hit_cap / 2 + 4096;
-    const unsigned long long s = (unsigned long long)std::max(S, 1);
-    const unsigned long long room = REC_BUDGET > z.sph_cap ? REC_BUDGET - z.sph_cap : 1ull << 20;
-    z.chunk_hits = std::max(1ull, std::min(z.hit_cap, room / s));
-    z.n_chunks = (z.hit_cap + z.chunk_hits - 1) / z.chunk_hits;
-    z.rec_cap = z.sph_cap + z.chunk_hits * s;
-    return z;
+    const unsigned long long rays = p->num_rays;
+    const int K = (p->sh_order + 1) * (p->sh_order + 1);
+    return step_sizes(&rays, &S, 1, p->max_order, sc->B, K, p->num_bins, REC_BUDGET);
 }
 
-int reserve(rp_ctx *c, const Sizes &z)
+// make the context workspace hold a group of these sizes with `njobs` jobs
+int reserve(rp_ctx *c, const StepSizes &z, int B, int njobs, int total_sources, int nchunks)
 {
     int r;
-    const size_t keys = (size_t)z.S * z.T;
-    const size_t cells = (size_t)z.S * z.B * z.K * z.T;
     if ((r = ensure(c, c->hit_p, z.hit_cap * sizeof(float4)))) return r;
     if ((r = ensure(c, c->hit_plo, z.hit_cap * sizeof(float4)))) return r;
     if ((r = ensure(c, c->hit_n, z.hit_cap * sizeof(float4)))) return r;
-    if ((r = ensure(c, c->hit_ws, z.hit_cap * z.B * sizeof(float)))) return r;
+    if ((r = ensure(c, c->hit_ws, z.hit_cap * B * sizeof(float)))) return r;
     if ((r = ensure(c, c->hit_rid, z.hit_cap * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->rec_key, z.rec_cap * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->rec_rid, z.rec_cap * sizeof(uint32_t)))) return r;
-    if ((r = ensure(c, c->rec_e, z.rec_cap * z.B * sizeof(float)))) return r;
+    if ((r = ensure(c, c->rec_e, z.rec_cap * B * sizeof(float)))) return r;
     if ((r = ensure(c, c->perm, z.rec_cap * sizeof(uint32_t)))) return r;
-    if ((r = ensure(c, c->rerun, (z.rec_cap / 8 + 4096) * sizeof(unsigned long long)))) return r;
-    if ((r = ensure(c, c->cnt, keys * sizeof(uint32_t)))) return r;
-    if ((r = ensure(c, c->cur, keys * sizeof(uint32_t)))) return r;
-    if ((r = ensure(c, c->off, (keys + 1) * sizeof(uint32_t)))) return r;
-    if ((r = ensure(c, c->Hs, cells * sizeof(float)))) return r;
-    if ((r = ensure(c, c->He, cells * sizeof(float)))) return r;
-    if ((r = ensure(c, c->src, (z.S + 1) * sizeof(float4)))) return r;
+    if ((r = ensure(c, c->rerun, z.rerun_cap * sizeof(unsigned long long)))) return r;
+    if ((r = ensure(c, c->cnt, z.keys * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->cur, z.keys * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->off, (z.keys + 1) * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->Hs, z.cells * sizeof(float)))) return r;
+    if ((r = ensure(c, c->He, z.cells * sizeof(float)))) return r;
+    if ((r = ensure(c, c->src, (size_t)(total_sources + njobs) * sizeof(float4)))) return r;
+    if ((r = ensure(c, c->src_job, (size_t)std::max(total_sources, 1) * sizeof(int)))) return r;
+    if ((r = ensure(c, c->jobs, (size_t)njobs * sizeof(SceneJob)))) return r;
+    if ((r = ensure(c, c->js, (size_t)njobs * sizeof(JobState)))) return r;
+    if ((r = ensure(c, c->chunks, (size_t)std::max(nchunks, 1) * sizeof(RayChunk)))) return r;
     if ((r = ensure(c, c->ctr, sizeof(TraceCounters)))) return r;
     if ((r = ensure(c, c->stats, sizeof(rp_trace_stats)))) return r;
     return RP_OK;
+}
+
+// bind the context workspace into a TraceWork for a group of these sizes
+void bind_workspace(rp_ctx *c, const StepSizes &z, TraceWork &w)
+{
+    w.ctr = (TraceCounters *)c->ctr.p;
+    w.hits = {(float4 *)c->hit_p.p, (float4 *)c->hit_plo.p, (float4 *)c->hit_n.p, (float *)c->hit_ws.p,
+              (uint32_t *)c->hit_rid.p, z.hit_cap};
+    w.rec = {(uint32_t *)c->rec_key.p, (uint32_t *)c->rec_rid.p, (float *)c->rec_e.p, z.rec_cap};
+    w.stats = (rp_trace_stats *)c->stats.p;
+    w.status = c->d_status;
+    w.cnt = (uint32_t *)c->cnt.p;
+    w.off = (uint32_t *)c->off.p;
+    w.cur = (uint32_t *)c->cur.p;
+    w.perm = (uint32_t *)c->perm.p;
+    w.Hs = (float *)c->Hs.p;
+    w.He = (float *)c->He.p;
+    w.items_per_chunk = z.items_per_chunk;
+    w.rerun = (unsigned long long *)c->rerun.p;
+    w.rerun_cap = z.rerun_cap;
+    w.num_sms = c->num_sms;
+    w.jobs = (const SceneJob *)c->jobs.p;
+    w.js = (JobState *)c->js.p;
+    w.chunks = (const RayChunk *)c->chunks.p;
+    w.src_job = (const int *)c->src_job.p;
+    w.pos = (const float4 *)c->src.p;
+}
+
+void fill_consts(const rp_scene *sc, const rp_trace_params *p, int S, TraceWork &w)
+{
+    w.k.S = S;
+    w.k.B = sc->B;
+    w.k.K = (p->sh_order + 1) * (p->sh_order + 1);
+    w.k.T = p->num_bins;
+    w.k.M = p->max_order;
+    w.k.min_order = p->min_order;
+    w.k.sh_order = p->sh_order;
+    w.k.rate = p->ir_rate_hz;
+    w.k.c = p->speed_of_sound;
+    w.k.rs = p->source_radius;
+    w.k.flags = p->flags;
+}
+
+SceneView scene_view(const rp_scene *sc)
+{
+    return {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris, sc->num_nodes,
+            sc->B, sc->tmin, sc->tmin_d};
+}
+
+void prof_hook(void *ctx, const char *name, int begin)
+{
+    rp_ctx *c = (rp_ctx *)ctx;
+    if (!c->prof) return;
+    cudaEvent_t e = get_event(c);
+    cudaEventRecord(e, c->stream);
+    if (begin) {
+        c->open_events.push_back({name, e, nullptr});
+    } else if (!c->open_events.empty()) {
+        ProfPair pp = c->open_events.back();
+        c->open_events.pop_back();
+        pp.b = e;
+        c->pending.push_back(pp);
+    }
 }
 
 int check_params(const rp_scene *sc, const rp_trace_params *p, int S)
@@ -177,11 +228,6 @@ __global__ void k_pack_positions(const float *lis, const float *src, int S, floa
     out[i] = make_float4(x, y, z, 0.f);
 }
 
-__global__ void k_copy_status(const int *status, const TraceCounters *ctr, rp_trace_stats *st)
-{
-    st->error = *status;
-    st->hits_stored = ctr->n_hits;
-}
 
 }  // namespace
 
@@ -224,6 +270,7 @@ int rp_create(rp_ctx **out, int device, void *cuda_stream)
     }
     cudaMemset(c->d_status, 0, sizeof(int));
     c->paths_blocks = c->num_sms * paths_occupancy(0);
+    c->shadow_steps = 8;
     c->shadow_blocks = c->num_sms * shadow_occupancy(0);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -242,7 +289,7 @@ int rp_destroy(rp_ctx *c)
     cudaStreamSynchronize(c->stream);
     for (Buf *b : {&c->hit_p, &c->hit_plo, &c->hit_n, &c->hit_ws, &c->hit_rid, &c->rec_key, &c->rec_rid, &c->rec_e, &c->perm, &c->rerun,
                    &c->cnt, &c->off, &c->cur, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H, &c->direct,
-                   &c->params, &c->state})
+                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job})
         free_buf(*b);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
@@ -404,7 +451,7 @@ int rp_trace_reserve(rp_scene *sc, const rp_trace_params *p, int32_t S)
     int rc = check_params(sc, p, S);
     if (rc) return rc;
     CK(cudaSetDevice(sc->ctx->device));
-    return reserve(sc->ctx, trace_sizes(sc, p, S));
+    return reserve(sc->ctx, trace_sizes(sc, p, S), sc->B, 1, S, 1);
 }
 
 int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, const float *sources, int32_t S,
@@ -415,10 +462,13 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
     if (!listener || (S > 0 && !sources) || (!H && S > 0)) return RP_ERR_INVALID_ARG;
     rp_ctx *c = sc->ctx;
     CK(cudaSetDevice(c->device));
-    const Sizes z = trace_sizes(sc, p, S);
-    if ((rc = reserve(c, z))) return rc;
+    const StepSizes z = trace_sizes(sc, p, S);
+    if ((rc = reserve(c, z, sc->B, 1, S, 1))) return rc;
     cudaStream_t st = c->stream;
 
+    TraceWork w;
+    bind_workspace(c, z, w);
+    fill_consts(sc, p, S, w);
     // positions: sources then the listener, packed as float4 on the device
     float4 *dsrc = (float4 *)c->src.p;
     if (p->flags & RP_FLAG_DEVICE_POSITIONS) {
@@ -434,117 +484,41 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
         // from pageable memory the copy is staged before the call returns
         CK(cudaMemcpyAsync(dsrc, hp.data(), sizeof(float4) * (S + 1), cudaMemcpyHostToDevice, st));
     }
-
-    TraceWork w;
-    w.sc = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris, sc->num_nodes,
-            sc->B, sc->tmin, sc->tmin_d};
-    w.k.S = S;
-    w.k.B = sc->B;
-    w.k.K = z.K;
-    w.k.T = z.T;
-    w.k.M = p->max_order;
-    w.k.min_order = p->min_order;
-    w.k.sh_order = p->sh_order;
-    w.k.rate = p->ir_rate_hz;
-    w.k.c = p->speed_of_sound;
-    w.k.rs = p->source_radius;
-    w.k.scene_id = p->scene_id;
-    w.k.key0 = (uint32_t)p->seed;
-    w.k.key1 = (uint32_t)(p->seed >> 32);
-    w.k.num_rays = p->num_rays;
-    w.k.first_ray = p->first_ray;
-    w.k.flags = p->flags;
-    w.src = dsrc;
-    w.ctr = (TraceCounters *)c->ctr.p;
-    w.hits = {(float4 *)c->hit_p.p, (float4 *)c->hit_plo.p, (float4 *)c->hit_n.p, (float *)c->hit_ws.p, (uint32_t *)c->hit_rid.p,
-              z.hit_cap};
-    w.rec = {(uint32_t *)c->rec_key.p, (uint32_t *)c->rec_rid.p, (float *)c->rec_e.p, z.rec_cap};
-    w.stats = (rp_trace_stats *)c->stats.p;
+    SceneJob job;
+    job.sc = scene_view(sc);
+    job.first_ray = p->first_ray;
+    job.num_rays = p->num_rays;
+    job.hit_off = 0;
+    job.hit_cap = z.hit_cap;
+    job.scene_id = p->scene_id;
+    job.S = S;
+    job.src_off = 0;
+    job.lis = S;
+    CK(cudaMemcpyAsync(c->jobs.p, &job, sizeof(SceneJob), cudaMemcpyHostToDevice, st));
+    w.job0 = job;
+    w.njobs = 1;
+    w.wave_mode = 1;
+    w.nchunks = 0;
+    w.chunk_rays = 1;
+    w.src_base = 0;
+    w.seed = nullptr;
+    w.seed_val = p->seed;
     w.ray_hash = (p->flags & RP_FLAG_RAY_HASH) ? ray_hash : nullptr;
-    w.status = c->d_status;
-    w.cnt = (uint32_t *)c->cnt.p;
-    w.off = (uint32_t *)c->off.p;
-    w.cur = (uint32_t *)c->cur.p;
-    w.perm = (uint32_t *)c->perm.p;
-    w.Hs = (float *)c->Hs.p;
-    w.He = (float *)c->He.p;
     w.H = H;
     w.direct = direct;
-    w.hits_per_chunk = z.chunk_hits;
-    w.rerun = (unsigned long long *)c->rerun.p;
-    w.rerun_cap = z.rec_cap / 8 + 4096;
-    w.num_sms = c->num_sms;
+    w.shadow_steps = c->shadow_steps;
 
-    CK(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
-    CK(cudaMemsetAsync(w.stats, 0, sizeof(rp_trace_stats), st));
-    {
-        ProfScope ps(c, "wave_setup");
-        launch_wave_setup(w, 0, st);
-    }
-    if (p->max_order > 0) {
-        ProfScope ps(c, "paths");
-        launch_paths(w, c->paths_blocks, st);
-    }
-    if (p->budget_refill && p->max_order > 0) {
-        for (int wave = 1; wave < 4096; ++wave) {
-            {
-                ProfScope ps(c, "wave_setup");
-                launch_wave_setup(w, wave, st);
-            }
-            unsigned long long cnt = 0;
-            CK(cudaMemcpyAsync(&cnt, &w.ctr->wave_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (cnt == 0) break;
-            ProfScope ps(c, "paths");
-            launch_paths(w, c->paths_blocks, st);
-        }
-    }
-    {
-        ProfScope ps(c, "direct");
-        launch_direct(w, st);
-    }
-    const int grid_flat = c->num_sms * 8;
-    const long long nkeys = (long long)S * z.T;
-    const int acc_blocks = (int)std::max(1ll, std::min<long long>((nkeys + 7) / 8, (long long)c->num_sms * 8));
-    for (unsigned long long ch = 0; ch < z.n_chunks && S > 0; ++ch) {
-        if (ch > 0) CK(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
-        CK(cudaMemsetAsync(&w.ctr->next_item, 0, 2 * sizeof(unsigned long long), st));  // + n_rerun
-        if (p->max_order > 0) {
-            {
-                ProfScope ps(c, "shadow");
-                launch_shadow(w, ch, c->shadow_blocks, st);
-            }
-            ProfScope ps(c, "shadow_exact");
-            launch_shadow_exact(w, ch, c->num_sms * 2, st);
-        }
-        CK(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nkeys, st));
-        CK(cudaMemsetAsync(w.cur, 0, sizeof(uint32_t) * nkeys, st));
-        {
-            ProfScope ps(c, "count");
-            launch_count(w, grid_flat, st);
-        }
-        {
-            ProfScope ps(c, "scan");
-            launch_scan(w, st);
-        }
-        {
-            ProfScope ps(c, "scatter");
-            launch_scatter(w, grid_flat, st);
-        }
-        {
-            ProfScope ps(c, "accum");
-            launch_accum(w, ch == 0 ? 1 : 0, acc_blocks, st);
-        }
-    }
-    if (S > 0) {
-        ProfScope ps(c, "finalize");
-        launch_finalize(w, st);
-    }
-    {
-        ProfScope ps(c, "copy_status");
-        k_copy_status<<<1, 1, 0, st>>>(c->d_status, w.ctr, w.stats);
-    }
-    CK(cudaGetLastError());
+    StepLaunch L;
+    L.w = w;
+    L.n_rec_chunks = z.n_chunks;
+    L.refill = p->budget_refill;
+    L.reset_stats = 1;
+    L.paths_blocks = c->paths_blocks;
+    L.shadow_blocks = c->shadow_blocks;
+    L.exact_blocks = c->num_sms * 2;
+    L.flat_blocks = c->num_sms * 8;
+    L.acc_blocks = (int)std::max(1ll, std::min<long long>(((long long)z.keys + 7) / 8, (long long)c->num_sms * 8));
+    CK(enqueue_step(L, st, prof_hook, c));
     if (stats) CK(cudaMemcpyAsync(stats, w.stats, sizeof(rp_trace_stats), cudaMemcpyDeviceToDevice, st));
     return RP_OK;
 }

@@ -35,12 +35,15 @@ struct rp_ctx {
     int num_sms = 0;
     int *d_status = nullptr;
     int paths_blocks = 0, shadow_blocks = 0;
+    int shadow_steps = 8;
+    unsigned long long ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
     // workspace
     Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, Hs, He, src, ctr,
-        stats, H, direct, params, state;
+        stats, H, direct, params, state, jobs, js, chunks, src_job;
     // profiling
     bool prof = false;
     std::vector<ProfPair> pending;
+    std::vector<ProfPair> open_events;
     std::vector<cudaEvent_t> free_events;
     std::map<std::string, std::pair<unsigned long long, double>> totals;
 };

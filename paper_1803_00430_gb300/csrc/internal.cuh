@@ -2,6 +2,7 @@
 // translation units (not part of the public ABI).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -39,19 +40,53 @@ struct SceneView {
     double tmin_d;  // the same guard for FP64 re-decisions
 };
 
-// Counters and accumulators of one trace step (device memory, zeroed per step).
-struct TraceCounters {
-    unsigned long long next_ray;     // primaries handed out in the current wave
-    unsigned long long wave_begin;   // first ray id of the current wave
-    unsigned long long wave_count;   // primaries in the current wave
-    unsigned long long n_hits;       // stored reflections (next-event work)
-    unsigned long long n_records;    // contribution records in the current chunk
-    unsigned long long n_sphere;     // records written by the path kernel
-    unsigned long long next_item;    // shadow work fetched in the current chunk
-    unsigned long long n_rerun;      // shadow items queued for an FP64 decision (current chunk)
+// One scene of a trace step.  A single-scene step is a batch of one job; a
+// batched step runs many jobs (scenes, each with its own sources, listener and
+// ray budget) in the same persistent launches.
+struct SceneJob {
+    SceneView sc;
+    unsigned long long first_ray;  // id of the job's first primary
+    unsigned long long num_rays;   // primaries of the first wave
+    unsigned long long hit_off;    // first slot of the job's region of the reflection buffer
+    unsigned long long hit_cap;    // slots in that region (num_rays * M)
+    unsigned int scene_id;         // Philox counter word 1
+    int S;                         // sources of the job
+    int src_off;                   // global index of the job's first source
+    int lis;                       // index of the job's listener in the position table
 };
 
-// Contribution records: key = source * T + bin, ray id, e[B] (row of B floats).
+// Per-job state of one step (device memory, zeroed per step).
+struct JobState {
+    unsigned long long n_hits;      // stored reflections
+    unsigned long long primaries;   // K over all waves; the job's H is divided by it
+    unsigned long long wave_begin;  // first ray id of the current wave
+    unsigned long long wave_count;  // primaries of the current wave
+    unsigned long long item_off;    // first shadow item of the job
+    unsigned long long segments;    // closest-hit rays traced
+    unsigned long long mfp_count;
+    double mfp_sum;
+};
+
+// A run of consecutive primaries of one job; the batched paths kernel hands out
+// chunks in longest-processing-time order.
+struct RayChunk {
+    int job;
+    int count;
+    unsigned long long start;
+};
+
+// Global counters of one step (device memory, zeroed per step).
+struct TraceCounters {
+    unsigned long long next_ray;     // virtual ray index handed out in the current wave
+    unsigned long long n_records;    // contribution records in the current chunk
+    unsigned long long next_item;    // shadow items fetched in the current chunk
+    unsigned long long n_rerun;      // shadow items queued for an FP64 decision (current chunk)
+    unsigned long long total_items; // shadow items of the step (sum over jobs of hits x sources)
+    unsigned long long pad[3];
+};
+
+// Contribution records: key = (global source - first source of the group) * T + bin,
+// ray id, e[B] (row of B floats).
 struct Records {
     uint32_t *key;
     uint32_t *rid;
@@ -70,10 +105,9 @@ struct Hits {
 };
 
 struct TraceConsts {
-    int S, B, K, T, M, min_order, sh_order;
+    int S;           // sources of the group (keys and accumulation span them)
+    int B, K, T, M, min_order, sh_order;
     float rate, c, rs;
-    uint32_t scene_id, key0, key1;
-    uint64_t num_rays, first_ray;
     int flags;
 };
 
@@ -106,28 +140,41 @@ struct BvhOut {
 cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStream_t st);
 
 struct TraceWork {
-    SceneView sc;
+    SceneJob job0;         // the first (in single-job steps the only) job, by value
+    const SceneJob *jobs;  // [njobs], device
+    int njobs;
+    JobState *js;          // [njobs], device
+    int wave_mode;         // 1: one job, rays js[0].wave_begin + v (waves / refill)
+    const RayChunk *chunks;  // [nchunks] in LPT order (wave_mode == 0)
+    int nchunks;
+    int chunk_rays;
+    const int *src_job;    // [global sources] job of each source
+    int src_base;          // global index of the group's first source
     TraceConsts k;
-    const float4 *src;   // [S + 1] sources then the listener, (x, y, z, 0), device
+    const unsigned long long *seed;  // device Philox key (lo, hi words), or NULL: seed_val
+    unsigned long long seed_val;
+    const float4 *pos;     // sources (global index) then listeners (SceneJob::lis)
     TraceCounters *ctr;
     Hits hits;
     Records rec;
-    rp_trace_stats *stats;  // device accumulators
-    uint64_t *ray_hash;
+    rp_trace_stats *stats;  // aggregate statistics of the step
+    uint64_t *ray_hash;     // one job: hash of primary first_ray + i at [i]
     int *status;
     // accumulation
     uint32_t *cnt, *off, *cur, *perm;
-    float *Hs, *He;  // running compensated sums [S][B][K][T]
-    float *H;        // output
-    rp_direct *direct;
-    unsigned long long hits_per_chunk;
+    float *Hs, *He;  // running compensated sums [S][B][K][T] of the group
+    float *H;        // output, [global source][B][K][T]
+    rp_direct *direct;  // [global sources]
+    unsigned long long items_per_chunk;
     unsigned long long *rerun;  // queue of rounding-sensitive shadow items
     unsigned long long rerun_cap;
     int num_sms;
+    int shadow_steps;  // node visits a shadow lane makes between refills
 };
 
-void launch_wave_setup(const TraceWork &w, int wave, cudaStream_t st);
+void launch_setup(const TraceWork &w, int wave, cudaStream_t st);
 void launch_paths(const TraceWork &w, int blocks, cudaStream_t st);
+void launch_item_prefix(const TraceWork &w, cudaStream_t st);
 void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_shadow_exact(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_direct(const TraceWork &w, cudaStream_t st);
@@ -138,6 +185,25 @@ void launch_accum(const TraceWork &w, int first_chunk, int blocks, cudaStream_t 
 void launch_finalize(const TraceWork &w, cudaStream_t st);
 int paths_occupancy(int flags);
 int shadow_occupancy(int flags);
+
+// Host side: the launches of one trace step (one group of jobs).
+typedef void (*ProfHook)(void *ctx, const char *name, int begin);
+
+struct StepLaunch {
+    TraceWork w;                      // fully populated
+    unsigned long long n_rec_chunks;  // record chunks (worst case)
+    int refill;                       // one job: host-synchronised refill waves
+    int reset_stats;                  // zero the aggregate statistics first
+    int paths_blocks, shadow_blocks, exact_blocks, flat_blocks, acc_blocks;
+};
+cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, void *hook_ctx);
+
+struct StepSizes {
+    unsigned long long hit_cap, items, sph_cap, items_per_chunk, n_chunks, rec_cap, rerun_cap, keys, cells;
+    int S;
+};
+StepSizes step_sizes(const unsigned long long *rays, const int *sources, int njobs, int M, int B, int K, int T,
+                     unsigned long long rec_budget);
 
 struct EstimateWork {
     const float *H;

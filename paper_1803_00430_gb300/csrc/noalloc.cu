@@ -74,12 +74,6 @@ __global__ void k_pack_positions_na(const float *lis, const float *src, int S, f
     out[i] = make_float4(x, y, z, 0.f);
 }
 
-__global__ void k_copy_status_na(const int *status, const TraceCounters *ctr, rp_trace_stats *st)
-{
-    st->error = *status;
-    st->hits_stored = ctr->n_hits;
-}
-
 #define CKN(x)                                        \
     do {                                              \
         const cudaError_t e_ = (x);                   \
@@ -101,33 +95,30 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
         return RP_ERR_NAN_INPUT;
     rp_ctx *c = sc->ctx;
     const int B = sc->B, K = (p->sh_order + 1) * (p->sh_order + 1), T = p->num_bins, M = p->max_order;
-    const unsigned long long keys = (unsigned long long)S * T, cells = keys * B * K;
-    const unsigned long long hit_cap = std::max(1ull, p->num_rays * (unsigned long long)M);
-    const unsigned long long sph_cap = hit_cap / 2 + 4096;
-    const unsigned long long s1 = (unsigned long long)std::max(S, 1);
-
-    // fixed part of the layout
+    const unsigned long long rays = p->num_rays;
+    // the record budget is what the fixed part of the layout leaves; size it by
+    // trying the layout with the whole array first
+    StepSizes z = step_sizes(&rays, &S, 1, M, B, K, T, 1ull << 40);
     Carve cv;
     const unsigned long long o_ctr = cv.take<TraceCounters>(1), o_st = cv.take<rp_trace_stats>(1);
+    const unsigned long long o_job = cv.take<SceneJob>(1), o_js = cv.take<JobState>(1);
     const unsigned long long o_src = cv.take<float4>(S + 1), o_raw = cv.take<float>(3ull * (S + 1));
-    const unsigned long long o_hp = cv.take<float4>(hit_cap), o_hl = cv.take<float4>(hit_cap),
-                             o_hn = cv.take<float4>(hit_cap), o_hw = cv.take<float>(hit_cap * B),
-                             o_hr = cv.take<uint32_t>(hit_cap);
-    const unsigned long long o_cnt = cv.take<uint32_t>(keys), o_off = cv.take<uint32_t>(keys + 1),
-                             o_cur = cv.take<uint32_t>(keys);
-    const unsigned long long o_hs = cv.take<float>(cells), o_he = cv.take<float>(cells);
+    const unsigned long long o_hp = cv.take<float4>(z.hit_cap), o_hl = cv.take<float4>(z.hit_cap),
+                             o_hn = cv.take<float4>(z.hit_cap), o_hw = cv.take<float>(z.hit_cap * B),
+                             o_hr = cv.take<uint32_t>(z.hit_cap);
+    const unsigned long long o_cnt = cv.take<uint32_t>(z.keys), o_off = cv.take<uint32_t>(z.keys + 1),
+                             o_cur = cv.take<uint32_t>(z.keys);
+    const unsigned long long o_hs = cv.take<float>(z.cells), o_he = cv.take<float>(z.cells);
     if (cv.off >= RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
-    // the rest holds contribution records: key, ray, energies, sort index
-    const unsigned long long per_rec = 4ull + 4ull + 4ull * B + 4ull + 1ull + 16ull;  // + FP64 queue, slack
+    // the rest holds contribution records (key, ray, energies, sort index) and the
+    // FP64 re-decision queue (one entry per 8 records)
+    const unsigned long long per_rec = 4ull + 4ull + 4ull * B + 4ull + 1ull + 16ull;
     const unsigned long long rec_room = (RP_NOALLOC_SCRATCH_BYTES - cv.off) / per_rec;
-    if (rec_room < sph_cap + s1) return RP_ERR_TOO_LARGE;
-    const unsigned long long chunk_hits = std::max(1ull, std::min(hit_cap, (rec_room - sph_cap) / s1));
-    const unsigned long long n_chunks = (hit_cap + chunk_hits - 1) / chunk_hits;
-    const unsigned long long rec_cap = sph_cap + chunk_hits * s1;
-    const unsigned long long o_rk = cv.take<uint32_t>(rec_cap), o_rr = cv.take<uint32_t>(rec_cap),
-                             o_re = cv.take<float>(rec_cap * B), o_pm = cv.take<uint32_t>(rec_cap);
-    const unsigned long long rerun_cap = rec_cap / 8 + 4096;
-    const unsigned long long o_rq = cv.take<unsigned long long>(rerun_cap);
+    if (rec_room < z.sph_cap + (unsigned long long)std::max(S, 1)) return RP_ERR_TOO_LARGE;
+    z = step_sizes(&rays, &S, 1, M, B, K, T, rec_room);
+    const unsigned long long o_rk = cv.take<uint32_t>(z.rec_cap), o_rr = cv.take<uint32_t>(z.rec_cap),
+                             o_re = cv.take<float>(z.rec_cap * B), o_pm = cv.take<uint32_t>(z.rec_cap);
+    const unsigned long long o_rq = cv.take<unsigned long long>(z.rerun_cap);
     if (cv.off > RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
 
     CKN(cudaSetDevice(c->device));
@@ -152,8 +143,29 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     k_pack_positions_na<<<(S + 1 + 127) / 128, 128, 0, st>>>(lis, srcs, S, dsrc, c->d_status);
 
     TraceWork w;
-    w.sc = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris, sc->num_nodes,
-            sc->B, sc->tmin, sc->tmin_d};
+    SceneJob job;
+    job.sc = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris,
+              sc->num_nodes, sc->B, sc->tmin, sc->tmin_d};
+    job.first_ray = p->first_ray;
+    job.num_rays = p->num_rays;
+    job.hit_off = 0;
+    job.hit_cap = z.hit_cap;
+    job.scene_id = p->scene_id;
+    job.S = S;
+    job.src_off = 0;
+    job.lis = S;
+    // the job table lives in the scratch too; the copy is staged from the stack
+    CKN(cudaMemcpyAsync(base + o_job, &job, sizeof(SceneJob), cudaMemcpyHostToDevice, st));
+    w.job0 = job;
+    w.jobs = (const SceneJob *)(base + o_job);
+    w.njobs = 1;
+    w.js = (JobState *)(base + o_js);
+    w.wave_mode = 1;
+    w.chunks = nullptr;
+    w.nchunks = 0;
+    w.chunk_rays = 1;
+    w.src_job = nullptr;
+    w.src_base = 0;
     w.k.S = S;
     w.k.B = B;
     w.k.K = K;
@@ -164,17 +176,14 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.k.rate = p->ir_rate_hz;
     w.k.c = p->speed_of_sound;
     w.k.rs = p->source_radius;
-    w.k.scene_id = p->scene_id;
-    w.k.key0 = (uint32_t)p->seed;
-    w.k.key1 = (uint32_t)(p->seed >> 32);
-    w.k.num_rays = p->num_rays;
-    w.k.first_ray = p->first_ray;
     w.k.flags = p->flags & ~RP_FLAG_RAY_HASH;
-    w.src = dsrc;
+    w.seed = nullptr;
+    w.seed_val = p->seed;
+    w.pos = dsrc;
     w.ctr = (TraceCounters *)(base + o_ctr);
     w.hits = {(float4 *)(base + o_hp), (float4 *)(base + o_hl), (float4 *)(base + o_hn), (float *)(base + o_hw),
-              (uint32_t *)(base + o_hr), hit_cap};
-    w.rec = {(uint32_t *)(base + o_rk), (uint32_t *)(base + o_rr), (float *)(base + o_re), rec_cap};
+              (uint32_t *)(base + o_hr), z.hit_cap};
+    w.rec = {(uint32_t *)(base + o_rk), (uint32_t *)(base + o_rr), (float *)(base + o_re), z.rec_cap};
     w.stats = (rp_trace_stats *)(base + o_st);
     w.ray_hash = nullptr;
     w.status = c->d_status;
@@ -186,47 +195,23 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.He = (float *)(base + o_he);
     w.H = H;
     w.direct = direct;
-    w.hits_per_chunk = chunk_hits;
+    w.items_per_chunk = z.items_per_chunk;
     w.rerun = (unsigned long long *)(base + o_rq);
-    w.rerun_cap = rerun_cap;
+    w.rerun_cap = z.rerun_cap;
     w.num_sms = c->num_sms;
+    w.shadow_steps = c->shadow_steps;
 
-    // what must start at zero: the counters and the statistics of this step
-    CKN(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
-    CKN(cudaMemsetAsync(w.stats, 0, sizeof(rp_trace_stats), st));
-    launch_wave_setup(w, 0, st);
-    if (M > 0) launch_paths(w, c->paths_blocks, st);
-    if (p->budget_refill && M > 0) {
-        for (int wave = 1; wave < 4096; ++wave) {
-            launch_wave_setup(w, wave, st);
-            unsigned long long cnt = 0;
-            CKN(cudaMemcpyAsync(&cnt, &w.ctr->wave_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
-            CKN(cudaStreamSynchronize(st));
-            if (cnt == 0) break;
-            launch_paths(w, c->paths_blocks, st);
-        }
-    }
-    launch_direct(w, st);
-    const int grid_flat = c->num_sms * 8;
-    const int acc_blocks =
-        (int)std::max(1ll, std::min<long long>(((long long)keys + 7) / 8, (long long)c->num_sms * 8));
-    for (unsigned long long ch = 0; ch < n_chunks && S > 0; ++ch) {
-        if (ch > 0) CKN(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
-        CKN(cudaMemsetAsync(&w.ctr->next_item, 0, 2 * sizeof(unsigned long long), st));  // + n_rerun
-        if (M > 0) {
-            launch_shadow(w, ch, c->shadow_blocks, st);
-            launch_shadow_exact(w, ch, c->num_sms * 2, st);
-        }
-        CKN(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * keys, st));
-        CKN(cudaMemsetAsync(w.cur, 0, sizeof(uint32_t) * keys, st));
-        launch_count(w, grid_flat, st);
-        launch_scan(w, st);
-        launch_scatter(w, grid_flat, st);
-        launch_accum(w, ch == 0 ? 1 : 0, acc_blocks, st);
-    }
-    if (S > 0) launch_finalize(w, st);
-    k_copy_status_na<<<1, 1, 0, st>>>(c->d_status, w.ctr, w.stats);
-    CKN(cudaGetLastError());
+    StepLaunch L;
+    L.w = w;
+    L.n_rec_chunks = z.n_chunks;
+    L.refill = p->budget_refill;
+    L.reset_stats = 1;  // what must start at zero: counters, job state, statistics
+    L.paths_blocks = c->paths_blocks;
+    L.shadow_blocks = c->shadow_blocks;
+    L.exact_blocks = c->num_sms * 2;
+    L.flat_blocks = c->num_sms * 8;
+    L.acc_blocks = (int)std::max(1ll, std::min<long long>(((long long)z.keys + 7) / 8, (long long)c->num_sms * 8));
+    CKN(enqueue_step(L, st, nullptr, nullptr));
     if (stats) CKN(cudaMemcpyAsync(stats, w.stats, sizeof(rp_trace_stats), cudaMemcpyDeviceToDevice, st));
     return RP_OK;
 }

@@ -1,0 +1,153 @@
+// step.cu -- the launch sequence of one trace step (one group of jobs), shared by
+// rp_trace, rp_trace_noalloc and the batched entry points.
+//
+//   setup -> paths (-> refill waves) -> shadow-item prefix -> direct sound ->
+//   per record chunk: shadow rays -> FP64 re-decisions -> count -> scan -> scatter
+//   -> compensated accumulation
+//   -> finalize (normalise by primaries, bin direct sound) -> status copy
+//
+// Everything is enqueued on one stream without host synchronisation, except the
+// refill waves of a single-job step (the next wave's size is read back), so a step
+// without refill can be captured into a CUDA graph.
+#include "internal.cuh"
+
+namespace rp {
+namespace {
+
+__global__ void k_copy_status(TraceWork w)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    w.stats->error = *w.status;
+    unsigned long long h = 0;
+    for (int j = 0; j < w.njobs; ++j) h += min(w.js[j].n_hits, w.jobs[j].hit_cap);
+    w.stats->hits_stored += h;
+}
+
+struct Hook {
+    ProfHook fn;
+    void *ctx;
+    const char *name;
+    Hook(ProfHook f, void *c, const char *n) : fn(f), ctx(c), name(n)
+    {
+        if (fn) fn(ctx, name, 1);
+    }
+    ~Hook()
+    {
+        if (fn) fn(ctx, name, 0);
+    }
+};
+
+#define CKS(x)                                    \
+    do {                                          \
+        const cudaError_t e_ = (x);               \
+        if (e_ != cudaSuccess) return e_;         \
+    } while (0)
+
+}  // namespace
+
+cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, void *hook_ctx)
+{
+    const TraceWork &w = L.w;
+    const int S = w.k.S;
+    CKS(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
+    CKS(cudaMemsetAsync(w.js, 0, sizeof(JobState) * (size_t)w.njobs, st));
+    if (L.reset_stats) CKS(cudaMemsetAsync(w.stats, 0, sizeof(rp_trace_stats), st));
+    {
+        Hook h(hook, hook_ctx, "setup");
+        launch_setup(w, 0, st);
+    }
+    if (w.k.M > 0) {
+        Hook h(hook, hook_ctx, "paths");
+        launch_paths(w, L.paths_blocks, st);
+    }
+    if (L.refill && w.k.M > 0 && w.njobs == 1) {
+        for (int wave = 1; wave < 4096; ++wave) {
+            {
+                Hook h(hook, hook_ctx, "setup");
+                launch_setup(w, wave, st);
+            }
+            unsigned long long cnt = 0;
+            CKS(cudaMemcpyAsync(&cnt, &w.js[0].wave_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+            CKS(cudaStreamSynchronize(st));
+            if (cnt == 0) break;
+            Hook h(hook, hook_ctx, "paths");
+            launch_paths(w, L.paths_blocks, st);
+        }
+    }
+    {
+        Hook h(hook, hook_ctx, "item_prefix");
+        launch_item_prefix(w, st);
+    }
+    {
+        Hook h(hook, hook_ctx, "direct");
+        launch_direct(w, st);
+    }
+    const long long nkeys = (long long)S * w.k.T;
+    for (unsigned long long ch = 0; ch < L.n_rec_chunks && S > 0; ++ch) {
+        if (ch > 0) CKS(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
+        CKS(cudaMemsetAsync(&w.ctr->next_item, 0, 2 * sizeof(unsigned long long), st));  // + n_rerun
+        if (w.k.M > 0) {
+            {
+                Hook h(hook, hook_ctx, "shadow");
+                launch_shadow(w, ch, L.shadow_blocks, st);
+            }
+            Hook h(hook, hook_ctx, "shadow_exact");
+            launch_shadow_exact(w, ch, L.exact_blocks, st);
+        }
+        CKS(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nkeys, st));
+        CKS(cudaMemsetAsync(w.cur, 0, sizeof(uint32_t) * nkeys, st));
+        {
+            Hook h(hook, hook_ctx, "count");
+            launch_count(w, L.flat_blocks, st);
+        }
+        {
+            Hook h(hook, hook_ctx, "scan");
+            launch_scan(w, st);
+        }
+        {
+            Hook h(hook, hook_ctx, "scatter");
+            launch_scatter(w, L.flat_blocks, st);
+        }
+        {
+            Hook h(hook, hook_ctx, "accum");
+            launch_accum(w, ch == 0 ? 1 : 0, L.acc_blocks, st);
+        }
+    }
+    if (S > 0) {
+        Hook h(hook, hook_ctx, "finalize");
+        launch_finalize(w, st);
+    }
+    {
+        Hook h(hook, hook_ctx, "copy_status");
+        k_copy_status<<<1, 1, 0, st>>>(w);
+    }
+    return cudaGetLastError();
+}
+
+// Worst-case sizes of a group: reflections, shadow items and record chunks.
+StepSizes step_sizes(const unsigned long long *rays, const int *sources, int njobs, int M, int B, int K, int T,
+                     unsigned long long rec_budget)
+{
+    StepSizes z;
+    z.hit_cap = 0;
+    z.items = 0;
+    z.S = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const unsigned long long h = rays[j] * (unsigned long long)std::max(M, 0);
+        z.hit_cap += h;
+        z.items += h * (unsigned long long)sources[j];
+        z.S += sources[j];
+    }
+    z.hit_cap = std::max(1ull, z.hit_cap);
+    z.sph_cap = z.hit_cap / 2 + 4096;
+    const unsigned long long room = rec_budget > z.sph_cap + 1 ? rec_budget - z.sph_cap : 1ull << 20;
+    z.items_per_chunk = std::max(1ull, std::min(std::max(z.items, 1ull), room));
+    z.n_chunks = (std::max(z.items, 1ull) + z.items_per_chunk - 1) / z.items_per_chunk;
+    z.rec_cap = z.sph_cap + z.items_per_chunk;
+    z.rerun_cap = z.rec_cap / 8 + 4096;
+    z.keys = (unsigned long long)z.S * T;
+    z.cells = z.keys * B * K;
+    return z;
+}
+
+}  // namespace rp

@@ -1,9 +1,12 @@
 // trace.cu -- backward path tracing from the listener with diffuse rain
 // (Section 5, "Sound Propagation"), direct sound, and the segment-budget waves.
 //
+// A step runs one or many jobs (scenes with their own sources, listener and ray
+// budget) through the same persistent launches; BATCH selects the many-job form.
+//
 // Kernels of one trace step:
-//   k_wave_setup  sets the ray range of the next wave of primaries; with budget
-//                 refill the unused part of the N*M segment budget buys
+//   k_setup       sets each job's first wave; with budget refill (one job) later
+//                 waves spend the unused part of the N*M segment budget on
 //                 floor(unused / M) extra primaries (Section 5).
 //   k_paths       persistent: each warp takes 32 primaries at a time from a global
 //                 counter; each thread follows its path bounce by bounce: closest
@@ -132,26 +135,120 @@ __device__ __forceinline__ void emit_record(const TraceWork &w, uint32_t key, ui
     }
 }
 
-__global__ void k_wave_setup(TraceWork w, int wave)
+__global__ void k_setup(TraceWork w, int wave)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    TraceCounters *c = w.ctr;
-    unsigned long long count;
     if (wave == 0) {
-        c->wave_begin = w.k.first_ray;
-        count = w.k.num_rays;
-    } else {
-        c->wave_begin += c->wave_count;
-        const unsigned long long budget = w.k.num_rays * (unsigned long long)w.k.M;
-        const unsigned long long used = w.stats->segments;
-        const unsigned long long unused = budget > used ? budget - used : 0ull;
-        count = (w.k.M > 0 && unused >= (unsigned long long)w.k.M) ? unused / (unsigned long long)w.k.M : 0ull;
+        const int j = blockIdx.x * blockDim.x + threadIdx.x;
+        if (j >= w.njobs) return;
+        const SceneJob &J = w.jobs[j];
+        JobState &s = w.js[j];
+        s.wave_begin = J.first_ray;
+        s.wave_count = J.num_rays;
+        s.primaries = J.num_rays;
+        if (J.num_rays > 0) atomicAdd((unsigned long long *)&w.stats->primaries, J.num_rays);
+        if (j == 0) {
+            w.stats->waves = 1;
+            w.ctr->next_ray = 0;
+        }
+        return;
     }
-    c->wave_count = count;
-    c->next_ray = 0;
+    // later waves: one job, refill of the unused segment budget
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    JobState &s = w.js[0];
+    const SceneJob &J = w.jobs[0];
+    s.wave_begin += s.wave_count;
+    const unsigned long long budget = J.num_rays * (unsigned long long)w.k.M;
+    const unsigned long long used = s.segments;
+    const unsigned long long unused = budget > used ? budget - used : 0ull;
+    const unsigned long long count =
+        (w.k.M > 0 && unused >= (unsigned long long)w.k.M) ? unused / (unsigned long long)w.k.M : 0ull;
+    s.wave_count = count;
+    w.ctr->next_ray = 0;
     if (count > 0) {
         w.stats->waves += 1;
         w.stats->primaries += count;
+        s.primaries += count;
+    }
+}
+
+// first shadow item of every job: sum over earlier jobs of stored reflections x sources
+__global__ void k_item_prefix(TraceWork w)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long acc = 0;
+    for (int j = 0; j < w.njobs; ++j) {
+        w.js[j].item_off = acc;
+        const unsigned long long h = min(w.js[j].n_hits, w.jobs[j].hit_cap);
+        acc += h * (unsigned long long)w.jobs[j].S;
+    }
+    w.ctr->total_items = acc;
+}
+
+// job of shadow item q: the last job whose first item is <= q
+__device__ __forceinline__ int job_of_item(const TraceWork &w, unsigned long long q)
+{
+    int lo = 0, hi = w.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w.js[mid].item_off <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Warp-aggregated append on a per-job counter: lanes grouped by job.
+__device__ __forceinline__ unsigned long long warp_append_job(unsigned long long *counter, int job)
+{
+    const unsigned mask = __activemask();
+    const unsigned peers = __match_any_sync(mask, job);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + (unsigned long long)__popc(peers & ((1u << lane) - 1u));
+}
+
+// per-job path statistics kept per lane and flushed when the lane changes job
+struct JobAcc {
+    int job;
+    unsigned long long segs, mc;
+    double mfp;
+};
+
+__device__ __forceinline__ void job_flush(const TraceWork &w, JobAcc &a)
+{
+    if (a.job >= 0 && (a.segs || a.mc)) {
+        JobState &s = w.js[a.job];
+        atomicAdd(&s.segments, a.segs);
+        atomicAdd(&s.mfp_count, a.mc);
+        atomicAdd(&s.mfp_sum, a.mfp);
+    }
+    a.segs = a.mc = 0;
+    a.mfp = 0.0;
+}
+
+// final flush: whole warps that share a job reduce first
+__device__ __forceinline__ void job_flush_final(const TraceWork &w, JobAcc &a)
+{
+    const int lane = threadIdx.x & 31;
+    const int j0 = __shfl_sync(FULL, a.job, 0);
+    if (__all_sync(FULL, a.job == j0)) {
+        unsigned long long segs = a.segs, mc = a.mc;
+        double mfp = a.mfp;
+        for (int o = 16; o > 0; o >>= 1) {
+            segs += __shfl_xor_sync(FULL, segs, o);
+            mc += __shfl_xor_sync(FULL, mc, o);
+            mfp += __shfl_xor_sync(FULL, mfp, o);
+        }
+        if (lane == 0) {
+            a.segs = segs;
+            a.mc = mc;
+            a.mfp = mfp;
+            job_flush(w, a);
+        }
+    } else {
+        job_flush(w, a);
     }
 }
 
@@ -214,7 +311,7 @@ __device__ __forceinline__ V3<R> primary_dir_r(uint32_t rid, uint32_t scene_id, 
     return v3<R>(rad * c, rad * s, z);
 }
 
-template <typename R, bool HASH, bool COUNT>
+template <typename R, bool HASH, bool COUNT, bool BATCH>
 __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
 {
     __shared__ int sstack[SMEM_STACK * PATH_THREADS];
@@ -222,20 +319,25 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
     acc_init(acc);
     __syncthreads();
 
-    const SceneView &sc = w.sc;
     const TraceConsts &k = w.k;
-    const int B = k.B, S = k.S, T = k.T, M = k.M;
+    const int B = k.B, T = k.T, M = k.M;
     const int lane = threadIdx.x & 31;
-    const unsigned long long wave_begin = w.ctr->wave_begin, wave_count = w.ctr->wave_count;
+    const unsigned long long seed = w.seed ? w.seed[0] : w.seed_val;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    const unsigned long long wave_begin = BATCH ? 0ull : w.js[0].wave_begin;  // set by k_setup
+    const unsigned long long wave_count = BATCH ? 0ull : w.js[0].wave_count;
+    const unsigned long long vtotal = BATCH ? (unsigned long long)w.nchunks * w.chunk_rays : wave_count;
     const float inv_pi_rs2 = 1.0f / (PI_F * k.rs * k.rs);
-    const V3<R> lis = from4<R>(__ldg(w.src + S));  // the listener follows the S sources
 
-    double mfp = 0.0, mfp_np = 0.0;
-    unsigned long long mc = 0, mcnp = 0, segs = 0, sphere = 0, contrib = 0, reruns = 0;
+    double mfp_np = 0.0;
+    unsigned long long mcnp = 0, sphere = 0, contrib = 0, reruns = 0, segs_all = 0, mc_all = 0;
+    double mfp_all = 0.0;
     TravStats ts = {0u, 0u};
+    JobAcc ja = {BATCH ? -1 : 0, 0ull, 0ull, 0.0};
 
     // path state
-    bool have = false, done = wave_count == 0;
+    bool have = false, done = vtotal == 0;
+    int job = 0;
     uint32_t rid = 0;
     V3<R> o = v3<R>(0, 0, 0), d = o;
     R L = 0;
@@ -252,12 +354,31 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
             if (lane == leader) base = atomicAdd(&w.ctr->next_ray, (unsigned long long)__popc(need));
             base = __shfl_sync(FULL, base, leader);
             if (!have && !done) {
-                const unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
-                if (my < wave_count) {
-                    rid = (uint32_t)(wave_begin + my);
+                const unsigned long long v = base + __popc(need & ((1u << lane) - 1u));
+                bool got = false;
+                if (v >= vtotal) {
+                    done = true;
+                } else if (BATCH) {
+                    const RayChunk ch = w.chunks[v / (unsigned long long)w.chunk_rays];
+                    const unsigned r = (unsigned)(v % (unsigned long long)w.chunk_rays);
+                    if (r < (unsigned)ch.count) {  // otherwise padding of a short chunk
+                        job = ch.job;
+                        rid = (uint32_t)(ch.start + r);
+                        got = true;
+                    }
+                } else {
+                    rid = (uint32_t)(wave_begin + v);
+                    got = true;
+                }
+                if (got) {
+                    if (BATCH && job != ja.job) {
+                        job_flush(w, ja);
+                        ja.job = job;
+                    }
+                    const SceneJob &J = BATCH ? w.jobs[job] : w.job0;
                     have = true;
-                    o = lis;
-                    d = primary_dir_r<R>(rid, k.scene_id, k.key0, k.key1);
+                    o = from4<R>(__ldg(w.pos + J.lis));
+                    d = primary_dir_r<R>(rid, J.scene_id, key0, key1);
                     L = 0;
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b) {
@@ -268,14 +389,14 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
                     h = 1;
                     spec_prev = false;
                     hash = FNV_OFFSET;
-                } else {
-                    done = true;
                 }
             }
         }
-        if (!__any_sync(FULL, have)) break;
+        if (!__any_sync(FULL, have) && __all_sync(FULL, done || have)) break;
         if (!have) continue;
 
+        const SceneJob &J = BATCH ? w.jobs[job] : w.job0;
+        const SceneView sc = J.sc;
         // ---- one segment: closest hit (FP32 traversal) ----
         const float3 of = to_f3(o), df = to_f3(d);
         const float Lf = (float)L;
@@ -301,11 +422,13 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
             tri = traverse<false, COUNT, false>(sc, of, df, sc.tmin, INFINITY, prev, sstack + threadIdx.x, tf, ts,
                                                 w.status);
         }
-        ++segs;
+        ++ja.segs;
+        ++segs_all;
         if (spec_prev && h - 1 >= k.min_order) {
-            // the source as a sphere of radius r_s, seen through the specular bounce
-            for (int s = 0; s < S; ++s) {
-                const float4 cs = __ldg(w.src + s);
+            // the job's sources as spheres of radius r_s, seen through the specular bounce
+            for (int s = 0; s < J.S; ++s) {
+                const int gs = J.src_off + s;
+                const float4 cs = __ldg(w.pos + gs);
                 const float3 oc = of - xyz(cs);
                 const float bq = dot(oc, df);
                 const float cq = dot(oc, oc) - k.rs * k.rs;
@@ -331,7 +454,7 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
                     binf = floorf(x);
                 }
                 if (binf < (float)T) {
-                    emit_record(w, (uint32_t)s * (uint32_t)T + (uint32_t)binf, rid, e, B);
+                    emit_record(w, (uint32_t)(gs - w.src_base) * (uint32_t)T + (uint32_t)binf, rid, e, B);
                 } else {
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b)
@@ -362,8 +485,10 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
             }
             L += t;
             const V3<R> p = o + d * t;
-            mfp += (double)t;
-            ++mc;
+            ja.mfp += (double)t;
+            ++ja.mc;
+            mfp_all += (double)t;
+            ++mc_all;
             if (h > 1) {
                 mfp_np += (double)t;
                 ++mcnp;
@@ -381,9 +506,11 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
                     wgt[b] *= (1.0f - a);
                 }
             }
-            if (h >= k.min_order && S > 0) {
-                const unsigned long long j = warp_append(&w.ctr->n_hits);
-                if (j < w.hits.cap) {
+            if (h >= k.min_order && J.S > 0) {
+                const unsigned long long jl =
+                    BATCH ? warp_append_job(&w.js[job].n_hits, job) : warp_append(&w.js[0].n_hits);
+                if (jl < J.hit_cap) {
+                    const unsigned long long j = J.hit_off + jl;
                     const float4 phi = make_float4((float)p.x, (float)p.y, (float)p.z, (float)L);
                     w.hits.p[j] = phi;
                     w.hits.plo[j] = make_float4((float)(p.x - (R)phi.x), (float)(p.y - (R)phi.y),
@@ -404,7 +531,7 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
                     if (b < B) atomicAdd(&acc.rem[b], (double)wgt[b]);
                 end_ray = true;
             } else {
-                const U4 r = philox4x32_10(rid, k.scene_id, (uint32_t)h, 0u, k.key0, k.key1);
+                const U4 r = philox4x32_10(rid, J.scene_id, (uint32_t)h, 0u, key0, key1);
                 if ((r.z >> 8) < __ldg(sc.thr + mat)) {
                     // cosine-weighted hemisphere about n (Malley), frame of Duff et al. 2017
                     const R u0 = u01r<R>(r.x), u1 = u01r<R>(r.y);
@@ -441,22 +568,23 @@ __global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
 #pragma unroll
             for (int b = 0; b < MAXB; ++b)
                 if (b < B) atomicAdd(&acc.absb[b], (double)absorbed[b]);
-            if (HASH && w.ray_hash && rid >= k.first_ray && rid - k.first_ray < k.num_rays)
-                w.ray_hash[rid - k.first_ray] = hash;
+            if (HASH && w.ray_hash && rid >= J.first_ray && rid - J.first_ray < J.num_rays)
+                w.ray_hash[rid - J.first_ray] = hash;
             have = false;
         }
     }
-    acc_counters(acc, mfp, mfp_np, mc, mcnp, segs, 0ull, contrib, sphere, ts);
+    job_flush_final(w, ja);
+    acc_counters(acc, mfp_all, mfp_np, mc_all, mcnp, segs_all, 0ull, contrib, sphere, ts);
     for (int o = 16; o > 0; o >>= 1) reruns += __shfl_xor_sync(FULL, reruns, o);
     if (lane == 0 && reruns) atomicAdd((unsigned long long *)&w.stats->fp64_reruns, reruns);
     acc_flush(acc, w.stats, B, 0);
 }
 
-// Emit the contribution of a visible (reflection j, source s) pair: energy
+// Emit the contribution of a visible (reflection j, global source gs) pair: energy
 // w_b s_b cos(theta) / (pi d^2), arrival (L + d) / c.  An FP32 arrival time that
 // lands within BIN_GUARD of a bin boundary is re-decided in FP64 from the stored
 // residuals.
-__device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc &acc, unsigned long long j, int s,
+__device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc &acc, unsigned long long j, int gs,
                                                     float f, float dist)
 {
     const TraceConsts &k = w.k;
@@ -469,7 +597,7 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
     const float x = ((P.w + dist) / k.c) * k.rate;
     if (fabsf(x - rintf(x)) < BIN_GUARD) {
         const float4 lo = w.hits.plo[j];
-        const float4 cs = __ldg(w.src + s);
+        const float4 cs = __ldg(w.pos + gs);
         const double dx = (double)cs.x - ((double)P.x + (double)lo.x);
         const double dy = (double)cs.y - ((double)P.y + (double)lo.y);
         const double dz = (double)cs.z - ((double)P.z + (double)lo.z);
@@ -480,7 +608,7 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
         binf = floorf(x);
     }
     if (binf < (float)T) {
-        emit_record(w, (uint32_t)s * (uint32_t)T + (uint32_t)binf, w.hits.rid[j], e, B);
+        emit_record(w, (uint32_t)(gs - w.src_base) * (uint32_t)T + (uint32_t)binf, w.hits.rid[j], e, B);
     } else {
 #pragma unroll
         for (int b = 0; b < MAXB; ++b)
@@ -488,13 +616,25 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
     }
 }
 
-// Shadow rays of one chunk of stored reflections: items q = (reflection, source)
-// pairs, reflection-major.  Persistent threads with per-lane refill: each lane
-// advances its any-hit query SHADOW_STEPS nodes at a time; a lane whose query ends
-// takes the next item at once, so lanes of a warp do not idle behind its longest
+// (job, reflection slot, global source) of shadow item q
+__device__ __forceinline__ void item_target(const TraceWork &w, bool batch, unsigned long long q, int &job,
+                                            unsigned long long &j, int &gs)
+{
+    job = batch ? job_of_item(w, q) : 0;
+    const SceneJob &J = batch ? w.jobs[job] : w.job0;
+    const unsigned long long local = q - (batch ? w.js[job].item_off : 0ull);
+    const unsigned long long jj = local / (unsigned long long)J.S;
+    j = J.hit_off + jj;
+    gs = J.src_off + (int)(local - jj * (unsigned long long)J.S);
+}
+
+// Shadow rays of one chunk of the step's items q = (reflection, source) pairs,
+// reflection-major within each job.  Persistent threads with per-lane refill:
+// each lane advances its any-hit query a few nodes at a time and takes the next
+// item as soon as its query ends, so lanes of a warp do not idle behind the longest
 // ray.  Queries whose FP32 answer is rounding-sensitive are queued for the FP64
 // kernel below (EXACT); when the queue is full the FP32 answer stands.
-template <bool COUNT, bool EXACT>
+template <bool COUNT, bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned long long chunk)
 {
     __shared__ int sstack[SMEM_STACK * SHADOW_THREADS];
@@ -502,15 +642,11 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
     acc_init(acc);
     __syncthreads();
 
-    const SceneView &sc = w.sc;
-    const TraceConsts &k = w.k;
-    const int S = k.S;
     const int lane = threadIdx.x & 31;
-    const unsigned long long nh = min(w.ctr->n_hits, w.hits.cap);
-    const unsigned long long j0 = chunk * w.hits_per_chunk;
-    const unsigned long long j1 = min(j0 + w.hits_per_chunk, nh);
-    const unsigned long long items = j1 > j0 ? (j1 - j0) * (unsigned long long)S : 0ull;
-    const int iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
+    const unsigned long long total = w.ctr->total_items;
+    const unsigned long long q0 = chunk * w.items_per_chunk;
+    const unsigned long long items = total > q0 ? min(w.items_per_chunk, total - q0) : 0ull;
+    const int steps_per_visit = w.shadow_steps;
     const float inv_pi = 1.0f / PI_F;
     int lstack[LOCAL_STACK];
 
@@ -518,10 +654,11 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
     TravStats ts = {0u, 0u};
     bool busy = false, exhausted = items == 0;
     unsigned long long item = 0;
+    int job = 0;
     AnyRay ray;
     float3 dir = mk3(0.f, 0.f, 0.f);
     AnyState st = {-1, 0, INFINITY, false, false};
-    int steps = 0;
+    int steps = 0, iter_cap = 0;
     float f = 0.f, dist = 0.f;
     while (true) {
         const unsigned need = __ballot_sync(FULL, !busy && !exhausted);
@@ -535,13 +672,14 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
                 if (my >= items) {
                     exhausted = true;
                 } else {
-                    item = my;
-                    const unsigned long long jj = my / (unsigned long long)S;
-                    const int s = (int)(my - jj * (unsigned long long)S);
-                    const unsigned long long j = j0 + jj;
+                    item = q0 + my;
+                    unsigned long long j;
+                    int gs;
+                    item_target(w, BATCH, item, job, j, gs);
+                    const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
                     const float4 P = w.hits.p[j], N = w.hits.n[j];
                     const float3 p = xyz(P);
-                    const float3 v = xyz(__ldg(w.src + s)) - p;
+                    const float3 v = xyz(__ldg(w.pos + gs)) - p;
                     const float dist2 = dot(v, v);
                     dist = sqrtf(dist2);
                     const float cth = dot(xyz(N), v) / dist;
@@ -551,6 +689,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
                         ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
                         st = {0, 0, INFINITY, false, false};
                         steps = 0;
+                        iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
                         f = cth * inv_pi / dist2;
                         busy = true;
                     }
@@ -559,9 +698,10 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
         }
         if (__all_sync(FULL, !busy && exhausted)) break;
         if (!busy) continue;
-        bool done = any_hit_steps<COUNT, EXACT>(sc, ray, dir, st, sstack + threadIdx.x, lstack, SHADOW_STEPS, ts,
+        const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
+        bool done = any_hit_steps<COUNT, EXACT>(sc, ray, dir, st, sstack + threadIdx.x, lstack, steps_per_visit, ts,
                                                  w.status);
-        steps += SHADOW_STEPS;
+        steps += steps_per_visit;
         if (!done && steps > iter_cap) {
             raise_error(w.status, RP_ERR_TIMEOUT);
             done = true;
@@ -577,13 +717,15 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
             }
         }
         if (!st.blocked) {
-            const unsigned long long jj = item / (unsigned long long)S;
+            unsigned long long j;
+            int gs, jb;
+            item_target(w, BATCH, item, jb, j, gs);
             ++contrib;
-            shadow_contribution(w, acc, j0 + jj, (int)(item - jj * (unsigned long long)S), f, dist);
+            shadow_contribution(w, acc, j, gs, f, dist);
         }
     }
     acc_counters(acc, 0.0, 0.0, 0ull, 0ull, 0ull, shadow, contrib, 0ull, ts);
-    acc_flush(acc, w.stats, k.B, 1);
+    acc_flush(acc, w.stats, w.k.B, 1);
 }
 
 // FP64 decisions for the shadow rays whose FP32 visibility was rounding-sensitive
@@ -593,30 +735,29 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_exact(TraceWork w, un
     __shared__ BlockAcc acc;
     acc_init(acc);
     __syncthreads();
-    const int S = w.k.S;
     const unsigned long long n = min(w.ctr->n_rerun, w.rerun_cap);
-    const unsigned long long j0 = chunk * w.hits_per_chunk;
     unsigned long long contrib = 0;
+    (void)chunk;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long item = w.rerun[i];
-        const unsigned long long jj = item / (unsigned long long)S;
-        const int s = (int)(item - jj * (unsigned long long)S);
-        const unsigned long long j = j0 + jj;
+        int job, gs;
+        unsigned long long j;
+        item_target(w, w.njobs > 1, w.rerun[i], job, j, gs);
+        const SceneView &sc = w.njobs > 1 ? w.jobs[job].sc : w.job0.sc;
         const float4 P = w.hits.p[j], N = w.hits.n[j], lo = w.hits.plo[j];
-        const float4 cs = __ldg(w.src + s);
+        const float4 cs = __ldg(w.pos + gs);
         const D3 pd = {(double)P.x + lo.x, (double)P.y + lo.y, (double)P.z + lo.z};
         const double vx = (double)cs.x - pd.x, vy = (double)cs.y - pd.y, vz = (double)cs.z - pd.z;
         const double dd = sqrt(vx * vx + vy * vy + vz * vz);
         double te;
-        const int blk = traverse_exact<true>(w.sc, pd, D3{vx / dd, vy / dd, vz / dd}, w.sc.tmin_d, dd,
+        const int blk = traverse_exact<true>(sc, pd, D3{vx / dd, vy / dd, vz / dd}, sc.tmin_d, dd,
                                              __float_as_int(N.w), sstack + threadIdx.x, te, w.status);
         if (blk < 0) {
             const float3 v = xyz(cs) - xyz(P);
             const float dist2 = dot(v, v), dist = sqrtf(dist2);
             const float cth = dot(xyz(N), v) / dist;
             ++contrib;
-            shadow_contribution(w, acc, j, s, cth * (1.0f / PI_F) / dist2, dist);
+            shadow_contribution(w, acc, j, gs, cth * (1.0f / PI_F) / dist2, dist);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd((unsigned long long *)&w.stats->fp64_reruns, n);
@@ -625,25 +766,29 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_exact(TraceWork w, un
     acc_flush(acc, w.stats, w.k.B, 1);
 }
 
+// Direct sound of the group's sources: distance, time and bin in FP64, the
+// visibility ray in FP32 (re-decided in FP64 when rounding-sensitive).
 __global__ void __launch_bounds__(128) k_direct(TraceWork w)
 {
     __shared__ int sstack[SMEM_STACK * 128];
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= w.k.S) return;
-    const float4 l4 = __ldg(w.src + w.k.S), s4 = __ldg(w.src + s);
-    // distance, time and bin in FP64; the visibility ray in FP32
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.k.S) return;
+    const int gs = w.src_base + i;
+    const int job = w.njobs > 1 ? w.src_job[gs] : 0;
+    const SceneJob &J = w.njobs > 1 ? w.jobs[job] : w.job0;
+    const float4 l4 = __ldg(w.pos + J.lis), s4 = __ldg(w.pos + gs);
     const double vx = (double)s4.x - l4.x, vy = (double)s4.y - l4.y, vz = (double)s4.z - l4.z;
     const double dist = sqrt(vx * vx + vy * vy + vz * vz);
     const float3 dir = mk3((float)(vx / dist), (float)(vy / dist), (float)(vz / dist));
     TravStats ts = {0u, 0u};
     float tt;
     bool amb = false;
-    int blk = traverse<true, false, true>(w.sc, xyz(l4), dir, w.sc.tmin, (float)dist, -1, sstack + threadIdx.x, tt,
+    int blk = traverse<true, false, true>(J.sc, xyz(l4), dir, J.sc.tmin, (float)dist, -1, sstack + threadIdx.x, tt,
                                           ts, w.status, &amb);
     if (amb) {
         double te;
-        blk = traverse_exact<true>(w.sc, D3{(double)l4.x, (double)l4.y, (double)l4.z},
-                                   D3{vx / dist, vy / dist, vz / dist}, w.sc.tmin_d, dist, -1, sstack + threadIdx.x,
+        blk = traverse_exact<true>(J.sc, D3{(double)l4.x, (double)l4.y, (double)l4.z},
+                                   D3{vx / dist, vy / dist, vz / dist}, J.sc.tmin_d, dist, -1, sstack + threadIdx.x,
                                    te, w.status);
     }
     rp_direct out;
@@ -657,38 +802,56 @@ __global__ void __launch_bounds__(128) k_direct(TraceWork w)
     float Y[MAXK];
     sh_eval(w.k.sh_order, dir.x, dir.y, dir.z, Y);
     for (int kk = 0; kk < MAXK; ++kk) out.sh[kk] = kk < w.k.K ? out.energy * Y[kk] : 0.f;
-    w.direct[s] = out;
+    w.direct[gs] = out;
 }
 
 }  // namespace
 
-void launch_wave_setup(const TraceWork &w, int wave, cudaStream_t st) { k_wave_setup<<<1, 32, 0, st>>>(w, wave); }
+void launch_setup(const TraceWork &w, int wave, cudaStream_t st)
+{
+    k_setup<<<wave == 0 ? (w.njobs + 127) / 128 : 1, 128, 0, st>>>(w, wave);
+}
 
-template <typename R>
+void launch_item_prefix(const TraceWork &w, cudaStream_t st) { k_item_prefix<<<1, 32, 0, st>>>(w); }
+
+template <typename R, bool BATCH>
 void launch_paths_r(const TraceWork &w, int blocks, cudaStream_t st)
 {
     const bool hash = (w.k.flags & RP_FLAG_RAY_HASH) && w.ray_hash;
     const bool count = (w.k.flags & RP_FLAG_COUNT_VISITS) != 0;
-    if (hash && count) k_paths<R, true, true><<<blocks, PATH_THREADS, 0, st>>>(w);
-    else if (hash) k_paths<R, true, false><<<blocks, PATH_THREADS, 0, st>>>(w);
-    else if (count) k_paths<R, false, true><<<blocks, PATH_THREADS, 0, st>>>(w);
-    else k_paths<R, false, false><<<blocks, PATH_THREADS, 0, st>>>(w);
+    if (hash && count) k_paths<R, true, true, BATCH><<<blocks, PATH_THREADS, 0, st>>>(w);
+    else if (hash) k_paths<R, true, false, BATCH><<<blocks, PATH_THREADS, 0, st>>>(w);
+    else if (count) k_paths<R, false, true, BATCH><<<blocks, PATH_THREADS, 0, st>>>(w);
+    else k_paths<R, false, false, BATCH><<<blocks, PATH_THREADS, 0, st>>>(w);
 }
 
 void launch_paths(const TraceWork &w, int blocks, cudaStream_t st)
 {
-    if (w.k.flags & RP_FLAG_FP32_PATHS) launch_paths_r<float>(w, blocks, st);
-    else launch_paths_r<double>(w, blocks, st);
+    const bool batch = !w.wave_mode;
+    if (w.k.flags & RP_FLAG_FP32_PATHS) {
+        if (batch) launch_paths_r<float, true>(w, blocks, st);
+        else launch_paths_r<float, false>(w, blocks, st);
+    } else {
+        if (batch) launch_paths_r<double, true>(w, blocks, st);
+        else launch_paths_r<double, false>(w, blocks, st);
+    }
+}
+
+template <bool BATCH>
+void launch_shadow_b(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
+{
+    const bool count = (w.k.flags & RP_FLAG_COUNT_VISITS) != 0;
+    const bool exact = (w.k.flags & RP_FLAG_FP32_PATHS) == 0;
+    if (count && exact) k_shadow<true, true, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    else if (count) k_shadow<true, false, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    else if (exact) k_shadow<false, true, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    else k_shadow<false, false, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
 }
 
 void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
 {
-    const bool count = (w.k.flags & RP_FLAG_COUNT_VISITS) != 0;
-    const bool exact = (w.k.flags & RP_FLAG_FP32_PATHS) == 0;
-    if (count && exact) k_shadow<true, true><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
-    else if (count) k_shadow<true, false><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
-    else if (exact) k_shadow<false, true><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
-    else k_shadow<false, false><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+    if (w.njobs > 1) launch_shadow_b<true>(w, chunk, blocks, st);
+    else launch_shadow_b<false>(w, chunk, blocks, st);
 }
 
 void launch_shadow_exact(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
@@ -705,9 +868,9 @@ int paths_occupancy(int flags)
 {
     int n = 0;
     if (flags & RP_FLAG_FP32_PATHS)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_paths<float, false, false>, PATH_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_paths<float, false, false, false>, PATH_THREADS, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_paths<double, false, false>, PATH_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_paths<double, false, false, false>, PATH_THREADS, 0);
     return n > 0 ? n : 1;
 }
 
@@ -715,9 +878,9 @@ int shadow_occupancy(int flags)
 {
     int n = 0;
     if (flags & RP_FLAG_FP32_PATHS)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false, false>, SHADOW_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false, false, false>, SHADOW_THREADS, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false, true>, SHADOW_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false, true, false>, SHADOW_THREADS, 0);
     return n > 0 ? n : 1;
 }
 

@@ -85,6 +85,22 @@ class rp_reverb_params(C.Structure):
                 ("fit_j1", C.c_int32), ("xbar", C.c_double * MAX_SH)]
 
 
+class rp_batch_item(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("listener", C.c_void_p), ("sources", C.c_void_p),
+                ("num_sources", C.c_int32), ("scene_id", C.c_uint32), ("num_rays", C.c_uint64),
+                ("first_ray", C.c_uint64)]
+
+
+class rp_batch_tuning(C.Structure):
+    _fields_ = [("chunk_rays", C.c_int32), ("shadow_steps", C.c_int32), ("paths_blocks_per_sm", C.c_int32),
+                ("shadow_blocks_per_sm", C.c_int32)]
+
+
+class rp_batch_info(C.Structure):
+    _fields_ = [("num_items", C.c_int32), ("total_sources", C.c_int32), ("num_groups", C.c_int32),
+                ("reserved", C.c_int32), ("total_rays", C.c_uint64), ("max_group_reflections", C.c_uint64)]
+
+
 class rp_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -106,6 +122,16 @@ _SIGS = {
     "rp_update": ([C.c_void_p, C.POINTER(rp_trace_params), C.POINTER(rp_estimate_params), C.c_void_p,
                    C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                   C.c_int),
+    "rp_batch_create": ([C.c_void_p, C.POINTER(rp_batch_item), C.c_int32, C.POINTER(rp_trace_params),
+                         C.POINTER(rp_estimate_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                         C.POINTER(C.c_void_p)], C.c_int),
+    "rp_batch_destroy": ([C.c_void_p], C.c_int),
+    "rp_batch_run": ([C.c_void_p, C.c_uint64, C.c_int], C.c_int),
+    "rp_batch_set_tuning": ([C.c_void_p, C.POINTER(rp_batch_tuning)], C.c_int),
+    "rp_batch_get_tuning": ([C.c_void_p, C.POINTER(rp_batch_tuning)], C.c_int),
+    "rp_batch_info_get": ([C.c_void_p, C.POINTER(rp_batch_info)], C.c_int),
+    "rp_batch_autotune": ([C.c_void_p, C.c_uint64, C.c_char_p, C.POINTER(rp_batch_tuning),
+                           C.POINTER(C.c_double)], C.c_int),
     "rp_trace_noalloc": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                           C.c_void_p, C.c_void_p], C.c_int),
     "rp_sync_status": ([C.c_void_p], C.c_int),
@@ -123,7 +149,7 @@ def _close_all():
     """Release library objects while the CUDA runtime is still alive (interpreter
     exit runs Python's atexit handlers before the C runtime's)."""
     global _closed
-    for obj in sorted(list(_live), key=lambda o: 0 if isinstance(o, Scene) else 1):
+    for obj in sorted(list(_live), key=lambda o: 0 if isinstance(o, Batch) else 1 if isinstance(o, Scene) else 2):
         try:
             obj.close()
         except Exception:
@@ -405,6 +431,96 @@ def trace_noalloc(scene: Scene, p: TraceParams, listener, sources, out: DeviceTr
     if sync:
         check(scene.ctx.sync_status(), "rp_trace_noalloc (device)")
     return out
+
+
+class Batch:
+    """rp_batch: many scenes traced and estimated in the same launches.  `items` is a
+    list of (Scene, listener[3], sources[S,3], num_rays, scene_id).  Outputs are torch
+    CUDA tensors owned by this object; item i's sources start at self.offsets[i]."""
+
+    def __init__(self, ctx: Context, items, p: TraceParams, est_tau: float = 0.0, est_dt: float = 0.0,
+                 estimate: bool = True):
+        import torch
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.p = p
+        self._keep = []
+        arr = (rp_batch_item * len(items))()
+        self.offsets = []
+        S_total = 0
+        B = None
+        for i, (scene, lis, src, rays, sid) in enumerate(items):
+            lis = np.ascontiguousarray(lis, np.float32).reshape(3)
+            src = np.ascontiguousarray(src, np.float32).reshape(-1, 3)
+            self._keep += [lis, src]
+            arr[i] = rp_batch_item(scene.h, lis.ctypes.data, src.ctypes.data, src.shape[0], int(sid),
+                                   int(rays), 0)
+            self.offsets.append(S_total)
+            S_total += src.shape[0]
+            B = scene.B
+        self.S, self.B, self.K, self.T = S_total, B, p.K, p.num_bins
+        dev = "cuda"
+        self.H = torch.empty((S_total, B, p.K, p.num_bins), dtype=torch.float32, device=dev)
+        self.direct = torch.zeros(max(S_total, 1) * C.sizeof(rp_direct), dtype=torch.uint8, device=dev)
+        self.params = (torch.zeros(max(S_total * B, 1) * C.sizeof(rp_reverb_params), dtype=torch.uint8,
+                                   device=dev) if estimate else None)
+        self.stats = torch.zeros(C.sizeof(rp_trace_stats), dtype=torch.uint8, device=dev)
+        ep = rp_estimate_params(float(p.ir_rate_hz), float(est_dt), float(est_tau))
+        cp = p.c()
+        h = C.c_void_p()
+        check(self.lib.rp_batch_create(ctx.h, arr, len(items), C.byref(cp), C.byref(ep), _ptr(self.H),
+                                       _ptr(self.direct), _ptr(self.params), _ptr(self.stats), C.byref(h)),
+              "rp_batch_create")
+        self.h = h
+        self._keep = None
+        _live.add(self)
+
+    def run(self, seed: int, use_graph: bool = False, sync: bool = True):
+        check(self.lib.rp_batch_run(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF, int(use_graph)), "rp_batch_run")
+        if sync:
+            check(self.ctx.sync_status(), "rp_batch_run (device)")
+
+    def tuning(self) -> rp_batch_tuning:
+        t = rp_batch_tuning()
+        check(self.lib.rp_batch_get_tuning(self.h, C.byref(t)), "rp_batch_get_tuning")
+        return t
+
+    def set_tuning(self, t: rp_batch_tuning):
+        check(self.lib.rp_batch_set_tuning(self.h, C.byref(t)), "rp_batch_set_tuning")
+
+    def info(self) -> rp_batch_info:
+        i = rp_batch_info()
+        check(self.lib.rp_batch_info_get(self.h, C.byref(i)), "rp_batch_info_get")
+        return i
+
+    def autotune(self, seed: int, cache_path: str | None = None):
+        t = rp_batch_tuning()
+        ms = C.c_double()
+        check(self.lib.rp_batch_autotune(self.h, int(seed), cache_path.encode() if cache_path else None,
+                                         C.byref(t), C.byref(ms)), "rp_batch_autotune")
+        return t, ms.value
+
+    def stats_dict(self) -> dict:
+        st = rp_trace_stats.from_buffer_copy(bytes(self.stats.cpu().numpy()))
+        return stats_to_dict(st, self.B)
+
+    def params_dict(self) -> dict:
+        return params_to_dict(self.params.cpu().numpy().tobytes()[: self.S * self.B * C.sizeof(rp_reverb_params)],
+                              self.S, self.B, self.K)
+
+    def direct_dict(self) -> dict:
+        return direct_to_dict(self.direct.cpu().numpy()[: self.S * C.sizeof(rp_direct)], self.S, self.K)
+
+    def close(self):
+        if getattr(self, "h", None) and not _closed:
+            self.lib.rp_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def estimate(ctx: Context, H, direct, ir_rate_hz: float, dt_update: float = 0.0, tau: float = 0.0,

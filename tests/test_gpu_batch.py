@@ -1,0 +1,145 @@
+"""Batched updates (many scenes in the same persistent launches, CUDA graph replay,
+autotuned launch shapes): every item of a batch must equal the single-scene trace
+of the same scene, rays and key (same algorithm on the same random numbers), and
+the oracle on sampled items."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1803_00430_gb300 import build, rpr, scenes  # noqa: E402
+
+import parity_util as pu  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    c = rpr.Context(0)
+    yield c
+    c.close()
+
+
+def _items(ctx, n=6, bands=4, seed=scenes.SEED_BATCHED):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        tris = int(np.exp(rng.uniform(np.log(12), np.log(3000))))
+        S = int(rng.integers(1, 6))
+        rays = int(rng.integers(500, 4000))
+        sc = scenes.room_or_corridor(seed * 1000 + i, tris, bands=bands, num_sources=S)
+        out.append((sc, rpr.Scene.from_scene(ctx, sc), rays, 100 + i))
+    return out
+
+
+P = dict(max_order=12, sh_order=1, num_bins=600, min_order=1, ir_rate_hz=1000.0)
+
+
+def _single(ctx, sc, scene, rays, sid, seed):
+    p = rpr.TraceParams(num_rays=rays, scene_id=sid, seed=seed, **P)
+    out = rpr.trace(scene, p, sc.listener, sc.sources)
+    return out.H.double().cpu().numpy(), out.direct_dict()
+
+
+def _check_items(b, its, ctx, seed):
+    Hb = b.H.double().cpu().numpy()
+    db = b.direct_dict()
+    for (sc, scene, rays, sid), off in zip(its, b.offsets):
+        Hs, ds = _single(ctx, sc, scene, rays, sid, seed)
+        S = sc.num_sources
+        part = Hb[off:off + S]
+        np.testing.assert_allclose(part, Hs, rtol=0, atol=1e-6 * max(np.abs(Hs).max(), 1e-30))
+        np.testing.assert_array_equal(db["energy"][off:off + S], ds["energy"])
+
+
+def test_batch_items_equal_single_scene_traces(ctx):
+    its = _items(ctx)
+    p = rpr.TraceParams(**P)
+    b = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    assert b.info().num_groups == 1
+    b.run(seed=777)
+    _check_items(b, its, ctx, 777)
+    st = b.stats_dict()
+    assert st["error"] == 0 and st["primaries"] == sum(r for _, _, r, _ in its)
+    # parameters: rp_estimate on the same H
+    pb = b.params_dict()
+    ref = rpr.estimate(ctx, b.H, b.direct, p.ir_rate_hz)
+    pr = rpr.params_to_dict(ref.cpu().numpy().tobytes(), b.S, b.B, b.K)
+    np.testing.assert_array_equal(pb["range_kind"], pr["range_kind"])
+    np.testing.assert_allclose(pb["rt60_raw"], pr["rt60_raw"], rtol=1e-12, equal_nan=True)
+
+
+def test_batch_item_matches_oracle(ctx):
+    its = _items(ctx, n=3, seed=scenes.SEED_BATCHED + 5)
+    p = rpr.TraceParams(**P)
+    b = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    b.run(seed=31)
+    Hb = b.H.double().cpu().numpy()
+    for (sc, scene, rays, sid), off in zip(its, b.offsets):
+        q = rpr.TraceParams(num_rays=rays, scene_id=sid, seed=31, **P)
+        o = pu.run_oracle(sc, q, want_hash=False)
+        l1, _ = pu.band_l1(Hb[off:off + sc.num_sources], o["H"])
+        assert l1.max() <= pu.L1_BAR, l1
+
+
+def test_graph_replay_takes_new_keys(ctx):
+    its = _items(ctx, n=4, seed=scenes.SEED_BATCHED + 9)
+    p = rpr.TraceParams(**P)
+    b = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    b.run(seed=5, use_graph=True)
+    H1 = b.H.double().cpu().numpy()
+    b.run(seed=6, use_graph=True)
+    H2 = b.H.double().cpu().numpy()
+    b.run(seed=5, use_graph=False)
+    H3 = b.H.double().cpu().numpy()
+    tol = 1e-6 * np.abs(H1).max()
+    np.testing.assert_allclose(H1, H3, rtol=0, atol=tol)
+    assert np.abs(H1 - H2).max() > 100 * tol  # a new key gives a new estimate
+    _check_items(b, its, ctx, 5)
+
+
+def test_several_groups(ctx, monkeypatch):
+    monkeypatch.setenv("RP_BATCH_HIT_BUDGET", "30000")
+    its = _items(ctx, n=5, seed=scenes.SEED_BATCHED + 13)
+    p = rpr.TraceParams(**P)
+    b = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    assert b.info().num_groups > 1
+    b.run(seed=9, use_graph=True)
+    _check_items(b, its, ctx, 9)
+
+
+def test_autotune_applies_and_caches(ctx, tmp_path):
+    its = _items(ctx, n=4, seed=scenes.SEED_BATCHED + 17)
+    p = rpr.TraceParams(**P)
+    b = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    cache = str(tmp_path / "autotune.txt")
+    t, ms = b.autotune(seed=3, cache_path=cache)
+    assert ms > 0 and t.shadow_steps in (4, 8, 16) and t.chunk_rays in (64, 256, 1024)
+    got = b.tuning()
+    assert (got.chunk_rays, got.shadow_steps) == (t.chunk_rays, t.shadow_steps)
+    assert os.path.exists(cache) and len(open(cache).read().splitlines()) == 1
+    # a second batch of the same shape takes the cached entry without timing
+    b2 = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    t2, ms2 = b2.autotune(seed=3, cache_path=cache)
+    assert (t2.chunk_rays, t2.shadow_steps, t2.paths_blocks_per_sm) == (t.chunk_rays, t.shadow_steps,
+                                                                         t.paths_blocks_per_sm)
+    assert len(open(cache).read().splitlines()) == 1
+    b2.run(seed=3)
+    _check_items(b2, its, ctx, 3)
+
+
+def test_batch_rejects_bad_input(ctx):
+    its = _items(ctx, n=2)
+    p = rpr.TraceParams(**{**P, "budget_refill": 1})
+    with pytest.raises(rpr.RprError):
+        rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    sc8 = scenes.shoebox(bands=8)
+    s8 = rpr.Scene.from_scene(ctx, sc8)
+    mixed = [(its[0][1], its[0][0].listener, its[0][0].sources, 100, 0), (s8, sc8.listener, sc8.sources, 100, 1)]
+    with pytest.raises(rpr.RprError):
+        rpr.Batch(ctx, mixed, rpr.TraceParams(**P))
