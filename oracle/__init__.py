@@ -123,6 +123,8 @@ def _bind_mlp(lib):
     lib.orc_mlp_loss_grad.restype = C.c_double
     lib.orc_adamw_step.argtypes = [C.c_int64, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_double, C.c_int]
+    lib.orc_mlp_param_count.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.orc_mlp_param_count.restype = C.c_int64
 
 
 def _d(a):
@@ -412,3 +414,53 @@ def estimate(H, e_direct, ir_rate_hz: float, dt_update: float = 0.0, tau: float 
     res["xbar"] = out[:, :, 16:16 + K].copy()
     res["range_kind"] = res["range_kind"].astype(np.int64)
     return res
+
+
+# ----------------------------------------------------------------------------
+# learned estimator (oracle/mlp.c)
+# ----------------------------------------------------------------------------
+def mlp_param_count(din: int, dh: int, nh: int, dout: int) -> int:
+    return int(_load().orc_mlp_param_count(din, dh, nh, dout))
+
+
+def mlp_forward(P, X, din: int, dh: int, nh: int, dout: int) -> np.ndarray:
+    lib = _load()
+    P = np.ascontiguousarray(P, np.float64)
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, din)
+    Y = np.zeros((X.shape[0], dout))
+    lib.orc_mlp_forward(X.shape[0], din, dh, nh, dout, _d(P), _d(X), _d(Y))
+    return Y
+
+
+def mlp_loss_grad(P, X, T, mask, din: int, dh: int, nh: int, dout: int):
+    """(loss, gradient in the parameter layout) of the masked mean-squared error."""
+    lib = _load()
+    P = np.ascontiguousarray(P, np.float64)
+    X = np.ascontiguousarray(X, np.float64).reshape(-1, din)
+    T = np.ascontiguousarray(T, np.float64).reshape(-1, dout)
+    Mk = np.ascontiguousarray(mask, np.float64).reshape(-1, dout)
+    G = np.zeros_like(P)
+    loss = lib.orc_mlp_loss_grad(X.shape[0], din, dh, nh, dout, _d(P), _d(X), _d(T), _d(Mk), _d(G))
+    return float(loss), G
+
+
+def adamw_step(p, g, m, v, lr, beta1, beta2, eps, wd, step):
+    """In-place AdamW update of float64 arrays p, m, v with gradient g."""
+    lib = _load()
+    g = np.ascontiguousarray(g, np.float64)
+    lib.orc_adamw_step(p.size, _d(p), _d(g), _d(m), _d(v), float(lr), float(beta1), float(beta2), float(eps),
+                       float(wd), int(step))
+
+
+def mlp_split(P, din: int, dh: int, nh: int, dout: int):
+    """List of (W [in, out], b [out]) views of a flat parameter vector."""
+    out, o = [], 0
+    for l in range(nh + 1):
+        i = din if l == 0 else dh
+        w = dout if l == nh else dh
+        W = P[o:o + i * w].reshape(i, w)
+        o += i * w
+        b = P[o:o + w]
+        o += w
+        out.append((W, b))
+    return out
