@@ -334,6 +334,73 @@ int rp_batch_info_get(const rp_batch *batch, rp_batch_info *out);
 int rp_batch_autotune(rp_batch *batch, uint64_t seed, const char *cache_path,
                       rp_batch_tuning *best, double *best_ms);
 
+/* ---------------------------------------------------------------------------
+ * Learned estimator: an MLP that maps the energy IR of a low-ray-count trace plus
+ * scene features to per-band decay times and direct-to-reverberant ratios, trained
+ * on IRs the method itself produces at high ray counts.  BF16 tensor-core GEMMs with
+ * FP32 accumulation, FP32 master weights, AdamW (beta1 0.9, beta2 0.999, eps 1e-8).
+ * The paper has no learned part; the plain estimator (rp_estimate) stays the
+ * reference the network is judged against.  All arrays are device memory unless
+ * stated otherwise.
+ * --------------------------------------------------------------------------- */
+typedef struct rp_mlp rp_mlp;
+
+typedef struct {
+    int32_t in_dim;     /* input features, >= 522 and a multiple of 8 (features below) */
+    int32_t hidden;     /* width of each hidden layer, multiple of 8 */
+    int32_t layers;     /* hidden layers (GELU), 1..8 */
+    int32_t out_dim;    /* outputs (16: log RT60 [s] and DRR [dB] per band) */
+    int32_t max_batch;  /* largest n of one call */
+    int32_t reserved;
+    uint64_t seed;      /* weight initialisation: uniform +-sqrt(6/(in+out)) from Philox */
+} rp_mlp_config;
+
+/* Scene features of a scene, host float[10]: log10 of the bounding-box volume,
+ * log10 of the total triangle area, area-weighted mean absorption of bands 0..7
+ * (0 beyond the scene's band count). */
+int rp_scene_features(rp_scene *scene, float *out);
+
+/* Raw features X[S][in_dim] (float) of the S sources of H[S][B][K][T] (B <= 8,
+ * 4 <= T <= 11264).  Per band b: the energy-decay (Schroeder) curve of the band's
+ * omnidirectional series, D(t) = sum over t' >= t of H[s][b][0][t'], divided by D(0);
+ * t_end = the first bin where it is below 1e-4 (-40 dB; T when it never is; at least
+ * 4); X[b*64 + i] = log10(D(t_end * (i+1) / 63) + 1e-8) for i = 0..62, D taken
+ * between bins by linear interpolation (positions clamped to T - 1.001), and
+ * X[b*64 + 63] = ln(t_end / ir_rate_hz).  An empty band (or b >= B) gives -8 and
+ * ln(4 / ir_rate_hz).  Then scene_feats[S][10] (rp_scene_features) at 512..521 and
+ * zeros up to in_dim.  The decay curve is the backward energy integral that the
+ * plain estimator fits (Section 4.2, "Reverberation Time"); the window makes the
+ * features scale-free in time.
+ * RP_ERR_TOO_LARGE when T > 11264. */
+int rp_mlp_features(rp_ctx *ctx, const float *H, int32_t num_sources, int32_t num_bands,
+                    int32_t num_sh, int32_t num_bins, float ir_rate_hz, const float *scene_feats,
+                    int32_t in_dim, float *X);
+
+int rp_mlp_create(rp_ctx *ctx, const rp_mlp_config *config, rp_mlp **out);
+int rp_mlp_destroy(rp_mlp *mlp);
+int rp_mlp_param_count(const rp_mlp *mlp, int64_t *count);
+/* FP32 master parameters, layer by layer W[in][out] then b[out]; set refreshes the
+ * BF16 copies.  Together with the AdamW state they are a training checkpoint. */
+int rp_mlp_get_params(rp_mlp *mlp, float *params);
+int rp_mlp_set_params(rp_mlp *mlp, const float *params);
+int rp_mlp_get_adam_state(rp_mlp *mlp, float *m, float *v, int32_t *step);
+int rp_mlp_set_adam_state(rp_mlp *mlp, const float *m, const float *v, int32_t step);
+/* Standardisation of inputs and targets (host arrays): x' = (x - mean) / std, y = y' std + mean. */
+int rp_mlp_set_normalization(rp_mlp *mlp, const float *in_mean, const float *in_std,
+                             const float *out_mean, const float *out_std);
+/* Standardise raw features X[n][in_dim] into the BF16 network input Xb[n][in_dim]. */
+int rp_mlp_prepare(rp_mlp *mlp, const float *X, int32_t n, void *Xb);
+/* Y[n][out_dim] = network(Xb), de-standardised when destandardize != 0. */
+int rp_mlp_forward(rp_mlp *mlp, const void *Xb, int32_t n, float *Y, int32_t destandardize);
+/* Masked MSE on standardised targets T[n][out_dim] with mask[n][out_dim] (0 or 1):
+ * loss = sum mask (y - t)^2 / max(1, sum mask); loss (device float) and the gradient
+ * in the parameter layout (or NULL). */
+int rp_mlp_loss_grad(rp_mlp *mlp, const void *Xb, const float *T, const float *mask, int32_t n,
+                     float *loss, float *grad);
+/* One AdamW step on that loss (decoupled weight decay). loss may be NULL. */
+int rp_mlp_train_step(rp_mlp *mlp, const void *Xb, const float *T, const float *mask, int32_t n,
+                      float lr, float weight_decay, float *loss);
+
 /* Size of the fixed device scratch array used by rp_trace_noalloc: 64 MiB, held by
  * every GPU that loads the library for the life of the process. */
 #define RP_NOALLOC_SCRATCH_BYTES (64ull << 20)

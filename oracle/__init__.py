@@ -123,6 +123,7 @@ def _bind_mlp(lib):
     lib.orc_mlp_loss_grad.restype = C.c_double
     lib.orc_adamw_step.argtypes = [C.c_int64, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_double, C.c_int]
+    lib.orc_mlp_features.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, dp, C.c_int, dp]
     lib.orc_mlp_param_count.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
     lib.orc_mlp_param_count.restype = C.c_int64
 
@@ -421,6 +422,17 @@ def estimate(H, e_direct, ir_rate_hz: float, dt_update: float = 0.0, tau: float 
 # ----------------------------------------------------------------------------
 def mlp_param_count(din: int, dh: int, nh: int, dout: int) -> int:
     return int(_load().orc_mlp_param_count(din, dh, nh, dout))
+
+
+def mlp_features(H, scene, ir_rate: float, in_dim: int = 528) -> np.ndarray:
+    """Network inputs [S, in_dim] of H [S, B, K, T] and scene features [S, 10]."""
+    lib = _load()
+    H = np.ascontiguousarray(H, np.float64)
+    S, B, K, T = H.shape
+    scene = np.ascontiguousarray(scene, np.float64).reshape(S, 10)
+    X = np.zeros((S, in_dim))
+    lib.orc_mlp_features(S, B, K, T, float(ir_rate), _d(H), _d(scene), in_dim, _d(X))
+    return X
 
 
 def mlp_forward(P, X, din: int, dh: int, nh: int, dout: int) -> np.ndarray:

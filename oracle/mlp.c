@@ -13,6 +13,9 @@
  * Loss: sum over samples and outputs of mask * (y - t)^2, divided by the sum of the
  * mask (at least 1).
  * AdamW: Loshchilov & Hutter (decoupled weight decay), bias-corrected moments.
+ * Features: per band the energy-decay curve (the backward energy integral of
+ * Section 4.2, "Reverberation Time"), normalised, sampled in a window that ends
+ * where it first falls below -40 dB; the window length; the scene features.
  */
 #include <math.h>
 #include <stdint.h>
@@ -163,4 +166,48 @@ void orc_adamw_step(int64_t count, double *p, const double *g, double *m, double
         const double mh = m[i] / c1, vh = v[i] / c2;
         p[i] -= lr * (mh / (sqrt(vh) + eps) + wd * p[i]);
     }
+}
+
+/* Input features of S samples of H[S][B][K][T] (only the k = 0 series is read).
+ * Per band b < 8: D(t) = sum_{t' >= t} h(t'), r(t) = D(t) / D(0) (0 when D(0) = 0);
+ * t_end = first t with r(t) < 1e-4 (T if none), at least 4; for i = 0..62 the
+ * position p = t_end (i + 1) / 63, clamped to T - 1.001, and
+ * X[b*64 + i] = log10(r(floor p) (1 - w) + r(min(floor p + 1, T - 1)) w + 1e-8) with
+ * w = p - floor p; X[b*64 + 63] = ln(t_end / ir_rate).  Bands b >= B are empty bands.
+ * scene[S][10] goes to X[512..521], zeros to the end of the row (in_dim). */
+void orc_mlp_features(int S, int B, int K, int T, double ir_rate, const double *H, const double *scene, int in_dim,
+                      double *X)
+{
+    double *r = (double *)malloc(sizeof(double) * (size_t)T);
+    for (int s = 0; s < S; ++s) {
+        double *x = X + (int64_t)s * in_dim;
+        for (int b = 0; b < 8; ++b) {
+            double D = 0.0;
+            for (int t = T - 1; t >= 0; --t) {
+                if (b < B) D += H[(((int64_t)s * B + b) * K + 0) * T + t];
+                r[t] = D;
+            }
+            const double D0 = r[0];
+            for (int t = 0; t < T; ++t) r[t] = D0 > 0.0 ? r[t] / D0 : 0.0;
+            int first = T;
+            for (int t = 0; t < T; ++t)
+                if (r[t] < 1e-4) {
+                    first = t;
+                    break;
+                }
+            const double t_end = first < 4 ? 4.0 : (double)first;
+            for (int i = 0; i < 63; ++i) {
+                double p = t_end * (i + 1) / 63.0;
+                if (p > T - 1.001) p = T - 1.001;
+                const int i0 = (int)floor(p);
+                const int i1 = i0 + 1 < T ? i0 + 1 : T - 1;
+                const double w = p - i0;
+                x[b * 64 + i] = log10(r[i0] * (1.0 - w) + r[i1] * w + 1e-8);
+            }
+            x[b * 64 + 63] = log(t_end / ir_rate);
+        }
+        for (int f = 0; f < 10; ++f) x[512 + f] = scene[(int64_t)s * 10 + f];
+        for (int f = 522; f < in_dim; ++f) x[f] = 0.0;
+    }
+    free(r);
 }

@@ -101,6 +101,11 @@ class rp_batch_info(C.Structure):
                 ("reserved", C.c_int32), ("total_rays", C.c_uint64), ("max_group_reflections", C.c_uint64)]
 
 
+class rp_mlp_config(C.Structure):
+    _fields_ = [("in_dim", C.c_int32), ("hidden", C.c_int32), ("layers", C.c_int32), ("out_dim", C.c_int32),
+                ("max_batch", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+
+
 class rp_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -132,6 +137,23 @@ _SIGS = {
     "rp_batch_info_get": ([C.c_void_p, C.POINTER(rp_batch_info)], C.c_int),
     "rp_batch_autotune": ([C.c_void_p, C.c_uint64, C.c_char_p, C.POINTER(rp_batch_tuning),
                            C.POINTER(C.c_double)], C.c_int),
+    "rp_scene_features": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+    "rp_mlp_features": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_void_p,
+                         C.c_int32, C.c_void_p], C.c_int),
+    "rp_mlp_create": ([C.c_void_p, C.POINTER(rp_mlp_config), C.POINTER(C.c_void_p)], C.c_int),
+    "rp_mlp_destroy": ([C.c_void_p], C.c_int),
+    "rp_mlp_param_count": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "rp_mlp_get_params": ([C.c_void_p, C.c_void_p], C.c_int),
+    "rp_mlp_set_params": ([C.c_void_p, C.c_void_p], C.c_int),
+    "rp_mlp_get_adam_state": ([C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)], C.c_int),
+    "rp_mlp_set_adam_state": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
+    "rp_mlp_set_normalization": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "rp_mlp_prepare": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "rp_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32], C.c_int),
+    "rp_mlp_loss_grad": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p],
+                         C.c_int),
+    "rp_mlp_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_float,
+                           C.c_void_p], C.c_int),
     "rp_trace_noalloc": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                           C.c_void_p, C.c_void_p], C.c_int),
     "rp_sync_status": ([C.c_void_p], C.c_int),
@@ -149,7 +171,8 @@ def _close_all():
     """Release library objects while the CUDA runtime is still alive (interpreter
     exit runs Python's atexit handlers before the C runtime's)."""
     global _closed
-    for obj in sorted(list(_live), key=lambda o: 0 if isinstance(o, Batch) else 1 if isinstance(o, Scene) else 2):
+    for obj in sorted(list(_live), key=lambda o: 0 if isinstance(o, (Batch, MLP)) else 1 if isinstance(o, Scene)
+                      else 2):
         try:
             obj.close()
         except Exception:
@@ -252,7 +275,8 @@ class Context:
         check(self.lib.rp_create(C.byref(h), int(device), _stream_handle(stream)), "rp_create")
         self.h = h
         self.device = device
-        self.scenes = weakref.WeakSet()
+        self.scenes = weakref.WeakSet()   # objects that hold library handles of this context
+        self.deps = weakref.WeakSet()
         _live.add(self)
 
     def set_stream(self, stream):
@@ -276,6 +300,8 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None) and not _closed:
+            for d in list(self.deps):  # batches and networks before the scenes they use
+                d.close()
             for sc in list(self.scenes):
                 sc.close()
             self.lib.rp_destroy(self.h)
@@ -473,6 +499,7 @@ class Batch:
               "rp_batch_create")
         self.h = h
         self._keep = None
+        ctx.deps.add(self)
         _live.add(self)
 
     def run(self, seed: int, use_graph: bool = False, sync: bool = True):
@@ -512,8 +539,108 @@ class Batch:
         return direct_to_dict(self.direct.cpu().numpy()[: self.S * C.sizeof(rp_direct)], self.S, self.K)
 
     def close(self):
-        if getattr(self, "h", None) and not _closed:
+        if getattr(self, "h", None) and not _closed and getattr(self.ctx, "h", None):
             self.lib.rp_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scene_features(scene: Scene) -> np.ndarray:
+    out = (C.c_float * 10)()
+    check(scene.lib.rp_scene_features(scene.h, out), "rp_scene_features")
+    return np.array(list(out), np.float32)
+
+
+def mlp_features(ctx: Context, H, scene_feats, ir_rate_hz: float, in_dim: int = 528):
+    """Raw MLP features [S, in_dim] (torch float32 on the device) of H [S, B, K, T]:
+    per band the windowed decay curve and the window length, then scene features."""
+    import torch
+    S, B, K, T = H.shape
+    sf = torch.as_tensor(np.ascontiguousarray(scene_feats, np.float32).reshape(S, 10), device=H.device)
+    X = torch.empty((S, in_dim), dtype=torch.float32, device=H.device)
+    check(ctx.lib.rp_mlp_features(ctx.h, _ptr(H), S, B, K, T, float(ir_rate_hz), _ptr(sf), in_dim, _ptr(X)),
+          "rp_mlp_features")
+    return X
+
+
+class MLP:
+    """rp_mlp: the learned estimator (BF16 tensor-core GEMMs, FP32 masters, AdamW)."""
+
+    def __init__(self, ctx: Context, in_dim=528, hidden=256, layers=3, out_dim=16, max_batch=4096, seed=1):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.cfg = rp_mlp_config(in_dim, hidden, layers, out_dim, max_batch, 0, seed)
+        h = C.c_void_p()
+        check(self.lib.rp_mlp_create(ctx.h, C.byref(self.cfg), C.byref(h)), "rp_mlp_create")
+        self.h = h
+        n = C.c_int64()
+        check(self.lib.rp_mlp_param_count(h, C.byref(n)), "rp_mlp_param_count")
+        self.nparams = n.value
+        ctx.deps.add(self)
+        _live.add(self)
+
+    def params(self):
+        import torch
+        p = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        check(self.lib.rp_mlp_get_params(self.h, _ptr(p)), "rp_mlp_get_params")
+        torch.cuda.synchronize()
+        return p
+
+    def set_params(self, p):
+        import torch
+        p = torch.as_tensor(p, dtype=torch.float32, device="cuda").contiguous()
+        check(self.lib.rp_mlp_set_params(self.h, _ptr(p)), "rp_mlp_set_params")
+        torch.cuda.synchronize()
+
+    def adam_state(self):
+        import torch
+        m = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        v = torch.empty_like(m)
+        step = C.c_int32()
+        check(self.lib.rp_mlp_get_adam_state(self.h, _ptr(m), _ptr(v), C.byref(step)), "rp_mlp_get_adam_state")
+        torch.cuda.synchronize()
+        return m, v, step.value
+
+    def set_adam_state(self, m, v, step):
+        check(self.lib.rp_mlp_set_adam_state(self.h, _ptr(m), _ptr(v), int(step)), "rp_mlp_set_adam_state")
+
+    def set_normalization(self, in_mean, in_std, out_mean, out_std):
+        a = [np.ascontiguousarray(x, np.float32) for x in (in_mean, in_std, out_mean, out_std)]
+        check(self.lib.rp_mlp_set_normalization(self.h, *[x.ctypes.data_as(C.c_void_p) for x in a]),
+              "rp_mlp_set_normalization")
+
+    def prepare(self, X):
+        import torch
+        Xb = torch.empty(X.shape, dtype=torch.bfloat16, device="cuda")
+        check(self.lib.rp_mlp_prepare(self.h, _ptr(X), X.shape[0], _ptr(Xb)), "rp_mlp_prepare")
+        return Xb
+
+    def forward(self, Xb, destandardize=True):
+        import torch
+        Y = torch.empty((Xb.shape[0], self.cfg.out_dim), dtype=torch.float32, device="cuda")
+        check(self.lib.rp_mlp_forward(self.h, _ptr(Xb), Xb.shape[0], _ptr(Y), int(destandardize)), "rp_mlp_forward")
+        return Y
+
+    def loss_grad(self, Xb, T, mask):
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        g = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        check(self.lib.rp_mlp_loss_grad(self.h, _ptr(Xb), _ptr(T), _ptr(mask), Xb.shape[0], _ptr(loss), _ptr(g)),
+              "rp_mlp_loss_grad")
+        return loss, g
+
+    def train_step(self, Xb, T, mask, lr, weight_decay=0.0, loss=None):
+        check(self.lib.rp_mlp_train_step(self.h, _ptr(Xb), _ptr(T), _ptr(mask), Xb.shape[0], float(lr),
+                                         float(weight_decay), _ptr(loss)), "rp_mlp_train_step")
+
+    def close(self):
+        if getattr(self, "h", None) and not _closed and getattr(self.ctx, "h", None):
+            self.lib.rp_mlp_destroy(self.h)
         self.h = None
 
     def __del__(self):

@@ -140,9 +140,18 @@ def grid_quad_mesh(origin, du, dv, nu: int, nv: int):
     return verts, np.array(tris, dtype=np.int64)
 
 
-def _materials(rng, n_mat: int, bands: int, a_lo=0.05, a_hi=0.4, s_lo=0.1, s_hi=0.9):
+def _materials(rng, n_mat: int, bands: int, a_lo=0.05, a_hi=0.4, s_lo=0.1, s_hi=0.9, s_spread=None):
+    """Per-band absorption U[a_lo, a_hi].  Scattering U[s_lo, s_hi] drawn per band, or,
+    with s_spread set, a base value plus a rise of at most s_spread linear over the
+    bands (scattering of real surfaces grows smoothly with frequency)."""
     absorption = rng.uniform(a_lo, a_hi, size=(n_mat, bands)).astype(np.float32)
-    scattering = rng.uniform(s_lo, s_hi, size=(n_mat, bands)).astype(np.float32)
+    if s_spread is None:
+        scattering = rng.uniform(s_lo, s_hi, size=(n_mat, bands)).astype(np.float32)
+    else:
+        base = rng.uniform(s_lo, s_hi - s_spread, size=(n_mat, 1))
+        rise = rng.uniform(0.0, s_spread, size=(n_mat, 1))
+        ramp = np.linspace(0.0, 1.0, bands)[None, :] if bands > 1 else np.zeros((1, 1))
+        scattering = (base + rise * ramp).astype(np.float32)
     return absorption, scattering
 
 
@@ -234,10 +243,10 @@ def furnished_hall(seed: int = SEED_MEDIUM, n_boxes: int = 2000, bands: int = 8,
 
 
 def room_or_corridor(seed: int, target_tris: int, bands: int = 8, num_sources: int = 1,
-                     kind: str | None = None, n_mat: int = 8) -> Scene:
+                     kind: str | None = None, n_mat: int = 8, s_spread: float | None = None) -> Scene:
     """Batched / learned workload: either a room (outer box plus interior boxes) or a
     corridor (a long box with side rooms opened into it by box 'walls'), with about
-    target_tris triangles (at least 12)."""
+    target_tris triangles (at least 12).  s_spread: see _materials."""
     rng = np.random.default_rng(seed)
     if kind is None:
         kind = "room" if rng.uniform() < 0.5 else "corridor"
@@ -280,7 +289,7 @@ def room_or_corridor(seed: int, target_tris: int, bands: int = 8, num_sources: i
             mb.add_box(lo, hi, 1 + i % (n_mat - 1))
     verts, tris, mats = mb.finish()
     boxes = np.array(boxes).reshape(-1, 2, 3)
-    a, s = _materials(rng, n_mat, bands)
+    a, s = _materials(rng, n_mat, bands, s_spread=s_spread)
     margin = min(0.5, 0.2 * float(size.min()))
     pts = _free_points(rng, 1 + num_sources, np.zeros(3), size, boxes, margin, 0.3,
                        min_sep=min(1.0, 0.3 * float(size.min())))
