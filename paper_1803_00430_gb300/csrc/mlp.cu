@@ -60,8 +60,10 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 // C[M][N] = op(A)[M][K] x op(B)[K][N] with a fused epilogue.
 //   A: AT ? stored [K][M] (lda) : stored [M][K]
 //   B: BT ? stored [N][K] (ldb) : stored [K][N]
+// blockIdx.z takes the K range [z kchunk, (z+1) kchunk) (split K, EPI_F32 only): its
+// partial product goes to Cf + z M ldc and k_reduce_splits adds the partials.
 template <bool AT, bool BT, int EPI>
-__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *__restrict__ A, int lda,
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, int lda,
                                               const bf16 *__restrict__ Bm, int ldb, float *__restrict__ Cf,
                                               bf16 *__restrict__ Cb, int ldc, const float *__restrict__ bias,
                                               const float *__restrict__ Zin, float *__restrict__ Zout)
@@ -72,6 +74,8 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
     const int wm = warp >> 1, wn = warp & 1;
     const int g = lane >> 2, t4 = lane & 3;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    if (EPI == EPI_F32) Cf += (size_t)blockIdx.z * M * ldc;
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
     const bf16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int k0 = kbeg; k0 < kend; k0 += 32) {
         for (int e = tid; e < 64 * 32; e += 128) {
             int mm, kk;
             if (!AT) {
@@ -92,7 +96,7 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
             }
             const int gm = m0 + mm, gk = k0 + kk;
             bf16 v = zero;
-            if (gm < M && gk < K) v = AT ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+            if (gm < M && gk < kend) v = AT ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
             As[mm][kk] = v;
         }
         for (int e = tid; e < 64 * 32; e += 128) {
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *_
             }
             const int gn = n0 + nn, gk = k0 + kk;
             bf16 v = zero;
-            if (gn < N && gk < K) v = BT ? Bm[(size_t)gn * ldb + gk] : Bm[(size_t)gk * ldb + gn];
+            if (gn < N && gk < kend) v = BT ? Bm[(size_t)gn * ldb + gk] : Bm[(size_t)gk * ldb + gn];
             Bs[nn][kk] = v;
         }
         __syncthreads();
@@ -164,21 +168,85 @@ void gemm(cudaStream_t st, int M, int N, int K, const bf16 *A, int lda, const bf
           int ldc, const float *bias = nullptr, const float *Zin = nullptr, float *Zout = nullptr)
 {
     const dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<AT, BT, EPI><<<grid, 128, 0, st>>>(M, N, K, A, lda, B, ldb, Cf, Cb, ldc, bias, Zin, Zout);
+    k_gemm<AT, BT, EPI><<<grid, 128, 0, st>>>(M, N, K, K, A, lda, B, ldb, Cf, Cb, ldc, bias, Zin, Zout);
 }
 
-// sums of the columns of an M x N matrix (bias gradients)
+constexpr int MAX_SPLIT = 16;    // K splits of a weight-gradient GEMM
+constexpr int COLSUM_PARTS = 64;  // row chunks of a column sum
+
+// out[i] = sum over z of part[z][i], z in order (deterministic)
+__global__ void k_reduce_splits(long long count, int splits, const float *__restrict__ part, float *__restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * count + i];
+        out[i] = s;
+    }
+}
+
+// Weight gradient C[M][N] = A^T B with K = the batch: few output tiles and a long K,
+// so K is split until the grid covers the SMs about twice.
+void gemm_wgrad(cudaStream_t st, int num_sms, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
+                float *C, float *part)
+{
+    const dim3 tiles((N + 63) / 64, (M + 63) / 64);
+    const int want = (2 * std::max(num_sms, 1) + (int)(tiles.x * tiles.y) - 1) / (int)(tiles.x * tiles.y);
+    const int splits = std::max(1, std::min({MAX_SPLIT, want, (K + 255) / 256}));
+    if (splits == 1) {
+        k_gemm<true, false, EPI_F32><<<tiles, 128, 0, st>>>(M, N, K, K, A, lda, B, ldb, C, nullptr, N, nullptr,
+                                                           nullptr, nullptr);
+        return;
+    }
+    const int kchunk = ((K + splits - 1) / splits + 31) / 32 * 32;
+    const int used = (K + kchunk - 1) / kchunk;
+    k_gemm<true, false, EPI_F32><<<dim3(tiles.x, tiles.y, used), 128, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, part,
+                                                                              nullptr, N, nullptr, nullptr, nullptr);
+    const long long cnt = (long long)M * N;
+    k_reduce_splits<<<(int)std::min<long long>((cnt + 255) / 256, 4096), 256, 0, st>>>(cnt, used, part, C);
+}
+
 __device__ __forceinline__ float to_f(bf16 x) { return __bfloat162float(x); }
 __device__ __forceinline__ float to_f(float x) { return x; }
 
+// stage 1: block (x, r) sums rows [r rows_per, (r+1) rows_per) of columns
+// [32 x, 32 x + 32): thread (c, y) takes every 8th row, then the 8 partial sums of a
+// column are added in order; stage 2 adds the row chunks in order (deterministic).
 template <typename T>
-__global__ void k_colsum(int M, int N, const T *__restrict__ X, float *__restrict__ out)
+__global__ void k_colsum_part(int M, int N, int rows_per, const T *__restrict__ X, float *__restrict__ part)
+{
+    __shared__ float sh[8][33];
+    const int n = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * rows_per, r1 = min(M, r0 + rows_per);
+    float s = 0.f;
+    if (n < N)
+        for (int m = r0 + threadIdx.y; m < r1; m += 8) s += to_f(X[(size_t)m * N + n]);
+    sh[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float t = 0.f;
+        for (int y = 0; y < 8; ++y) t += sh[y][threadIdx.x];
+        part[(size_t)blockIdx.y * N + n] = t;
+    }
+}
+
+__global__ void k_colsum_final(int N, int parts, const float *__restrict__ part, float *__restrict__ out)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += to_f(X[(size_t)m * N + n]);
+    for (int r = 0; r < parts; ++r) s += part[(size_t)r * N + n];
     out[n] = s;
+}
+
+// sums of the columns of an M x N matrix (bias gradients)
+template <typename T>
+void colsum(cudaStream_t st, int M, int N, const T *X, float *out, float *part)
+{
+    const int parts = std::max(1, std::min(COLSUM_PARTS, (M + 255) / 256));
+    const int rows_per = (M + parts - 1) / parts;
+    k_colsum_part<T><<<dim3((N + 31) / 32, parts), dim3(32, 8), 0, st>>>(M, N, rows_per, X, part);
+    k_colsum_final<<<(N + 127) / 128, 128, 0, st>>>(N, parts, part, out);
 }
 
 __global__ void k_mask_sum(int count, const float *__restrict__ mask, float *__restrict__ out)
@@ -361,6 +429,7 @@ struct rp_mlp {
     float *in_mean = nullptr, *in_istd = nullptr, *out_mean = nullptr, *out_std = nullptr;
     float *Z = nullptr, *Y = nullptr, *scratch = nullptr;         // workspace for max_batch
     bf16 *Act = nullptr, *dA = nullptr, *dB = nullptr, *dY = nullptr;
+    float *part = nullptr, *cpart = nullptr;  // split-K and column-sum partials
     int step = 0;
 };
 
@@ -412,8 +481,9 @@ void backward(rp_mlp *mp, const bf16 *X, const float *Tg, const float *mask, int
     // output layer
     const bf16 *a_last = L > 0 ? mp->Act + (size_t)(L - 1) * c.max_batch * H : X;
     const int w_last = L > 0 ? H : c.in_dim;
-    gemm<true, false, EPI_F32>(st, w_last, O, n, a_last, w_last, mp->dY, O, mp->g + mp->w_off[L], nullptr, O);
-    k_colsum<bf16><<<(O + 127) / 128, 128, 0, st>>>(n, O, mp->dY, mp->g + mp->b_off[L]);
+    const int sms = mp->ctx->num_sms;
+    gemm_wgrad(st, sms, w_last, O, n, a_last, w_last, mp->dY, O, mp->g + mp->w_off[L], mp->part);
+    colsum<bf16>(st, n, O, mp->dY, mp->g + mp->b_off[L], mp->cpart);
     const bf16 *delta = mp->dY;
     int dw = O;
     bf16 *bufs[2] = {mp->dA, mp->dB};
@@ -424,8 +494,8 @@ void backward(rp_mlp *mp, const bf16 *X, const float *Tg, const float *mask, int
                                      mp->Z + (size_t)l * c.max_batch * H);
         const bf16 *a_in = l > 0 ? mp->Act + (size_t)(l - 1) * c.max_batch * H : X;
         const int w_in = l > 0 ? H : c.in_dim;
-        gemm<true, false, EPI_F32>(st, w_in, H, n, a_in, w_in, dl, H, mp->g + mp->w_off[l], nullptr, H);
-        k_colsum<bf16><<<(H + 127) / 128, 128, 0, st>>>(n, H, dl, mp->g + mp->b_off[l]);
+        gemm_wgrad(st, sms, w_in, H, n, a_in, w_in, dl, H, mp->g + mp->w_off[l], mp->part);
+        colsum<bf16>(st, n, H, dl, mp->g + mp->b_off[l], mp->cpart);
         delta = dl;
         dw = H;
     }
@@ -490,6 +560,9 @@ int rp_mlp_create(rp_ctx *ctx, const rp_mlp_config *cfg, rp_mlp **out)
         (e = cudaMalloc(&mp->dA, sizeof(bf16) * act)) || (e = cudaMalloc(&mp->dB, sizeof(bf16) * act)) ||
         (e = cudaMalloc(&mp->Y, sizeof(float) * (size_t)cfg->max_batch * cfg->out_dim)) ||
         (e = cudaMalloc(&mp->dY, sizeof(bf16) * (size_t)cfg->max_batch * cfg->out_dim)) ||
+        (e = cudaMalloc(&mp->part, sizeof(float) * MAX_SPLIT * (size_t)std::max(cfg->in_dim, cfg->hidden) *
+                                       std::max(cfg->hidden, cfg->out_dim))) ||
+        (e = cudaMalloc(&mp->cpart, sizeof(float) * COLSUM_PARTS * (size_t)std::max(cfg->hidden, cfg->out_dim))) ||
         (e = cudaMalloc(&mp->scratch, sizeof(float) * 16))) {
         rc = mrc(e);
         goto fail;
@@ -527,7 +600,7 @@ int rp_mlp_destroy(rp_mlp *mp)
     for (void *q : {(void *)mp->p, (void *)mp->g, (void *)mp->m, (void *)mp->v, (void *)mp->pb, (void *)mp->wmap,
                     (void *)mp->in_mean, (void *)mp->in_istd, (void *)mp->out_mean, (void *)mp->out_std,
                     (void *)mp->Z, (void *)mp->Act, (void *)mp->dA, (void *)mp->dB, (void *)mp->Y, (void *)mp->dY,
-                    (void *)mp->scratch})
+                    (void *)mp->part, (void *)mp->cpart, (void *)mp->scratch})
         cudaFree(q);
     delete mp;
     return RP_OK;

@@ -277,6 +277,47 @@ def sweep(ctx: rpr.Context, mlp: rpr.MLP, test: Dataset, ray_counts, test_scenes
     return out
 
 
+def mlp_flops_per_sample(in_dim: int = IN_DIM, hidden: int = 256, layers: int = 3, out_dim: int = OUT_DIM) -> float:
+    """Multiply-adds x 2 of one sample's forward pass through the dense layers."""
+    widths = [in_dim] + [hidden] * layers + [out_dim]
+    return 2.0 * sum(a * b for a, b in zip(widths[:-1], widths[1:]))
+
+
+def mlp_throughput(ctx: rpr.Context, batches=(512, 4096, 16384, 65536), reps: int = 20, seed: int = 3) -> dict:
+    """Achieved TFLOP/s of the network's forward pass and of a training step (forward,
+    backward and AdamW; counted as 3 x the forward flops) at each batch size, from
+    CUDA events on the context's stream around `reps` back-to-back calls."""
+    import torch
+    out = {}
+    rng = np.random.default_rng(seed)
+    for n in batches:
+        mlp = rpr.MLP(ctx, in_dim=IN_DIM, out_dim=OUT_DIM, max_batch=n, seed=seed)
+        X = torch.tensor(rng.normal(size=(n, IN_DIM)), dtype=torch.float32, device="cuda")
+        Xb = mlp.prepare(X)
+        T = torch.tensor(rng.normal(size=(n, OUT_DIM)), dtype=torch.float32, device="cuda")
+        M = torch.ones((n, OUT_DIM), dtype=torch.float32, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        st = torch.cuda.current_stream()
+        res = {}
+        for name, fn in (("forward", lambda: mlp.forward(Xb, destandardize=False)),
+                         ("train_step", lambda: mlp.train_step(Xb, T, M, 1e-4, 0.0, loss))):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(reps):
+                fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            flops = mlp_flops_per_sample() * n * (3.0 if name == "train_step" else 1.0)
+            res[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+        out[int(n)] = res
+        mlp.close()
+    return out
+
+
 def main(argv=None):
     """Train the network on the method's own IRs and sweep ray counts; prints JSON."""
     import argparse
@@ -293,9 +334,17 @@ def main(argv=None):
     ap.add_argument("--rays", type=int, nargs="+", default=[1000, 2000, 4000, 8000, 16000, 32000])
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--throughput-only", action="store_true", help="time the network's kernels on random data")
+    ap.add_argument("--batches", type=int, nargs="+", default=[512, 4096, 16384, 65536])
     a = ap.parse_args(argv)
     t0 = time.time()
-    ctx = rpr.Context(a.device)
+    import torch
+    ctx = rpr.Context(a.device, torch.cuda.current_stream())
+    if a.throughput_only:
+        print(json.dumps({"mlp_flops_per_sample": mlp_flops_per_sample(),
+                          "per_batch": mlp_throughput(ctx, a.batches)}))
+        ctx.close()
+        return
     train = make_dataset(ctx, a.train, seed=101, low_rays=a.train_rays, high_rays=a.train_label_rays,
                          copies=a.copies)
     t_data = time.time() - t0

@@ -75,10 +75,11 @@ def divergence(hg, ho):
 
 def param_errors(pg, po):
     ok = (po["range_kind"] > 0) & (pg["range_kind"] > 0)
-    rt = np.abs(pg["rt60_raw"] - po["rt60_raw"]) / po["rt60_raw"]
-    gr = np.abs(pg["g_reverb"] - po["g_reverb"]) / po["g_reverb"]
     fin = np.isfinite(po["drr_db"]) & np.isfinite(pg["drr_db"])
-    drr = np.abs(pg["drr_db"] - po["drr_db"])
+    with np.errstate(invalid="ignore", divide="ignore"):  # NaN/inf entries are masked below
+        rt = np.abs(pg["rt60_raw"] - po["rt60_raw"]) / po["rt60_raw"]
+        gr = np.abs(pg["g_reverb"] - po["g_reverb"]) / po["g_reverb"]
+        drr = np.abs(pg["drr_db"] - po["drr_db"])
     return {
         "rt60": float(np.max(rt[ok])) if ok.any() else 0.0,
         "g_reverb": float(np.max(gr[ok])) if ok.any() else 0.0,

@@ -37,7 +37,7 @@ def _oracle_params(mlp, P):
 
 
 def _setup(ctx, n=96, seed=0):
-    mlp = rpr.MLP(ctx, max_batch=256, seed=seed + 11)
+    mlp = rpr.MLP(ctx, max_batch=max(256, n), seed=seed + 11)
     rng = np.random.default_rng(seed)
     X = torch.tensor(rng.normal(size=(n, DIN)), dtype=torch.float32, device="cuda")
     Xb = mlp.prepare(X)  # identity normalisation
@@ -68,6 +68,26 @@ def test_gradients_match_oracle(ctx):
     for (Wg, bg), (Wo, bo) in zip(oracle.mlp_split(g, DIN, DH, NH, DOUT), oracle.mlp_split(go, DIN, DH, NH, DOUT)):
         assert np.linalg.norm(Wg - Wo) / np.linalg.norm(Wo) <= 2e-2
         assert np.linalg.norm(bg - bo) / np.linalg.norm(bo) <= 2e-2
+
+
+def test_split_k_gradients_match_oracle(ctx):
+    """1100 samples: the weight-gradient GEMMs split the batch dimension (5 ragged
+    chunks) and the bias gradients sum it in row chunks."""
+    mlp, X, Xb, T, M = _setup(ctx, n=1100, seed=5)
+    loss, g = mlp.loss_grad(Xb, T, M)
+    g = g.double().cpu().numpy()
+    Po = _oracle_params(mlp, mlp.params())
+    lo, go = oracle.mlp_loss_grad(Po, Xb.double().cpu().numpy(), T.double().cpu().numpy(),
+                                  M.double().cpu().numpy(), DIN, DH, NH, DOUT)
+    assert float(loss.item()) == pytest.approx(lo, rel=2e-2)
+    cos = float(g @ go / (np.linalg.norm(g) * np.linalg.norm(go)))
+    assert cos >= 0.999, cos
+    for (Wg, bg), (Wo, bo) in zip(oracle.mlp_split(g, DIN, DH, NH, DOUT), oracle.mlp_split(go, DIN, DH, NH, DOUT)):
+        assert np.linalg.norm(Wg - Wo) / np.linalg.norm(Wo) <= 2e-2
+        assert np.linalg.norm(bg - bo) / np.linalg.norm(bo) <= 2e-2
+    # the same call twice gives the same bits (fixed reduction order)
+    _, g2 = mlp.loss_grad(Xb, T, M)
+    np.testing.assert_array_equal(g2.double().cpu().numpy(), g)
 
 
 def test_adamw_step_matches_oracle(ctx):
