@@ -41,6 +41,10 @@ WORKLOAD_NAME = ("medium: furnished hall 40x30x12 m + 2000 boxes (24,012 tris), 
                  "200k rays x 64 reflections, IR 2 s @ 1 kHz, SH order 2")
 FLOPS_PER_NODE = 24.0   # slab tests of two children
 FLOPS_PER_TRI = 27.0    # Moller-Trumbore
+# DRAM bytes (read + write) of one k_shadow launch in an ncu capture of the same
+# update at 30,000 primaries, and the shadow rays that launch traced; a full-size
+# launch is credited with the same bytes per shadow ray.
+NCU_SHADOW_DRAM = (133_543_424 + 28_790_272, 18_878_384)
 
 
 def _peaks():
@@ -302,6 +306,8 @@ def main():
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / avg_s / 1e12
+    traffic = (NCU_SHADOW_DRAM[0] * st["shadow_rays"] / NCU_SHADOW_DRAM[1]
+               if name == "shadow" and not args.fp32_paths else None)
     shares = {k: round(v[1] / sum(x[1] for x in kt.values()), 4) for k, v in kt.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -315,7 +321,9 @@ def main():
         "updates_per_s": ws * 1000.0 / ms_step,
         "closest_hit_segments_per_step": st["segments"], "shadow_rays_per_step": st["shadow_rays"],
         "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                     "traffic_note": "DRAM bytes per launch, from an ncu capture at 30k primaries scaled by "
+                                     "shadow rays" if traffic else None,
                      "peak_note": f"FP32 FMA peak 152 SMs x 128 lanes x 2 at the median sampled SM clock "
                                   f"{sm_mhz:.0f} MHz (derived, not measured)",
                      "algorithmic": f"{FLOPS_PER_NODE:.0f} flop/node visit + {FLOPS_PER_TRI:.0f} flop/triangle test, "

@@ -28,37 +28,51 @@ __global__ void k_count(TraceWork w)
 }
 
 // exclusive scan of cnt[0..n) into off[0..n], off[n] = total; one block of 1024
-__global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ cnt, uint32_t *__restrict__ off, int n)
+// exclusive scan of cnt[0..n) into off[0..n] (off[n] = total; off may be cnt): one
+// block of 1024 threads walks the array in tiles of 4096, each thread taking 4
+// consecutive counts, with the running total carried from tile to tile.
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t *cnt, uint32_t *off, int n)
 {
     __shared__ uint32_t warp_sums[32];
-    const int t = threadIdx.x;
-    const int per = (n + 1023) / 1024;
-    const int b = t * per, e = min(n, b + per);
-    uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += cnt[i];
-    const int lane = t & 31, wid = t >> 5;
-    uint32_t x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[wid] = x;
+    __shared__ uint32_t carry;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) carry = 0;
     __syncthreads();
-    if (wid == 0) {
-        uint32_t v = warp_sums[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, v, o);
-            if (lane >= o) v += y;
+    for (int base = 0; base < n; base += 4096) {
+        const int i0 = base + 4 * t;
+        uint32_t v[4], s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = i0 + k < n ? cnt[i0 + k] : 0u;
+            s += v[k];
         }
-        warp_sums[lane] = v;
+        uint32_t x = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t ws = warp_sums[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, ws, o);
+                if (lane >= o) ws += y;
+            }
+            warp_sums[lane] = ws;
+        }
+        __syncthreads();
+        uint32_t run = carry + x - s + (wid > 0 ? warp_sums[wid - 1] : 0u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < n) off[i0 + k] = run;
+            run += v[k];
+        }
+        __syncthreads();  // every thread has read carry and warp_sums
+        if (t == 1023) carry = run;
+        __syncthreads();
     }
-    __syncthreads();
-    uint32_t run = x - s + (wid > 0 ? warp_sums[wid - 1] : 0u);
-    for (int i = b; i < e; ++i) {
-        off[i] = run;
-        run += cnt[i];
-    }
-    if (t == 1023) off[n] = run;
+    if (t == 0) off[n] = carry;
 }
 
 __global__ void k_scatter(TraceWork w)
@@ -184,10 +198,12 @@ __global__ void k_direct_add(TraceWork w)
 
 void launch_count(const TraceWork &w, int blocks, cudaStream_t st) { k_count<<<blocks, 256, 0, st>>>(w); }
 
-void launch_scan(const TraceWork &w, cudaStream_t st)
+void launch_scan_u32(const uint32_t *cnt, uint32_t *off, int n, cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(w.cnt, w.off, w.k.S * w.k.T);
+    k_scan<<<1, 1024, 0, st>>>(cnt, off, n);
 }
+
+void launch_scan(const TraceWork &w, cudaStream_t st) { launch_scan_u32(w.cnt, w.off, w.k.S * w.k.T, st); }
 
 void launch_scatter(const TraceWork &w, int blocks, cudaStream_t st) { k_scatter<<<blocks, 256, 0, st>>>(w); }
 

@@ -148,6 +148,10 @@ int reserve_batch(rp_batch *b)
     if ((r = grow(c, c->hit_n, z.hit_cap * sizeof(float4)))) return r;
     if ((r = grow(c, c->hit_ws, z.hit_cap * B * sizeof(float)))) return r;
     if ((r = grow(c, c->hit_rid, z.hit_cap * sizeof(uint32_t)))) return r;
+    if ((r = grow(c, c->hord_cell, z.hit_cap * sizeof(uint32_t)))) return r;
+    if ((r = grow(c, c->hord_perm, z.hit_cap * sizeof(uint32_t)))) return r;
+    const long long cells = std::max(1ll << 18, 8ll * b->max_jobs) + 1;  // >= hit_order_cells of any group
+    if ((r = grow(c, c->hord_cnt, (size_t)cells * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->rec_key, z.rec_cap * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->rec_rid, z.rec_cap * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->rec_e, z.rec_cap * B * sizeof(float)))) return r;
@@ -188,6 +192,8 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
     w.job0 = b->h_jobs[g.job_begin];
     w.jobs = b->d_jobs + g.job_begin;
     w.njobs = g.job_end - g.job_begin;
+    w.horder = {(uint32_t *)c->hord_cell.p, (uint32_t *)c->hord_perm.p, (uint32_t *)c->hord_cnt.p,
+                hit_order_bits(w.njobs), (int)hit_order_cells(w.njobs)};
     w.js = (JobState *)c->js.p;
     w.wave_mode = 0;
     w.chunks = b->d_chunks + g.chunk_begin;
@@ -397,8 +403,7 @@ int rp_batch_create(rp_ctx *c, const rp_batch_item *items, int32_t n, const rp_t
         const rp_batch_item &it = items[i];
         SceneJob J;
         const rp_scene *sc = it.scene;
-        J.sc = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris, sc->num_nodes,
-                sc->B, sc->tmin, sc->tmin_d};
+        J.sc = make_view(sc);
         J.first_ray = it.first_ray;
         J.num_rays = it.num_rays;
         J.hit_off = 0;

@@ -38,7 +38,8 @@ struct rp_ctx {
     int shadow_steps = 8;
     unsigned long long ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
     // workspace
-    Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, Hs, He, src, ctr,
+    Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, hord_cell, hord_perm, hord_cnt, rec_key, rec_rid, rec_e, perm, rerun,
+        cnt, off, cur, Hs, He, src, ctr,
         stats, H, direct, params, state, jobs, js, chunks, src_job;
     // profiling
     bool prof = false;
@@ -58,3 +59,14 @@ struct rp_scene {
     uint32_t *thr = nullptr;
 };
 
+// the device view of a scene that a trace step uses
+inline rp::SceneView make_view(const rp_scene *sc)
+{
+    rp::SceneView v = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris,
+                       sc->num_nodes, sc->B, sc->tmin, sc->tmin_d, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    for (int a = 0; a < 3; ++a) {
+        v.lo[a] = sc->lo[a];
+        v.ext[a] = sc->hi[a] - sc->lo[a];
+    }
+    return v;
+}

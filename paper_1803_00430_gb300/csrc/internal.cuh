@@ -38,6 +38,8 @@ struct SceneView {
     int B;
     float tmin;     // self-intersection guard used by FP32 queries
     double tmin_d;  // the same guard for FP64 re-decisions
+    float lo[3];    // bounding box of the vertices (cells of the shadow-ray order)
+    float ext[3];
 };
 
 // One scene of a trace step.  A single-scene step is a batch of one job; a
@@ -62,6 +64,7 @@ struct JobState {
     unsigned long long wave_begin;  // first ray id of the current wave
     unsigned long long wave_count;  // primaries of the current wave
     unsigned long long item_off;    // first shadow item of the job
+    unsigned long long hit_prefix;  // stored reflections of the earlier jobs
     unsigned long long segments;    // closest-hit rays traced
     unsigned long long mfp_count;
     double mfp_sum;
@@ -82,7 +85,8 @@ struct TraceCounters {
     unsigned long long next_item;    // shadow items fetched in the current chunk
     unsigned long long n_rerun;      // shadow items queued for an FP64 decision (current chunk)
     unsigned long long total_items; // shadow items of the step (sum over jobs of hits x sources)
-    unsigned long long pad[3];
+    unsigned long long total_hits;  // stored reflections of the step (sum over jobs)
+    unsigned long long pad[2];
 };
 
 // Contribution records: key = (global source - first source of the group) * T + bin,
@@ -139,6 +143,26 @@ struct BvhOut {
 // cudaError_t; device-detected input errors go to *status.
 cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStream_t st);
 
+// The step's stored reflections sorted by cell (job, Morton code of the position on
+// a 2^bits grid per axis over the job's scene box), so that the shadow rays a warp
+// traces start close together and aim at the same source.
+struct HitOrder {
+    uint32_t *cell;  // [total hits] cell of the flattened reflection f
+    uint32_t *perm;  // [total hits] reflection slot, in cell order (jobs in order)
+    uint32_t *cnt;   // [ncells + 1] counts, then cursors
+    int bits;        // grid bits per axis
+    int ncells;      // njobs x 2^(3 bits)
+};
+
+// grid bits per axis for njobs jobs: about 2^18 cells in all, 1..6 bits
+inline int hit_order_bits(int njobs)
+{
+    int bits = 6;
+    while (bits > 1 && (long long)njobs << (3 * bits) > (1ll << 18)) --bits;
+    return bits;
+}
+inline long long hit_order_cells(int njobs) { return (long long)std::max(njobs, 1) << (3 * hit_order_bits(njobs)); }
+
 struct TraceWork {
     SceneJob job0;         // the first (in single-job steps the only) job, by value
     const SceneJob *jobs;  // [njobs], device
@@ -170,16 +194,19 @@ struct TraceWork {
     unsigned long long rerun_cap;
     int num_sms;
     int shadow_steps;  // node visits a shadow lane makes between refills
+    HitOrder horder;   // reflections in spatial order for coherent shadow rays
 };
 
 void launch_setup(const TraceWork &w, int wave, cudaStream_t st);
 void launch_paths(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_item_prefix(const TraceWork &w, cudaStream_t st);
+void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_shadow_exact(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_direct(const TraceWork &w, cudaStream_t st);
 void launch_count(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_scan(const TraceWork &w, cudaStream_t st);
+void launch_scan_u32(const uint32_t *cnt, uint32_t *off, int n, cudaStream_t st);
 void launch_scatter(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_accum(const TraceWork &w, int first_chunk, int blocks, cudaStream_t st);
 void launch_finalize(const TraceWork &w, cudaStream_t st);

@@ -105,7 +105,9 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     const unsigned long long o_src = cv.take<float4>(S + 1), o_raw = cv.take<float>(3ull * (S + 1));
     const unsigned long long o_hp = cv.take<float4>(z.hit_cap), o_hl = cv.take<float4>(z.hit_cap),
                              o_hn = cv.take<float4>(z.hit_cap), o_hw = cv.take<float>(z.hit_cap * B),
-                             o_hr = cv.take<uint32_t>(z.hit_cap);
+                             o_hr = cv.take<uint32_t>(z.hit_cap), o_hc = cv.take<uint32_t>(z.hit_cap),
+                             o_hq = cv.take<uint32_t>(z.hit_cap),
+                             o_hk = cv.take<uint32_t>((unsigned long long)hit_order_cells(1) + 1);
     const unsigned long long o_cnt = cv.take<uint32_t>(z.keys), o_off = cv.take<uint32_t>(z.keys + 1),
                              o_cur = cv.take<uint32_t>(z.keys);
     const unsigned long long o_hs = cv.take<float>(z.cells), o_he = cv.take<float>(z.cells);
@@ -144,8 +146,7 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
 
     TraceWork w;
     SceneJob job;
-    job.sc = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris,
-              sc->num_nodes, sc->B, sc->tmin, sc->tmin_d};
+    job.sc = make_view(sc);
     job.first_ray = p->first_ray;
     job.num_rays = p->num_rays;
     job.hit_off = 0;
@@ -200,6 +201,8 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.rerun_cap = z.rerun_cap;
     w.num_sms = c->num_sms;
     w.shadow_steps = c->shadow_steps;
+    w.horder = {(uint32_t *)(base + o_hc), (uint32_t *)(base + o_hq), (uint32_t *)(base + o_hk), hit_order_bits(1),
+                (int)hit_order_cells(1)};
 
     StepLaunch L;
     L.w = w;

@@ -78,6 +78,10 @@ cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, vo
         Hook h(hook, hook_ctx, "item_prefix");
         launch_item_prefix(w, st);
     }
+    if (S > 0 && w.k.M > 0) {
+        Hook h(hook, hook_ctx, "hit_order");
+        launch_hit_order(w, L.flat_blocks, st);
+    }
     {
         Hook h(hook, hook_ctx, "direct");
         launch_direct(w, st);

@@ -32,6 +32,7 @@ constexpr int SHADOW_THREADS = 128;
 constexpr float BIN_GUARD = 2e-3f;
 // node visits a shadow-ray lane makes before the warp refills finished lanes
 constexpr int SHADOW_STEPS = 8;
+constexpr int SHADOW_WINDOW = 256;  // items a warp takes from the chunk at a time
 
 struct BlockAcc {
     double esc[MAXB], absb[MAXB], rem[MAXB], late[MAXB];
@@ -171,17 +172,83 @@ __global__ void k_setup(TraceWork w, int wave)
     }
 }
 
-// first shadow item of every job: sum over earlier jobs of stored reflections x sources
+// first shadow item of every job (sum over earlier jobs of stored reflections x
+// sources) and first reflection in the flattened order of the step
 __global__ void k_item_prefix(TraceWork w)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long acc = 0;
+    unsigned long long acc = 0, hits = 0;
     for (int j = 0; j < w.njobs; ++j) {
         w.js[j].item_off = acc;
+        w.js[j].hit_prefix = hits;
         const unsigned long long h = min(w.js[j].n_hits, w.jobs[j].hit_cap);
         acc += h * (unsigned long long)w.jobs[j].S;
+        hits += h;
     }
     w.ctr->total_items = acc;
+    w.ctr->total_hits = hits;
+}
+
+// job of flattened reflection f: the last job whose first reflection is <= f
+__device__ __forceinline__ int job_of_hit(const TraceWork &w, unsigned long long f)
+{
+    int lo = 0, hi = w.njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (w.js[mid].hit_prefix <= f) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t x)  // bits 0..9 to every third bit
+{
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+// cell of every stored reflection, and the cell counts
+__global__ void k_hit_cells(TraceWork w)
+{
+    const unsigned long long n = w.ctr->total_hits;
+    const int bits = w.horder.bits;
+    const float cells = (float)(1 << bits);
+    for (unsigned long long f = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; f < n;
+         f += (unsigned long long)gridDim.x * blockDim.x) {
+        const int job = w.njobs > 1 ? job_of_hit(w, f) : 0;
+        const SceneJob &J = w.njobs > 1 ? w.jobs[job] : w.job0;
+        const unsigned long long slot = J.hit_off + (f - (w.njobs > 1 ? w.js[job].hit_prefix : 0ull));
+        const float4 P = w.hits.p[slot];
+        const float pc[3] = {P.x, P.y, P.z};
+        uint32_t code = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float e = J.sc.ext[a] > 0.f ? J.sc.ext[a] : 1.f;
+            const float q = fminf(fmaxf((pc[a] - J.sc.lo[a]) / e * cells, 0.f), cells - 1.f);
+            code |= spread3((uint32_t)q) << (2 - a);
+        }
+        const uint32_t cell = ((uint32_t)job << (3 * bits)) | code;
+        w.horder.cell[f] = cell;
+        atomicAdd(&w.horder.cnt[cell], 1u);
+    }
+}
+
+// reflection slots in cell order (the order inside a cell is not fixed)
+__global__ void k_hit_scatter(TraceWork w)
+{
+    const unsigned long long n = w.ctr->total_hits;
+    for (unsigned long long f = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; f < n;
+         f += (unsigned long long)gridDim.x * blockDim.x) {
+        const int job = w.njobs > 1 ? job_of_hit(w, f) : 0;
+        const SceneJob &J = w.njobs > 1 ? w.jobs[job] : w.job0;
+        const unsigned long long slot = J.hit_off + (f - (w.njobs > 1 ? w.js[job].hit_prefix : 0ull));
+        const uint32_t pos = atomicAdd(&w.horder.cnt[w.horder.cell[f]], 1u);
+        w.horder.perm[pos] = (uint32_t)slot;
+    }
 }
 
 // job of shadow item q: the last job whose first item is <= q
@@ -616,16 +683,24 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
     }
 }
 
-// (job, reflection slot, global source) of shadow item q
+// (job, reflection slot, global source) of shadow item q.  A job's items come in
+// tiles of 32 reflections (consecutive in cell order) x its S sources, source-major
+// inside a tile: 32 consecutive items are rays from nearby points to one source.
 __device__ __forceinline__ void item_target(const TraceWork &w, bool batch, unsigned long long q, int &job,
                                             unsigned long long &j, int &gs)
 {
     job = batch ? job_of_item(w, q) : 0;
     const SceneJob &J = batch ? w.jobs[job] : w.job0;
-    const unsigned long long local = q - (batch ? w.js[job].item_off : 0ull);
-    const unsigned long long jj = local / (unsigned long long)J.S;
-    j = J.hit_off + jj;
-    gs = J.src_off + (int)(local - jj * (unsigned long long)J.S);
+    const JobState &js = w.js[job];
+    const unsigned long long local = q - (batch ? js.item_off : 0ull);
+    const unsigned long long n = min(js.n_hits, J.hit_cap);
+    const unsigned long long per_tile = 32ull * (unsigned long long)J.S;
+    const unsigned long long tile = local / per_tile;
+    const unsigned r = (unsigned)(local - tile * per_tile);
+    const unsigned tsz = (unsigned)min(32ull, n - tile * 32ull);
+    const unsigned s = r / tsz;
+    j = w.horder.perm[js.hit_prefix + tile * 32ull + (r - s * tsz)];
+    gs = J.src_off + (int)s;
 }
 
 // Shadow rays of one chunk of the step's items q = (reflection, source) pairs,
@@ -635,7 +710,7 @@ __device__ __forceinline__ void item_target(const TraceWork &w, bool batch, unsi
 // ray.  Queries whose FP32 answer is rounding-sensitive are queued for the FP64
 // kernel below (EXACT); when the queue is full the FP32 answer stands.
 template <bool COUNT, bool EXACT, bool BATCH>
-__global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned long long chunk)
+__global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsigned long long chunk)
 {
     __shared__ int sstack[SMEM_STACK * SHADOW_THREADS];
     __shared__ BlockAcc acc;
@@ -660,18 +735,26 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
     AnyState st = {-1, 0, INFINITY, false, false};
     int steps = 0, iter_cap = 0;
     float f = 0.f, dist = 0.f;
+    unsigned long long win = 0, win_end = 0;  // the warp's window of items (warp-uniform)
     while (true) {
-        const unsigned need = __ballot_sync(FULL, !busy && !exhausted);
-        if (need) {
-            const int leader = __ffs(need) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(&w.ctr->next_item, (unsigned long long)__popc(need));
-            base = __shfl_sync(FULL, base, leader);
-            if (!busy && !exhausted) {
-                const unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
-                if (my >= items) {
-                    exhausted = true;
-                } else {
+        unsigned need = __ballot_sync(FULL, !busy && !exhausted);
+        while (need) {
+            if (win >= win_end) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(&w.ctr->next_item, (unsigned long long)SHADOW_WINDOW);
+                b = __shfl_sync(FULL, b, 0);
+                if (b >= items) {
+                    if ((need >> lane) & 1u) exhausted = true;
+                    break;
+                }
+                win = b;
+                win_end = min(b + (unsigned long long)SHADOW_WINDOW, items);
+            }
+            const unsigned avail = (unsigned)min(win_end - win, 32ull);
+            const unsigned rank = __popc(need & ((1u << lane) - 1u));
+            if (((need >> lane) & 1u) && rank < avail) {
+                {
+                    const unsigned long long my = win + rank;
                     item = q0 + my;
                     unsigned long long j;
                     int gs;
@@ -695,6 +778,8 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow(TraceWork w, unsigned
                     }
                 }
             }
+            win += min(avail, (unsigned)__popc(need));
+            need = __ballot_sync(FULL, !busy && !exhausted);
         }
         if (__all_sync(FULL, !busy && exhausted)) break;
         if (!busy) continue;
@@ -813,6 +898,14 @@ void launch_setup(const TraceWork &w, int wave, cudaStream_t st)
 }
 
 void launch_item_prefix(const TraceWork &w, cudaStream_t st) { k_item_prefix<<<1, 32, 0, st>>>(w); }
+
+void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st)
+{
+    cudaMemsetAsync(w.horder.cnt, 0, sizeof(uint32_t) * ((size_t)w.horder.ncells + 1), st);
+    k_hit_cells<<<blocks, 256, 0, st>>>(w);
+    launch_scan_u32(w.horder.cnt, w.horder.cnt, w.horder.ncells, st);
+    k_hit_scatter<<<blocks, 256, 0, st>>>(w);
+}
 
 template <typename R, bool BATCH>
 void launch_paths_r(const TraceWork &w, int blocks, cudaStream_t st)
