@@ -112,6 +112,18 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_over_ranks(total_ms: float, rank_work: float, device) -> tuple:
+    """(max over ranks of the timed milliseconds, sum over ranks of the work units):
+    the job's time is its slowest rank's, its work every rank's."""
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    wsum = torch.tensor([rank_work], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(wsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(wsum[0])
+
+
 def cpu_sample(rays: int, threads: int):
     """The oracle on `rays` primaries of the medium workload, all given threads.
     Returns (seconds, segments + shadow rays)."""
@@ -253,11 +265,7 @@ def main():
     work = float(st["segments"] + st["shadow_rays"])  # last step (same workload each step)
     rank_work = work * args.steps
     if ws > 1:
-        t = torch.tensor([total_ms, rank_work], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        total_ms, all_work = float(tmax[0]), float(t[1])
+        total_ms, all_work = reduce_over_ranks(total_ms, rank_work, "cuda")
     else:
         all_work = rank_work
     value = all_work / (total_ms / 1000.0)
