@@ -44,7 +44,7 @@ FLOPS_PER_TRI = 27.0    # Moller-Trumbore
 # DRAM bytes (read + write) of one k_shadow launch in an ncu capture of the same
 # update at 30,000 primaries, and the shadow rays that launch traced; a full-size
 # launch is credited with the same bytes per shadow ray.
-NCU_SHADOW_DRAM = (133_543_424 + 28_790_272, 18_878_384)
+NCU_SHADOW_DRAM = (560_882_432 + 43_546_624, 18_878_384)
 
 
 def _peaks():
