@@ -251,25 +251,21 @@ def room_or_corridor(seed: int, target_tris: int, bands: int = 8, num_sources: i
     if kind is None:
         kind = "room" if rng.uniform() < 0.5 else "corridor"
     n_inner = max(0, (int(target_tris) - 12) // 12)
-    mb = _MeshBuilder()
-    boxes = []
+    boxes = []  # interior boxes (lo, hi, material)
     if kind == "room":
         size = rng.uniform([4.0, 4.0, 2.5], [30.0, 25.0, 10.0])
-        mb.add_box(np.zeros(3), size, 0)
         for i in range(n_inner):
             ext = rng.uniform(0.2, 0.25 * size.min() + 0.3, size=3)
             c = rng.uniform(np.zeros(3), size)
             lo, hi = np.clip(c - ext / 2, 0, size), np.clip(c + ext / 2, 0, size)
             if rng.uniform() < 0.6:
                 lo[2], hi[2] = 0.0, min(ext[2], size[2])
-            boxes.append((lo, hi))
-            mb.add_box(lo, hi, 1 + i % (n_mat - 1))
+            boxes.append((lo, hi, 1 + i % (n_mat - 1)))
     else:
         length = rng.uniform(20.0, 80.0)
         width = rng.uniform(2.0, 5.0)
         height = rng.uniform(2.5, 5.0)
         size = np.array([length, width, height])
-        mb.add_box(np.zeros(3), size, 0)
         # interior "side rooms": thin partition boxes that split the corridor into
         # alcoves along one side, plus clutter for the rest of the triangle budget
         for i in range(n_inner):
@@ -285,16 +281,29 @@ def room_or_corridor(seed: int, target_tris: int, bands: int = 8, num_sources: i
                 ext = rng.uniform(0.2, min(1.5, 0.45 * width), size=3)
                 c = rng.uniform(np.zeros(3), size)
                 lo, hi = np.clip(c - ext / 2, 0, size), np.clip(c + ext / 2, 0, size)
-            boxes.append((lo, hi))
-            mb.add_box(lo, hi, 1 + i % (n_mat - 1))
-    verts, tris, mats = mb.finish()
-    boxes = np.array(boxes).reshape(-1, 2, 3)
+            boxes.append((lo, hi, 1 + i % (n_mat - 1)))
     a, s = _materials(rng, n_mat, bands, s_spread=s_spread)
     margin = min(0.5, 0.2 * float(size.min()))
-    pts = _free_points(rng, 1 + num_sources, np.zeros(3), size, boxes, margin, 0.3,
-                       min_sep=min(1.0, 0.3 * float(size.min())))
+    min_sep = min(1.0, 0.3 * float(size.min()))
+    bx = np.array([(lo, hi) for lo, hi, _ in boxes]).reshape(-1, 2, 3)
+    try:
+        pts = _free_points(rng, 1 + num_sources, np.zeros(3), size, bx, margin, 0.3, min_sep=min_sep,
+                           max_tries=20000)
+    except RuntimeError:
+        # the clutter fills the room: place the points first (apart from each other) and
+        # drop the boxes that would enclose one of them
+        frng = np.random.default_rng([seed, 1])
+        pts = _free_points(frng, 1 + num_sources, np.zeros(3), size, np.zeros((0, 2, 3)), margin, 0.3,
+                           min_sep=min_sep)
+        boxes = [b for b in boxes if not any(_inside_any(p, np.array([b[:2]]), 0.3) for p in pts)]
+        bx = np.array([(lo, hi) for lo, hi, _ in boxes]).reshape(-1, 2, 3)
+    mb = _MeshBuilder()
+    mb.add_box(np.zeros(3), size, 0)
+    for lo, hi, m in boxes:
+        mb.add_box(lo, hi, m)
+    verts, tris, mats = mb.finish()
     return Scene(f"{kind}", verts, tris, mats, a, s, pts[0].astype(np.float32),
-                 pts[1:].astype(np.float32), boxes=boxes, room_lo=np.zeros(3),
+                 pts[1:].astype(np.float32), boxes=bx, room_lo=np.zeros(3),
                  room_hi=size)
 
 
