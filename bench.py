@@ -37,6 +37,11 @@ METRIC = "ray segments/s; IR+reverb-param updates/s at ≤5% decay-time err vs p
 UNIT = "ray segments/s"
 WORKLOAD = dict(num_rays=200_000, max_order=64, sh_order=2, num_bins=2000, min_order=1, ir_rate_hz=1000.0,
                 speed_of_sound=343.0, source_radius=0.5)
+LARGE = dict(num_rays=1_000_000, max_order=200, sh_order=3, num_bins=3000, min_order=1, ir_rate_hz=1000.0,
+             speed_of_sound=343.0, source_radius=0.5)
+LARGE_NAME = ("large: procedural city, 64x64 buildings + ground (2,015,232 tris), 8 bands, 256 sources, "
+              "1M rays x 200 reflections, IR 3 s @ 1 kHz, SH order 3")
+SCENE = "furnished_hall"
 WORKLOAD_NAME = ("medium: furnished hall 40x30x12 m + 2000 boxes (24,012 tris), 8 bands, 16 sources, "
                  "200k rays x 64 reflections, IR 2 s @ 1 kHz, SH order 2")
 FLOPS_PER_NODE = 24.0   # slab tests of two children
@@ -125,11 +130,11 @@ def reduce_over_ranks(total_ms: float, rank_work: float, device) -> tuple:
 
 
 def cpu_sample(rays: int, threads: int):
-    """The oracle on `rays` primaries of the medium workload, all given threads.
+    """The oracle on `rays` primaries of the benchmark's workload, all given threads.
     Returns (seconds, segments + shadow rays)."""
     import oracle
     from paper_1803_00430_gb300 import scenes
-    sc = scenes.furnished_hall()
+    sc = getattr(scenes, SCENE)()
     osc = oracle.OracleScene.from_scene(sc)
     p = oracle.TraceParams(num_rays=rays, max_order=WORKLOAD["max_order"], sh_order=WORKLOAD["sh_order"],
                            num_bins=WORKLOAD["num_bins"], min_order=WORKLOAD["min_order"],
@@ -149,8 +154,9 @@ def cpu_baseline(target_s: float = 15.0):
     rays = int(min(WORKLOAD["num_rays"], max(probe_rays, probe_rays * target_s / max(dt, 1e-3))))
     dt, work = cpu_sample(rays, threads)
     return {"value": work / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{rays} of the {WORKLOAD['num_rays']} primaries of the medium workload "
-                      f"(full scene, 16 sources, 64 reflections), trace + estimate, {dt:.1f} s wall"}
+            "sample": f"{rays} of the {WORKLOAD['num_rays']} primaries of the {WORKLOAD_NAME.split(':')[0]} workload "
+                      f"(full scene and sources, {WORKLOAD['max_order']} reflections), trace + estimate, "
+                      f"{dt:.1f} s wall"}
 
 
 def run_reference(args):
@@ -172,7 +178,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_rays_per_step": rays},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{rays} primaries of the medium workload per step"},
+                             "sample": f"{rays} primaries of the {WORKLOAD_NAME.split(':')[0]} workload per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -189,7 +195,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--rays", type=int, default=0, help="primaries per update (default: the workload's 200k; "
                     "smaller values make a small case for profilers)")
+    ap.add_argument("--workload", default="medium", choices=["medium", "large"],
+                    help="medium: the furnished hall (default); large: the procedural city")
     args = ap.parse_args()
+    global SCENE, WORKLOAD_NAME
+    if args.workload == "large":
+        WORKLOAD.clear()
+        WORKLOAD.update(LARGE)
+        WORKLOAD_NAME, SCENE = LARGE_NAME, "city"
     if args.rays:
         WORKLOAD["num_rays"] = args.rays
     if args.impl == "reference":
@@ -211,7 +224,7 @@ def main():
 
     stream = torch.cuda.current_stream()
     ctx = rpr.Context(local, stream)
-    sc = scenes.furnished_hall()
+    sc = getattr(scenes, SCENE)()
     scene = rpr.Scene.from_scene(ctx, sc)
     S, B = sc.num_sources, sc.num_bands
     flags = rpr.RP_FLAG_DEVICE_POSITIONS | (rpr.RP_FLAG_FP32_PATHS if args.fp32_paths else 0)
@@ -315,7 +328,7 @@ def main():
     peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / avg_s / 1e12
     traffic = (NCU_SHADOW_DRAM[0] * st["shadow_rays"] / NCU_SHADOW_DRAM[1]
-               if name == "shadow" and not args.fp32_paths else None)
+               if name == "shadow" and not args.fp32_paths and args.workload == "medium" else None)
     shares = {k: round(v[1] / sum(x[1] for x in kt.values()), 4) for k, v in kt.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -19,8 +19,27 @@ constexpr int ACC_THREADS = 256;
 constexpr int ACC_WARPS = ACC_THREADS / 32;
 constexpr int ACC_SLOTS = (MAXB * MAXK + 31) / 32;
 
-__global__ void k_count(TraceWork w)
+// Record chunks are sized for the worst case (every primary reflecting M times);
+// a chunk past the step's actual shadow items has no records and is skipped on the
+// device.  Chunk 0 always runs: it also holds the source-sphere records of the paths.
+__device__ __forceinline__ bool chunk_active(const TraceWork &w, unsigned long long chunk)
 {
+    return chunk == 0 || chunk * w.items_per_chunk < w.ctr->total_items;
+}
+
+__global__ void k_clear_counts(TraceWork w, unsigned long long chunk)
+{
+    if (!chunk_active(w, chunk)) return;
+    const long long n = (long long)w.k.S * w.k.T;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        w.cnt[i] = 0u;
+        w.cur[i] = 0u;
+    }
+}
+
+__global__ void k_count(TraceWork w, unsigned long long chunk)
+{
+    if (!chunk_active(w, chunk)) return;
     const unsigned long long n = min(w.ctr->n_records, w.rec.cap);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x)
@@ -30,9 +49,12 @@ __global__ void k_count(TraceWork w)
 // exclusive scan of cnt[0..n) into off[0..n], off[n] = total; one block of 1024
 // exclusive scan of cnt[0..n) into off[0..n] (off[n] = total; off may be cnt): one
 // block of 1024 threads walks the array in tiles of 4096, each thread taking 4
-// consecutive counts, with the running total carried from tile to tile.
-__global__ void __launch_bounds__(1024) k_scan(const uint32_t *cnt, uint32_t *off, int n)
+// consecutive counts, with the running total carried from tile to tile.  With a gate,
+// the scan is skipped when *gate_total <= gate_q0 (an empty record chunk).
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t *cnt, uint32_t *off, int n,
+                                               const unsigned long long *gate_total, unsigned long long gate_q0)
 {
+    if (gate_total && gate_q0 > 0 && *gate_total <= gate_q0) return;
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t carry;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -75,8 +97,9 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t *cnt, uint32_t *of
     if (t == 0) off[n] = carry;
 }
 
-__global__ void k_scatter(TraceWork w)
+__global__ void k_scatter(TraceWork w, unsigned long long chunk)
 {
+    if (!chunk_active(w, chunk)) return;
     const unsigned long long n = min(w.ctr->n_records, w.rec.cap);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -95,8 +118,9 @@ __device__ __forceinline__ void kahan_add(float &sum, float &err, float x)
     sum = t;
 }
 
-__global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first)
+__global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, unsigned long long chunk)
 {
+    if (!chunk_active(w, chunk)) return;
     __shared__ float se[ACC_WARPS][32][MAXB];
     __shared__ float sy[ACC_WARPS][32][MAXK];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -107,6 +131,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first)
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
     for (long long key = (long long)blockIdx.x * ACC_WARPS + wp; key < nkeys; key += nwarps) {
         const uint32_t begin = w.off[key], end = w.off[key + 1];
+        if (!first && begin == end) continue;  // nothing to merge: the running pair stands
         const int gs = w.src_base + (int)(key / T);
         const uint32_t scene_id = w.njobs > 1 ? w.jobs[w.src_job[gs]].scene_id : w.job0.scene_id;
         float sum[ACC_SLOTS], err[ACC_SLOTS];
@@ -196,20 +221,34 @@ __global__ void k_direct_add(TraceWork w)
 
 }  // namespace
 
-void launch_count(const TraceWork &w, int blocks, cudaStream_t st) { k_count<<<blocks, 256, 0, st>>>(w); }
+void launch_clear_counts(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
+{
+    k_clear_counts<<<blocks, 256, 0, st>>>(w, chunk);
+}
+
+void launch_count(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
+{
+    k_count<<<blocks, 256, 0, st>>>(w, chunk);
+}
 
 void launch_scan_u32(const uint32_t *cnt, uint32_t *off, int n, cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(cnt, off, n);
+    k_scan<<<1, 1024, 0, st>>>(cnt, off, n, nullptr, 0ull);
 }
 
-void launch_scan(const TraceWork &w, cudaStream_t st) { launch_scan_u32(w.cnt, w.off, w.k.S * w.k.T, st); }
-
-void launch_scatter(const TraceWork &w, int blocks, cudaStream_t st) { k_scatter<<<blocks, 256, 0, st>>>(w); }
-
-void launch_accum(const TraceWork &w, int first_chunk, int blocks, cudaStream_t st)
+void launch_scan(const TraceWork &w, unsigned long long chunk, cudaStream_t st)
 {
-    k_accum<<<blocks, ACC_THREADS, 0, st>>>(w, first_chunk);
+    k_scan<<<1, 1024, 0, st>>>(w.cnt, w.off, w.k.S * w.k.T, &w.ctr->total_items, chunk * w.items_per_chunk);
+}
+
+void launch_scatter(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
+{
+    k_scatter<<<blocks, 256, 0, st>>>(w, chunk);
+}
+
+void launch_accum(const TraceWork &w, int first_chunk, unsigned long long chunk, int blocks, cudaStream_t st)
+{
+    k_accum<<<blocks, ACC_THREADS, 0, st>>>(w, first_chunk, chunk);
 }
 
 void launch_finalize(const TraceWork &w, cudaStream_t st)

@@ -204,11 +204,12 @@ void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_shadow_exact(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_direct(const TraceWork &w, cudaStream_t st);
-void launch_count(const TraceWork &w, int blocks, cudaStream_t st);
-void launch_scan(const TraceWork &w, cudaStream_t st);
+void launch_clear_counts(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
+void launch_count(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
+void launch_scan(const TraceWork &w, unsigned long long chunk, cudaStream_t st);
 void launch_scan_u32(const uint32_t *cnt, uint32_t *off, int n, cudaStream_t st);
-void launch_scatter(const TraceWork &w, int blocks, cudaStream_t st);
-void launch_accum(const TraceWork &w, int first_chunk, int blocks, cudaStream_t st);
+void launch_scatter(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
+void launch_accum(const TraceWork &w, int first_chunk, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_finalize(const TraceWork &w, cudaStream_t st);
 int paths_occupancy(int flags);
 int shadow_occupancy(int flags);

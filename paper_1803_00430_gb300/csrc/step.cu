@@ -86,7 +86,6 @@ cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, vo
         Hook h(hook, hook_ctx, "direct");
         launch_direct(w, st);
     }
-    const long long nkeys = (long long)S * w.k.T;
     for (unsigned long long ch = 0; ch < L.n_rec_chunks && S > 0; ++ch) {
         if (ch > 0) CKS(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
         CKS(cudaMemsetAsync(&w.ctr->next_item, 0, 2 * sizeof(unsigned long long), st));  // + n_rerun
@@ -98,23 +97,22 @@ cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, vo
             Hook h(hook, hook_ctx, "shadow_exact");
             launch_shadow_exact(w, ch, L.exact_blocks, st);
         }
-        CKS(cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nkeys, st));
-        CKS(cudaMemsetAsync(w.cur, 0, sizeof(uint32_t) * nkeys, st));
         {
             Hook h(hook, hook_ctx, "count");
-            launch_count(w, L.flat_blocks, st);
+            launch_clear_counts(w, ch, L.flat_blocks, st);
+            launch_count(w, ch, L.flat_blocks, st);
         }
         {
             Hook h(hook, hook_ctx, "scan");
-            launch_scan(w, st);
+            launch_scan(w, ch, st);
         }
         {
             Hook h(hook, hook_ctx, "scatter");
-            launch_scatter(w, L.flat_blocks, st);
+            launch_scatter(w, ch, L.flat_blocks, st);
         }
         {
             Hook h(hook, hook_ctx, "accum");
-            launch_accum(w, ch == 0 ? 1 : 0, L.acc_blocks, st);
+            launch_accum(w, ch == 0 ? 1 : 0, ch, L.acc_blocks, st);
         }
     }
     if (S > 0) {
