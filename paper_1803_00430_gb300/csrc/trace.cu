@@ -379,7 +379,7 @@ __device__ __forceinline__ V3<R> primary_dir_r(uint32_t rid, uint32_t scene_id, 
 }
 
 template <typename R, bool HASH, bool COUNT, bool BATCH>
-__global__ void __launch_bounds__(PATH_THREADS) k_paths(TraceWork w)
+__global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
 {
     __shared__ int sstack[SMEM_STACK * PATH_THREADS];
     __shared__ BlockAcc acc;
