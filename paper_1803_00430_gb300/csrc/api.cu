@@ -120,7 +120,11 @@ int reserve(rp_ctx *c, const StepSizes &z, int B, int njobs, int total_sources, 
     if ((r = ensure(c, c->hit_ws, z.hit_cap * B * sizeof(float)))) return r;
     if ((r = ensure(c, c->hit_rid, z.hit_cap * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->hord_cell, z.hit_cap * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->shit_p, z.hit_cap * sizeof(float4)))) return r;
     if ((r = ensure(c, c->hord_perm, z.hit_cap * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->shit_n, z.hit_cap * sizeof(float4)))) return r;
+    if ((r = ensure(c, c->shit_ws, z.hit_cap * B * sizeof(float)))) return r;
+    if ((r = ensure(c, c->shit_rid, z.hit_cap * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->hord_cnt, (size_t)(hit_order_cells(njobs) + 1) * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->rec_key, z.rec_cap * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->rec_rid, z.rec_cap * sizeof(uint32_t)))) return r;
@@ -166,6 +170,8 @@ void bind_workspace(rp_ctx *c, const StepSizes &z, TraceWork &w)
     w.chunks = (const RayChunk *)c->chunks.p;
     w.src_job = (const int *)c->src_job.p;
     w.pos = (const float4 *)c->src.p;
+    w.shits = {(float4 *)c->shit_p.p, nullptr, (float4 *)c->shit_n.p, (float *)c->shit_ws.p,
+               (uint32_t *)c->shit_rid.p, z.hit_cap};
     w.horder = {(uint32_t *)c->hord_cell.p, (uint32_t *)c->hord_perm.p, (uint32_t *)c->hord_cnt.p, hit_order_bits(1),
                 (int)hit_order_cells(1)};
 }
@@ -291,8 +297,9 @@ int rp_destroy(rp_ctx *c)
     if (!c) return RP_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    for (Buf *b : {&c->hit_p, &c->hit_plo, &c->hit_n, &c->hit_ws, &c->hit_rid, &c->hord_cell, &c->hord_perm,
-                   &c->hord_cnt, &c->rec_key, &c->rec_rid, &c->rec_e, &c->perm, &c->rerun,
+    for (Buf *b : {&c->hit_p, &c->hit_plo, &c->hit_n, &c->hit_ws, &c->hit_rid, &c->shit_p, &c->hord_perm,
+                   &c->shit_n, &c->shit_ws, &c->shit_rid, &c->hord_cell, &c->hord_cnt, &c->rec_key, &c->rec_rid,
+                   &c->rec_e, &c->perm, &c->rerun,
                    &c->cnt, &c->off, &c->cur, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H, &c->direct,
                    &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job})
         free_buf(*b);

@@ -149,7 +149,11 @@ int reserve_batch(rp_batch *b)
     if ((r = grow(c, c->hit_ws, z.hit_cap * B * sizeof(float)))) return r;
     if ((r = grow(c, c->hit_rid, z.hit_cap * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->hord_cell, z.hit_cap * sizeof(uint32_t)))) return r;
+    if ((r = grow(c, c->shit_p, z.hit_cap * sizeof(float4)))) return r;
     if ((r = grow(c, c->hord_perm, z.hit_cap * sizeof(uint32_t)))) return r;
+    if ((r = grow(c, c->shit_n, z.hit_cap * sizeof(float4)))) return r;
+    if ((r = grow(c, c->shit_ws, z.hit_cap * B * sizeof(float)))) return r;
+    if ((r = grow(c, c->shit_rid, z.hit_cap * sizeof(uint32_t)))) return r;
     const long long cells = std::max(1ll << 18, 8ll * b->max_jobs) + 1;  // >= hit_order_cells of any group
     if ((r = grow(c, c->hord_cnt, (size_t)cells * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->rec_key, z.rec_cap * sizeof(uint32_t)))) return r;
@@ -192,6 +196,8 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
     w.job0 = b->h_jobs[g.job_begin];
     w.jobs = b->d_jobs + g.job_begin;
     w.njobs = g.job_end - g.job_begin;
+    w.shits = {(float4 *)c->shit_p.p, nullptr, (float4 *)c->shit_n.p, (float *)c->shit_ws.p,
+               (uint32_t *)c->shit_rid.p, b->zmax.hit_cap};
     w.horder = {(uint32_t *)c->hord_cell.p, (uint32_t *)c->hord_perm.p, (uint32_t *)c->hord_cnt.p,
                 hit_order_bits(w.njobs), (int)hit_order_cells(w.njobs)};
     w.js = (JobState *)c->js.p;

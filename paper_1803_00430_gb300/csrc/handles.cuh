@@ -38,7 +38,8 @@ struct rp_ctx {
     int shadow_steps = 8;
     unsigned long long ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
     // workspace
-    Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, hord_cell, hord_perm, hord_cnt, rec_key, rec_rid, rec_e, perm, rerun,
+    Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, shit_p, shit_n, shit_ws, shit_rid, hord_cell, hord_perm, hord_cnt,
+        rec_key, rec_rid, rec_e, perm, rerun,
         cnt, off, cur, Hs, He, src, ctr,
         stats, H, direct, params, state, jobs, js, chunks, src_job;
     // profiling

@@ -103,7 +103,7 @@ struct Hits {
     float4 *p;      // hit point, path length to it in .w (FP32 part)
     float4 *plo;    // residuals: hit point and path length = p + plo in FP64
     float4 *n;      // normal facing the arriving ray, leaf triangle in .w (int bits)
-    float *ws;      // [b * cap + j] path weight after absorption times s_b
+    float *ws;      // [j * B + b] path weight after absorption times s_b
     uint32_t *rid;  // primary ray id
     unsigned long long cap;
 };
@@ -145,10 +145,11 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
 
 // The step's stored reflections sorted by cell (job, Morton code of the position on
 // a 2^bits grid per axis over the job's scene box), so that the shadow rays a warp
-// traces start close together and aim at the same source.
+// traces start close together and aim at the same source.  The records themselves
+// are copied in that order (TraceWork::shits), so a warp's loads are contiguous.
 struct HitOrder {
     uint32_t *cell;  // [total hits] cell of the flattened reflection f
-    uint32_t *perm;  // [total hits] reflection slot, in cell order (jobs in order)
+    uint32_t *perm;  // [total hits] slot in Hits of the i-th reflection in cell order
     uint32_t *cnt;   // [ncells + 1] counts, then cursors
     int bits;        // grid bits per axis
     int ncells;      // njobs x 2^(3 bits)
@@ -195,6 +196,8 @@ struct TraceWork {
     int num_sms;
     int shadow_steps;  // node visits a shadow lane makes between refills
     HitOrder horder;   // reflections in spatial order for coherent shadow rays
+    Hits shits;        // point, normal, weights and ray id of the reflections in that order (shadow
+                       // rays read these; the FP64 residuals stay in `hits`, found through horder.perm)
 };
 
 void launch_setup(const TraceWork &w, int wave, cudaStream_t st);

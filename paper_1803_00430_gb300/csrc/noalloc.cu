@@ -106,8 +106,10 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     const unsigned long long o_hp = cv.take<float4>(z.hit_cap), o_hl = cv.take<float4>(z.hit_cap),
                              o_hn = cv.take<float4>(z.hit_cap), o_hw = cv.take<float>(z.hit_cap * B),
                              o_hr = cv.take<uint32_t>(z.hit_cap), o_hc = cv.take<uint32_t>(z.hit_cap),
-                             o_hq = cv.take<uint32_t>(z.hit_cap),
                              o_hk = cv.take<uint32_t>((unsigned long long)hit_order_cells(1) + 1);
+    const unsigned long long o_sp = cv.take<float4>(z.hit_cap), o_sq = cv.take<uint32_t>(z.hit_cap),
+                             o_sn = cv.take<float4>(z.hit_cap), o_sw = cv.take<float>(z.hit_cap * B),
+                             o_sr = cv.take<uint32_t>(z.hit_cap);
     const unsigned long long o_cnt = cv.take<uint32_t>(z.keys), o_off = cv.take<uint32_t>(z.keys + 1),
                              o_cur = cv.take<uint32_t>(z.keys);
     const unsigned long long o_hs = cv.take<float>(z.cells), o_he = cv.take<float>(z.cells);
@@ -201,7 +203,9 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.rerun_cap = z.rerun_cap;
     w.num_sms = c->num_sms;
     w.shadow_steps = c->shadow_steps;
-    w.horder = {(uint32_t *)(base + o_hc), (uint32_t *)(base + o_hq), (uint32_t *)(base + o_hk), hit_order_bits(1),
+    w.shits = {(float4 *)(base + o_sp), nullptr, (float4 *)(base + o_sn), (float *)(base + o_sw),
+               (uint32_t *)(base + o_sr), z.hit_cap};
+    w.horder = {(uint32_t *)(base + o_hc), (uint32_t *)(base + o_sq), (uint32_t *)(base + o_hk), hit_order_bits(1),
                 (int)hit_order_cells(1)};
 
     StepLaunch L;

@@ -251,6 +251,23 @@ __global__ void k_hit_scatter(TraceWork w)
     }
 }
 
+// copy of the records the shadow rays read, in cell order (random reads, coalesced writes)
+__global__ void k_hit_gather(TraceWork w)
+{
+    const unsigned long long n = w.ctr->total_hits;
+    const int B = w.k.B;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long slot = w.horder.perm[i];
+        w.shits.p[i] = w.hits.p[slot];
+        w.shits.n[i] = w.hits.n[slot];
+        w.shits.rid[i] = w.hits.rid[slot];
+        const float *src = w.hits.ws + slot * B;
+        float *dst = w.shits.ws + i * B;
+        for (int b = 0; b < B; ++b) dst[b] = src[b];
+    }
+}
+
 // job of shadow item q: the last job whose first item is <= q
 __device__ __forceinline__ int job_of_item(const TraceWork &w, unsigned long long q)
 {
@@ -586,7 +603,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     const float *sb = sc.scat + mat * B;
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b)
-                        if (b < B) w.hits.ws[(unsigned long long)b * w.hits.cap + j] = wgt[b] * __ldg(sb + b);
+                        if (b < B) w.hits.ws[j * B + b] = wgt[b] * __ldg(sb + b);
                     w.hits.rid[j] = rid;
                 } else {
                     raise_error(w.status, RP_ERR_CAPACITY);
@@ -656,14 +673,14 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
 {
     const TraceConsts &k = w.k;
     const int B = k.B, T = k.T;
-    const float4 P = w.hits.p[j];
+    const float4 P = w.shits.p[j];
     float e[MAXB];
 #pragma unroll
-    for (int b = 0; b < MAXB; ++b) e[b] = b < B ? w.hits.ws[(unsigned long long)b * w.hits.cap + j] * f : 0.f;
+    for (int b = 0; b < MAXB; ++b) e[b] = b < B ? w.shits.ws[j * B + b] * f : 0.f;
     float binf;
     const float x = ((P.w + dist) / k.c) * k.rate;
     if (fabsf(x - rintf(x)) < BIN_GUARD) {
-        const float4 lo = w.hits.plo[j];
+        const float4 lo = w.hits.plo[w.horder.perm[j]];
         const float4 cs = __ldg(w.pos + gs);
         const double dx = (double)cs.x - ((double)P.x + (double)lo.x);
         const double dy = (double)cs.y - ((double)P.y + (double)lo.y);
@@ -675,7 +692,7 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
         binf = floorf(x);
     }
     if (binf < (float)T) {
-        emit_record(w, (uint32_t)(gs - w.src_base) * (uint32_t)T + (uint32_t)binf, w.hits.rid[j], e, B);
+        emit_record(w, (uint32_t)(gs - w.src_base) * (uint32_t)T + (uint32_t)binf, w.shits.rid[j], e, B);
     } else {
 #pragma unroll
         for (int b = 0; b < MAXB; ++b)
@@ -683,7 +700,7 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
     }
 }
 
-// (job, reflection slot, global source) of shadow item q.  A job's items come in
+// (job, reflection in the cell-ordered copy, global source) of shadow item q.  A job's items come in
 // tiles of 32 reflections (consecutive in cell order) x its S sources, source-major
 // inside a tile: 32 consecutive items are rays from nearby points to one source.
 __device__ __forceinline__ void item_target(const TraceWork &w, bool batch, unsigned long long q, int &job,
@@ -699,7 +716,7 @@ __device__ __forceinline__ void item_target(const TraceWork &w, bool batch, unsi
     const unsigned r = (unsigned)(local - tile * per_tile);
     const unsigned tsz = (unsigned)min(32ull, n - tile * 32ull);
     const unsigned s = r / tsz;
-    j = w.horder.perm[js.hit_prefix + tile * 32ull + (r - s * tsz)];
+    j = js.hit_prefix + tile * 32ull + (r - s * tsz);  // index into the cell-ordered copy
     gs = J.src_off + (int)s;
 }
 
@@ -760,7 +777,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
                     int gs;
                     item_target(w, BATCH, item, job, j, gs);
                     const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
-                    const float4 P = w.hits.p[j], N = w.hits.n[j];
+                    const float4 P = w.shits.p[j], N = w.shits.n[j];
                     const float3 p = xyz(P);
                     const float3 v = xyz(__ldg(w.pos + gs)) - p;
                     const float dist2 = dot(v, v);
@@ -829,7 +846,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_exact(TraceWork w, un
         unsigned long long j;
         item_target(w, w.njobs > 1, w.rerun[i], job, j, gs);
         const SceneView &sc = w.njobs > 1 ? w.jobs[job].sc : w.job0.sc;
-        const float4 P = w.hits.p[j], N = w.hits.n[j], lo = w.hits.plo[j];
+        const float4 P = w.shits.p[j], N = w.shits.n[j], lo = w.hits.plo[w.horder.perm[j]];
         const float4 cs = __ldg(w.pos + gs);
         const D3 pd = {(double)P.x + lo.x, (double)P.y + lo.y, (double)P.z + lo.z};
         const double vx = (double)cs.x - pd.x, vy = (double)cs.y - pd.y, vz = (double)cs.z - pd.z;
@@ -905,6 +922,7 @@ void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st)
     k_hit_cells<<<blocks, 256, 0, st>>>(w);
     launch_scan_u32(w.horder.cnt, w.horder.cnt, w.horder.ncells, st);
     k_hit_scatter<<<blocks, 256, 0, st>>>(w);
+    k_hit_gather<<<blocks, 256, 0, st>>>(w);
 }
 
 template <typename R, bool BATCH>

@@ -225,6 +225,7 @@ __device__ __forceinline__ int traverse(const SceneView &sc, float3 o, float3 d,
     });
     if (FLAG && ambiguous) {
         if (ANY) *ambiguous = !clear && amb_t < INFINITY;
+        else if (best < 0) *ambiguous = amb_t < INFINITY;  // a miss is sensitive only near a tested edge
         else *ambiguous = fminf(amb_t, second) <= bound * (1.0f + AMBIG_T) + tmin;
     }
     t_out = bound;
