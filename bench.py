@@ -226,6 +226,7 @@ def main():
     ctx = rpr.Context(local, stream)
     sc = getattr(scenes, SCENE)()
     scene = rpr.Scene.from_scene(ctx, sc)
+    info = scene.info()
     S, B = sc.num_sources, sc.num_bands
     flags = rpr.RP_FLAG_DEVICE_POSITIONS | (rpr.RP_FLAG_FP32_PATHS if args.fp32_paths else 0)
     base = rpr.TraceParams(**WORKLOAD, flags=flags, scene_id=rank)
@@ -341,6 +342,12 @@ def main():
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
         "updates_per_s": ws * 1000.0 / ms_step,
         "closest_hit_segments_per_step": st["segments"], "shadow_rays_per_step": st["shadow_rays"],
+        "bvh": {"build_ms": round(float(info.build_ms), 2), "max_depth": int(info.max_depth),
+                "nodes": int(info.num_nodes),
+                "node_visits_per_segment": stc["node_visits"][0] / max(1, stc["segments"]),
+                "node_visits_per_shadow_ray": stc["node_visits"][1] / max(1, stc["shadow_rays"]),
+                "tri_tests_per_segment": stc["tri_tests"][0] / max(1, stc["segments"]),
+                "tri_tests_per_shadow_ray": stc["tri_tests"][1] / max(1, stc["shadow_rays"])},
         "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                      "traffic_note": "DRAM bytes per launch, from an ncu capture at 30k primaries scaled by "

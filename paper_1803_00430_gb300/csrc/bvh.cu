@@ -6,11 +6,13 @@
 //   1. per-triangle bounds and centroids, checked for non-finite values;
 //   2. 30-bit Morton codes of the centroids;
 //   3. a stable LSD radix sort (8-bit digits) of (code, triangle) pairs;
-//   4. the binary radix tree of Karras (HPG 2012), one thread per internal node,
-//      with ties between equal codes broken by the leaf index;
-//   5. bottom-up child bounds (one thread per leaf, the second arrival at a node
-//      continues upward);
-//   6. packing into 64-byte nodes holding both children's boxes, and 48-byte
+//   4. the hierarchy by parallel locally-ordered clustering (PLOC, Meister & Bittner,
+//      IEEE TVCG 2018): in Morton order, every cluster finds the neighbour within
+//      +-PLOC_RADIUS positions whose union box has the smallest surface area;
+//      mutual nearest pairs merge into a new node; the survivors are compacted, and
+//      rounds repeat until one cluster is left.  Node ids come from prefix sums
+//      (the root is node 0), so the build is deterministic;
+//   5. packing into 64-byte nodes holding both children's boxes, and 48-byte
 //      triangles in leaf order; per-material constants.
 #include <cstdio>
 #include <vector>
@@ -216,59 +218,105 @@ __global__ void k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *_
     }
 }
 
-// --- 4. Karras radix tree ------------------------------------------------------------
-__device__ __forceinline__ int delta(const uint32_t *__restrict__ codes, int n, int i, int j)
+// --- 4. PLOC hierarchy -------------------------------------------------------------
+constexpr int PLOC_RADIUS = 32;
+
+__device__ __forceinline__ float union_area(float4 al, float4 ah, float4 bl, float4 bh)
 {
-    if (j < 0 || j >= n) return -1;
-    const uint32_t a = codes[i], b = codes[j];
-    if (a == b) return 32 + __clz((uint32_t)i ^ (uint32_t)j);
-    return __clz(a ^ b);
+    const float dx = fmaxf(ah.x, bh.x) - fminf(al.x, bl.x);
+    const float dy = fmaxf(ah.y, bh.y) - fminf(al.y, bl.y);
+    const float dz = fmaxf(ah.z, bh.z) - fminf(al.z, bl.z);
+    return dx * dy + dy * dz + dz * dx;  // half the surface area
 }
 
-__global__ void k_karras(const uint32_t *__restrict__ codes, int n, int2 *__restrict__ child,
-                         int *__restrict__ parent_int, int *__restrict__ parent_leaf)
+// leaves in Morton order as the first clusters
+__global__ void k_ploc_init(int n, const uint32_t *__restrict__ order, const float4 *__restrict__ blo,
+                            const float4 *__restrict__ bhi, int *__restrict__ cref, float4 *__restrict__ clo,
+                            float4 *__restrict__ chi)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    const int d = (delta(codes, n, i, i + 1) - delta(codes, n, i, i - 1)) >= 0 ? 1 : -1;
-    const int dmin = delta(codes, n, i, i - d);
-    int lmax = 2;
-    while (delta(codes, n, i, i + lmax * d) > dmin) lmax <<= 1;
-    int l = 0;
-    for (int t = lmax >> 1; t >= 1; t >>= 1)
-        if (delta(codes, n, i, i + (l + t) * d) > dmin) l += t;
-    const int j = i + l * d;
-    const int dnode = delta(codes, n, i, j);
-    int s = 0;
-    int div = 2;
-    int t = (l + div - 1) / div;
-    while (true) {
-        if (delta(codes, n, i, i + (s + t) * d) > dnode) s += t;
-        if (t <= 1) break;
-        div <<= 1;
-        t = (l + div - 1) / div;
-    }
-    const int gamma = i + s * d + min(d, 0);
-    const int lo = min(i, j), hi = max(i, j);
-    int left, right;
-    if (lo == gamma) {
-        left = ~gamma;
-        parent_leaf[gamma] = i;
-    } else {
-        left = gamma;
-        parent_int[gamma] = i;
-    }
-    if (hi == gamma + 1) {
-        right = ~(gamma + 1);
-        parent_leaf[gamma + 1] = i;
-    } else {
-        right = gamma + 1;
-        parent_int[gamma + 1] = i;
-    }
-    child[i] = make_int2(left, right);
+    if (i >= n) return;
+    const uint32_t t = order[i];
+    cref[i] = ~i;
+    clo[i] = blo[t];
+    chi[i] = bhi[t];
 }
 
-// --- 5. bottom-up bounds ---------------------------------------------------------------
+// nearest neighbour of every cluster within the window; the pair key (area, lower
+// index, higher index) is compared lexicographically, so the smallest pair overall
+// is always mutual and every round merges at least once
+__global__ void k_ploc_nn(int c, const float4 *__restrict__ clo, const float4 *__restrict__ chi,
+                          int *__restrict__ nn)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c) return;
+    const float4 li = clo[i], hi = chi[i];
+    float best = INFINITY;
+    int bj = -1, blo_ = 0, bhi_ = 0;
+    const int j0 = max(0, i - PLOC_RADIUS), j1 = min(c - 1, i + PLOC_RADIUS);
+    for (int j = j0; j <= j1; ++j) {
+        if (j == i) continue;
+        const float a = union_area(li, hi, clo[j], chi[j]);
+        const int lo = min(i, j), hh = max(i, j);
+        if (a < best || (a == best && (lo < blo_ || (lo == blo_ && hh < bhi_)))) {
+            best = a;
+            bj = j;
+            blo_ = lo;
+            bhi_ = hh;
+        }
+    }
+    nn[i] = bj;
+}
+
+// keep[i]: cluster i survives the round (alone, or as the merged pair's lower index);
+// merge[i]: it is the lower index of a mutual pair
+__global__ void k_ploc_flags(int c, const int *__restrict__ nn, uint32_t *__restrict__ keep,
+                             uint32_t *__restrict__ merge)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c) return;
+    const int j = nn[i];
+    const bool mutual = j >= 0 && nn[j] == i;
+    merge[i] = mutual && i < j ? 1u : 0u;
+    keep[i] = mutual && i > j ? 0u : 1u;
+}
+
+// merges (new node id = c - 2 - rank among this round's merges) and compaction
+__global__ void k_ploc_merge(int c, const int *__restrict__ cref, const float4 *__restrict__ clo,
+                             const float4 *__restrict__ chi, const int *__restrict__ nn,
+                             const uint32_t *__restrict__ keep, const uint32_t *__restrict__ kpos,
+                             const uint32_t *__restrict__ merge, const uint32_t *__restrict__ mpos,
+                             int2 *__restrict__ child, float4 *__restrict__ nlo, float4 *__restrict__ nhi,
+                             int *__restrict__ parent_int, int *__restrict__ parent_leaf, int *__restrict__ oref,
+                             float4 *__restrict__ olo, float4 *__restrict__ ohi)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c || !keep[i]) return;
+    const uint32_t pos = kpos[i];
+    if (merge[i]) {
+        const int j = nn[i];
+        const int id = c - 2 - (int)mpos[i];
+        const int a = cref[i], b = cref[j];
+        const float4 al = clo[i], ah = chi[i], bl = clo[j], bh = chi[j];
+        const float4 lo = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.f);
+        const float4 hi = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f);
+        child[id] = make_int2(a, b);
+        nlo[id] = lo;
+        nhi[id] = hi;
+        if (a < 0) parent_leaf[~a] = id;
+        else parent_int[a] = id;
+        if (b < 0) parent_leaf[~b] = id;
+        else parent_int[b] = id;
+        oref[pos] = id;
+        olo[pos] = lo;
+        ohi[pos] = hi;
+    } else {
+        oref[pos] = cref[i];
+        olo[pos] = clo[i];
+        ohi[pos] = chi[i];
+    }
+}
+
 __device__ __forceinline__ void child_box(int c, const uint32_t *__restrict__ order,
                                           const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
                                           const float4 *nlo, const float4 *nhi, float4 &lo, float4 &hi)
@@ -278,31 +326,8 @@ __device__ __forceinline__ void child_box(int c, const uint32_t *__restrict__ or
         lo = blo[t];
         hi = bhi[t];
     } else {
-        lo = __ldcg(nlo + c);
-        hi = __ldcg(nhi + c);
-    }
-}
-
-__global__ void k_bounds(int n, const uint32_t *__restrict__ order, const float4 *__restrict__ blo,
-                         const float4 *__restrict__ bhi, const int2 *__restrict__ child,
-                         const int *__restrict__ parent_int, const int *__restrict__ parent_leaf,
-                         int *__restrict__ flags, float4 *nlo, float4 *nhi)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int p = parent_leaf[i];
-    int guard = 0;
-    while (p >= 0 && p < n - 1 && guard++ < 4096) {
-        __threadfence();
-        if (atomicAdd(&flags[p], 1) == 0) return;  // the sibling subtree finishes this node
-        const int2 c = child[p];
-        float4 l0, h0, l1, h1;
-        child_box(c.x, order, blo, bhi, nlo, nhi, l0, h0);
-        child_box(c.y, order, blo, bhi, nlo, nhi, l1, h1);
-        __stcg(nlo + p, make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f));
-        __stcg(nhi + p, make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f));
-        if (p == 0) return;
-        p = parent_int[p];
+        lo = nlo[c];
+        hi = nhi[c];
     }
 }
 
@@ -410,7 +435,9 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
     float *partial = nullptr, *bounds = nullptr;
     uint32_t *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr;
     int2 *child = nullptr;
-    int *pint = nullptr, *pleaf = nullptr, *flags = nullptr, *depth = nullptr;
+    int *pint = nullptr, *pleaf = nullptr, *depth = nullptr, *nn = nullptr, *cref[2] = {nullptr, nullptr};
+    float4 *clo[2] = {nullptr, nullptr}, *chi[2] = {nullptr, nullptr};
+    uint32_t *keep = nullptr, *kpos = nullptr, *merge = nullptr, *mpos = nullptr;
     float hb[12];
     int hdepth = 0;
     RP_TRY(dalloc(&blo, nt));
@@ -425,7 +452,16 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
     RP_TRY(dalloc(&child, nt));
     RP_TRY(dalloc(&pint, nt));
     RP_TRY(dalloc(&pleaf, nt));
-    RP_TRY(dalloc(&flags, nt));
+    RP_TRY(dalloc(&nn, nt));
+    for (int b = 0; b < 2; ++b) {
+        RP_TRY(dalloc(&cref[b], nt));
+        RP_TRY(dalloc(&clo[b], nt));
+        RP_TRY(dalloc(&chi[b], nt));
+    }
+    RP_TRY(dalloc(&keep, nt + 1));
+    RP_TRY(dalloc(&kpos, nt + 1));
+    RP_TRY(dalloc(&merge, nt + 1));
+    RP_TRY(dalloc(&mpos, nt + 1));
     RP_TRY(dalloc(&nlo, nt));
     RP_TRY(dalloc(&nhi, nt));
     RP_TRY(dalloc(&depth, 1));
@@ -451,11 +487,28 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
     }
     RP_TRY(cudaMemsetAsync(pint, 0xff, sizeof(int) * nt, st));
     RP_TRY(cudaMemsetAsync(pleaf, 0xff, sizeof(int) * nt, st));
-    RP_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * nt, st));
     RP_TRY(cudaMemsetAsync(depth, 0, sizeof(int), st));
     if (nt > 1) {
-        k_karras<<<(nt - 1 + 255) / 256, 256, 0, st>>>(k0, nt, child, pint, pleaf);
-        k_bounds<<<nblk_tri, 256, 0, st>>>(nt, v0, blo, bhi, child, pint, pleaf, flags, nlo, nhi);
+        k_ploc_init<<<nblk_tri, 256, 0, st>>>(nt, v0, blo, bhi, cref[0], clo[0], chi[0]);
+        int c = nt, cur = 0;
+        for (int round = 0; c > 1; ++round) {
+            const int nb = (c + 255) / 256;
+            k_ploc_nn<<<nb, 256, 0, st>>>(c, clo[cur], chi[cur], nn);
+            k_ploc_flags<<<nb, 256, 0, st>>>(c, nn, keep, merge);
+            launch_scan_u32(keep, kpos, c, st);
+            launch_scan_u32(merge, mpos, c, st);
+            k_ploc_merge<<<nb, 256, 0, st>>>(c, cref[cur], clo[cur], chi[cur], nn, keep, kpos, merge, mpos, child,
+                                             nlo, nhi, pint, pleaf, cref[1 - cur], clo[1 - cur], chi[1 - cur]);
+            uint32_t next = 0;
+            RP_TRY(cudaMemcpyAsync(&next, kpos + c, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            RP_TRY(cudaStreamSynchronize(st));
+            if ((int)next >= c || round > nt) {  // no merge: cannot happen (see k_ploc_nn)
+                err = cudaErrorUnknown;
+                goto done;
+            }
+            c = (int)next;
+            cur = 1 - cur;
+        }
         k_depth<<<nblk_tri, 256, 0, st>>>(nt, pint, pleaf, depth);
     }
     RP_TRY(cudaGetLastError());
@@ -490,7 +543,13 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
 done:
     cudaFree(blo); cudaFree(bhi); cudaFree(partial); cudaFree(bounds);
     cudaFree(k0); cudaFree(v0); cudaFree(k1); cudaFree(v1); cudaFree(hist);
-    cudaFree(child); cudaFree(pint); cudaFree(pleaf); cudaFree(flags);
+    cudaFree(child); cudaFree(pint); cudaFree(pleaf); cudaFree(nn);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(cref[b]);
+        cudaFree(clo[b]);
+        cudaFree(chi[b]);
+    }
+    cudaFree(keep); cudaFree(kpos); cudaFree(merge); cudaFree(mpos);
     cudaFree(nlo); cudaFree(nhi); cudaFree(depth);
     return err;
 }
