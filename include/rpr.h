@@ -77,9 +77,17 @@ enum {
                                   triangle sequence (debug/divergence checks) */
     RP_FLAG_COUNT_VISITS = 2,  /* count BVH node visits and triangle tests in stats */
     RP_FLAG_DEVICE_POSITIONS = 4, /* listener and sources are device pointers */
-    RP_FLAG_FP32_PATHS = 8       /* carry path origin, direction and length in FP32 instead
+    RP_FLAG_FP32_PATHS = 8,      /* carry path origin, direction and length in FP32 instead
                                     of FP64 (faster; paths drift from the FP64 reference
                                     after tens of reflections) */
+    RP_FLAG_SHADOW_PACKETS = 16, /* trace shadow rays as warp packets (32 rays from nearby
+                                    reflections to one source walk the BVH together) */
+    RP_FLAG_SHADOW_LANES = 32    /* trace shadow rays one per lane, each lane taking a new
+                                    ray as soon as its own ends.  Neither flag: packets when
+                                    the scene has fewer than 2^19 triangles, lanes otherwise
+                                    (long, mostly blocked rays in large scenes leave packet
+                                    lanes idle).  Both flags: RP_ERR_INVALID_ARG.  The two
+                                    modes give the same answers. */
 };
 
 typedef struct rp_ctx rp_ctx;
@@ -286,6 +294,8 @@ typedef struct {
     int32_t shadow_steps;          /* BVH nodes a shadow-ray lane visits between refills, 1..64 */
     int32_t paths_blocks_per_sm;   /* persistent grid of the paths kernel, 1..occupancy */
     int32_t shadow_blocks_per_sm;  /* persistent grid of the shadow-ray kernel, 1..occupancy */
+    int32_t shadow_mode;           /* 0: by scene size (see RP_FLAG_SHADOW_LANES), 1: packets,
+                                      2: one ray per lane */
 } rp_batch_tuning;
 
 typedef struct {
@@ -326,11 +336,11 @@ int rp_batch_set_tuning(rp_batch *batch, const rp_batch_tuning *tuning);
 int rp_batch_get_tuning(const rp_batch *batch, rp_batch_tuning *tuning);
 int rp_batch_info_get(const rp_batch *batch, rp_batch_info *out);
 
-/* Time launch shapes on this batch (coordinate descent over shadow_steps {4,8,16},
- * chunk_rays {64,256,1024} and full or half persistent grids, two runs each) and
- * apply the fastest.  cache_path (or NULL) is a text file of
- * "key chunk steps paths_blocks shadow_blocks ms" lines keyed by device, SM count
- * and batch shape; a cached entry is applied without timing. */
+/* Time launch shapes on this batch (coordinate descent over the shadow-ray mode
+ * {packets, lanes}, shadow_steps {4,8,16}, chunk_rays {64,256,1024} and full or half
+ * persistent grids, two runs each) and apply the fastest.  cache_path (or NULL) is a
+ * text file of "key chunk steps paths_blocks shadow_blocks mode ms" lines keyed by
+ * device, SM count and batch shape; a cached entry is applied without timing. */
 int rp_batch_autotune(rp_batch *batch, uint64_t seed, const char *cache_path,
                       rp_batch_tuning *best, double *best_ms);
 

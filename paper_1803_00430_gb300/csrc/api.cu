@@ -218,6 +218,7 @@ int check_params(const rp_scene *sc, const rp_trace_params *p, int S)
     if (S < 0 || S > RP_MAX_SOURCES) return RP_ERR_INVALID_ARG;
     if (p->max_order < 0 || p->sh_order < 0 || p->sh_order > RP_MAX_SH_ORDER) return RP_ERR_INVALID_ARG;
     if (p->num_bins < 1 || p->min_order < 0) return RP_ERR_INVALID_ARG;
+    if ((p->flags & RP_FLAG_SHADOW_PACKETS) && (p->flags & RP_FLAG_SHADOW_LANES)) return RP_ERR_INVALID_ARG;
     if ((unsigned long long)S * (unsigned long long)p->num_bins >= (1ull << 31)) return RP_ERR_INVALID_ARG;
     if (p->num_rays > 0xffffffffull || p->first_ray + p->num_rays > 0x100000000ull) return RP_ERR_INVALID_ARG;
     if (p->num_rays * (unsigned long long)std::max(p->max_order, 1) >= (1ull << 40)) return RP_ERR_INVALID_ARG;
@@ -519,6 +520,7 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
     w.H = H;
     w.direct = direct;
     w.shadow_steps = c->shadow_steps;
+    w.shadow_packets = shadow_packets_for(p->flags, sc->num_tris);
 
     StepLaunch L;
     L.w = w;

@@ -225,6 +225,12 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
     w.H = b->H;
     w.direct = b->direct;
     w.shadow_steps = b->tuning.shadow_steps;
+    {
+        int max_tris = 0;
+        for (int j = g.job_begin; j < g.job_end; ++j) max_tris = std::max(max_tris, b->h_jobs[j].sc.num_tris);
+        const int mode = b->tuning.shadow_mode;
+        w.shadow_packets = mode == 1 ? 1 : mode == 2 ? 0 : shadow_packets_for(b->common.flags, max_tris);
+    }
     L.n_rec_chunks = g.z.n_chunks;
     L.refill = 0;
     L.reset_stats = &g == &b->groups.front();
@@ -323,8 +329,8 @@ bool cache_lookup(const char *path, const std::string &key, rp_batch_tuning &t, 
         char k[600];
         rp_batch_tuning x;
         double m;
-        if (sscanf(line, "%599s %d %d %d %d %lf", k, &x.chunk_rays, &x.shadow_steps, &x.paths_blocks_per_sm,
-                   &x.shadow_blocks_per_sm, &m) == 6 &&
+        if (sscanf(line, "%599s %d %d %d %d %d %lf", k, &x.chunk_rays, &x.shadow_steps, &x.paths_blocks_per_sm,
+                   &x.shadow_blocks_per_sm, &x.shadow_mode, &m) == 7 &&
             key == k) {
             t = x;
             ms = m;
@@ -340,8 +346,8 @@ void cache_store(const char *path, const std::string &key, const rp_batch_tuning
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), t.chunk_rays, t.shadow_steps, t.paths_blocks_per_sm,
-            t.shadow_blocks_per_sm, ms);
+    fprintf(f, "%s %d %d %d %d %d %.6f\n", key.c_str(), t.chunk_rays, t.shadow_steps, t.paths_blocks_per_sm,
+            t.shadow_blocks_per_sm, t.shadow_mode, ms);
     fclose(f);
 }
 
@@ -350,7 +356,7 @@ bool tuning_valid(const rp_batch *b, const rp_batch_tuning &t)
     const int pocc = paths_occupancy(b->common.flags), socc = shadow_occupancy(b->common.flags);
     return t.chunk_rays >= 32 && t.chunk_rays <= 65536 && t.shadow_steps >= 1 && t.shadow_steps <= 64 &&
            t.paths_blocks_per_sm >= 1 && t.paths_blocks_per_sm <= pocc && t.shadow_blocks_per_sm >= 1 &&
-           t.shadow_blocks_per_sm <= socc;
+           t.shadow_blocks_per_sm <= socc && t.shadow_mode >= 0 && t.shadow_mode <= 2;
 }
 
 }  // namespace
@@ -364,6 +370,7 @@ int rp_batch_create(rp_ctx *c, const rp_batch_item *items, int32_t n, const rp_t
     if (!c || !items || n <= 0 || !p || !H || !direct || !out || (params && !est)) return RP_ERR_INVALID_ARG;
     *out = nullptr;
     if (p->budget_refill || (p->flags & (RP_FLAG_RAY_HASH | RP_FLAG_DEVICE_POSITIONS))) return RP_ERR_INVALID_ARG;
+    if ((p->flags & RP_FLAG_SHADOW_PACKETS) && (p->flags & RP_FLAG_SHADOW_LANES)) return RP_ERR_INVALID_ARG;
     if (p->max_order < 0 || p->sh_order < 0 || p->sh_order > RP_MAX_SH_ORDER || p->num_bins < 1 ||
         p->min_order < 0 || !(p->ir_rate_hz > 0.f) || !(p->speed_of_sound > 0.f) || !(p->source_radius > 0.f))
         return RP_ERR_INVALID_ARG;
@@ -399,7 +406,7 @@ int rp_batch_create(rp_ctx *c, const rp_batch_item *items, int32_t n, const rp_t
     b->direct = direct;
     b->params = params;
     b->stats = stats;
-    b->tuning = {256, c->shadow_steps, paths_occupancy(p->flags), shadow_occupancy(p->flags)};
+    b->tuning = {256, c->shadow_steps, paths_occupancy(p->flags), shadow_occupancy(p->flags), 0};
     const int M = p->max_order;
     // jobs, positions (all sources, then one listener per job), source -> job
     std::vector<float4> pos((size_t)S_total + n);
@@ -590,12 +597,14 @@ int rp_batch_autotune(rp_batch *b, uint64_t seed, const char *cache_path, rp_bat
         const std::vector<int> chunks = {64, 256, 1024};
         const std::vector<int> pb = {pocc, std::max(1, pocc / 2)};
         const std::vector<int> sb = {socc, std::max(1, socc / 2)};
-        for (int knob = 0; knob < 4; ++knob) {
-            const std::vector<int> &cand = knob == 0 ? steps : knob == 1 ? chunks : knob == 2 ? pb : sb;
+        const std::vector<int> modes = {1, 2};
+        for (int knob = 0; knob < 5; ++knob) {
+            const std::vector<int> &cand = knob == 0 ? modes : knob == 1 ? steps : knob == 2 ? chunks
+                                         : knob == 3 ? pb : sb;
             for (int v : cand) {
                 rp_batch_tuning x = cur;
-                int &field = knob == 0 ? x.shadow_steps : knob == 1 ? x.chunk_rays
-                                       : knob == 2 ? x.paths_blocks_per_sm : x.shadow_blocks_per_sm;
+                int &field = knob == 0 ? x.shadow_mode : knob == 1 ? x.shadow_steps : knob == 2 ? x.chunk_rays
+                                       : knob == 3 ? x.paths_blocks_per_sm : x.shadow_blocks_per_sm;
                 if (field == v) continue;
                 field = v;
                 if (!tuning_valid(b, x)) continue;

@@ -164,6 +164,15 @@ inline int hit_order_bits(int njobs)
 }
 inline long long hit_order_cells(int njobs) { return (long long)std::max(njobs, 1) << (3 * hit_order_bits(njobs)); }
 
+// shadow-ray mode of a step: the flags, else packets below PACKET_MAX_TRIS triangles
+constexpr int PACKET_MAX_TRIS = 1 << 19;
+inline int shadow_packets_for(int flags, int max_tris)
+{
+    if (flags & RP_FLAG_SHADOW_PACKETS) return 1;
+    if (flags & RP_FLAG_SHADOW_LANES) return 0;
+    return max_tris < PACKET_MAX_TRIS ? 1 : 0;
+}
+
 struct TraceWork {
     SceneJob job0;         // the first (in single-job steps the only) job, by value
     const SceneJob *jobs;  // [njobs], device
@@ -196,6 +205,7 @@ struct TraceWork {
     int num_sms;
     int shadow_steps;  // node visits a shadow lane makes between refills
     HitOrder horder;   // reflections in spatial order for coherent shadow rays
+    int shadow_packets;  // 1: shadow rays as warp packets, 0: one ray per lane
     Hits shits;        // point, normal, weights and ray id of the reflections in that order (shadow
                        // rays read these; the FP64 residuals stay in `hits`, found through horder.perm)
 };

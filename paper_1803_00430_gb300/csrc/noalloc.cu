@@ -90,6 +90,7 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     if (p->max_order < 0 || p->sh_order < 0 || p->sh_order > RP_MAX_SH_ORDER || p->num_bins < 1 || p->min_order < 0)
         return RP_ERR_INVALID_ARG;
     if (p->num_rays > 0xffffffffull || p->first_ray + p->num_rays > 0x100000000ull) return RP_ERR_INVALID_ARG;
+    if ((p->flags & RP_FLAG_SHADOW_PACKETS) && (p->flags & RP_FLAG_SHADOW_LANES)) return RP_ERR_INVALID_ARG;
     if (!(p->ir_rate_hz > 0.f) || !(p->speed_of_sound > 0.f) || !(p->source_radius > 0.f)) return RP_ERR_INVALID_ARG;
     if (!std::isfinite(p->ir_rate_hz) || !std::isfinite(p->speed_of_sound) || !std::isfinite(p->source_radius))
         return RP_ERR_NAN_INPUT;
@@ -203,6 +204,7 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.rerun_cap = z.rerun_cap;
     w.num_sms = c->num_sms;
     w.shadow_steps = c->shadow_steps;
+    w.shadow_packets = shadow_packets_for(p->flags, sc->num_tris);
     w.shits = {(float4 *)(base + o_sp), nullptr, (float4 *)(base + o_sn), (float *)(base + o_sw),
                (uint32_t *)(base + o_sr), z.hit_cap};
     w.horder = {(uint32_t *)(base + o_hc), (uint32_t *)(base + o_sq), (uint32_t *)(base + o_hk), hit_order_bits(1),

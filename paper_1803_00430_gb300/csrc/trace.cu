@@ -830,6 +830,188 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
     acc_flush(acc, w.stats, w.k.B, 1);
 }
 
+// Shadow rays as packets.  A warp takes 32 consecutive items -- in the cell-ordered
+// tiles, rays from nearby points towards one source -- and walks the BVH with them
+// together: one node fetch per warp, and a stack of the warp's own in shared memory
+// whose entries carry the mask of lanes whose ray reached the node.  A lane tests only
+// the nodes its own ray reaches and leaves the walk once it has a clear blocker, so its
+// answer is the single-ray answer of any_hit_steps.  Items of different jobs in one
+// packet walk their own BVHs one after the other.
+template <bool COUNT, bool EXACT, bool BATCH>
+__global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_packet(TraceWork w, unsigned long long chunk)
+{
+    __shared__ int pnode[SHADOW_THREADS / 32][STACK_DEPTH];
+    __shared__ unsigned pmask[SHADOW_THREADS / 32][STACK_DEPTH];
+    __shared__ BlockAcc acc;
+    acc_init(acc);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long total = w.ctr->total_items;
+    const unsigned long long q0 = chunk * w.items_per_chunk;
+    const unsigned long long items = total > q0 ? min(w.items_per_chunk, total - q0) : 0ull;
+    const float inv_pi = 1.0f / PI_F;
+    unsigned long long shadow = 0, contrib = 0;
+    TravStats ts = {0u, 0u};
+    int *const sn = pnode[wid];
+    unsigned *const sm = pmask[wid];
+
+    while (true) {
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&w.ctr->next_item, 32ull);
+        b0 = __shfl_sync(FULL, b0, 0);
+        if (b0 >= items) break;
+        const unsigned long long item = q0 + b0 + lane;
+        bool traced = false;  // this lane traces a shadow ray
+        int job = 0;
+        AnyRay ray;
+        float3 dir = mk3(0.f, 0.f, 0.f);
+        float f = 0.f, dist = 0.f;
+        AnyState st = {-1, 0, INFINITY, false, false};
+        if (b0 + lane < items) {
+            unsigned long long j;
+            int gs;
+            item_target(w, BATCH, item, job, j, gs);
+            const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
+            const float4 P = w.shits.p[j], N = w.shits.n[j];
+            const float3 p = xyz(P);
+            const float3 v = xyz(__ldg(w.pos + gs)) - p;
+            const float dist2 = dot(v, v);
+            dist = sqrtf(dist2);
+            const float cth = dot(xyz(N), v) / dist;
+            if (cth > 0.f) {
+                ++shadow;
+                dir = v * (1.0f / dist);
+                ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
+                f = cth * inv_pi / dist2;
+                traced = true;
+            }
+        }
+        const float tlo = ray.tmin * (1.0f - AMBIG_T), tnear = ray.tmin * (1.0f + AMBIG_T);
+        bool fin = !traced;  // the lane has its answer
+        unsigned todo = __ballot_sync(FULL, traced);
+        while (todo) {
+            // the lanes of one job walk that job's BVH
+            const int leader = __ffs(todo) - 1;
+            const int jl = __shfl_sync(FULL, job, leader);
+            const unsigned grp = __ballot_sync(FULL, traced && job == jl) & todo;
+            todo &= ~grp;
+            const SceneView &sc = BATCH ? w.jobs[jl].sc : w.job0.sc;
+            auto leaf = [&](int tri) {  // the lane's any-hit test of one triangle
+                if (COUNT) ts.tris++;
+                if ((unsigned)tri >= (unsigned)sc.num_tris) {
+                    raise_error(w.status, RP_ERR_INVALID_ARG);
+                    fin = true;
+                    return;
+                }
+                if (tri == ray.exclude) return;
+                float t, margin;
+                uint32_t orig;
+                const bool inside = tri_intersect(sc.tris, tri, ray.o, dir, t, orig, margin);
+                if (EXACT && t > tlo && t < ray.tmax * (1.0f + AMBIG_T) &&
+                    (fabsf(margin) < AMBIG_BARY || (inside && t < tnear)))
+                    st.amb_t = fminf(st.amb_t, t);
+                if (!inside || !(t > ray.tmin) || !(t < ray.tmax)) return;
+                st.blocked = true;
+                if (!EXACT || (fabsf(margin) >= AMBIG_BARY && t >= tnear)) {
+                    st.clear = true;
+                    fin = true;
+                }
+            };
+            if (sc.num_nodes == 0) {
+                if (((grp >> lane) & 1u) && sc.num_tris > 0) leaf(0);
+                continue;
+            }
+            const int iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
+            int node = 0, sp = 0, iters = 0;
+            unsigned mask = grp;
+            while (true) {
+                mask &= ~__ballot_sync(FULL, fin);
+                if (mask == 0) {
+                    if (sp == 0) break;
+                    --sp;
+                    node = sn[sp];
+                    mask = sm[sp];
+                    continue;
+                }
+                if (++iters > iter_cap) {
+                    if (lane == 0) raise_error(w.status, RP_ERR_TIMEOUT);
+                    break;
+                }
+                if ((unsigned)node >= (unsigned)sc.num_nodes) {
+                    if (lane == 0) raise_error(w.status, RP_ERR_INVALID_ARG);
+                    break;
+                }
+                const bool need = (mask >> lane) & 1u;
+                if (COUNT && need) ts.nodes++;
+                const float4 *np = sc.nodes + 4 * node;
+                const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+                const float a0 = n0.x * ray.idir.x - ray.ood.x, b0 = n0.y * ray.idir.x - ray.ood.x;
+                const float a1 = n0.z * ray.idir.y - ray.ood.y, b1 = n0.w * ray.idir.y - ray.ood.y;
+                const float a2 = n2.x * ray.idir.z - ray.ood.z, b2 = n2.y * ray.idir.z - ray.ood.z;
+                const float c0min = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), ray.tmin));
+                const float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), ray.tmax));
+                const float a3 = n1.x * ray.idir.x - ray.ood.x, b3 = n1.y * ray.idir.x - ray.ood.x;
+                const float a4 = n1.z * ray.idir.y - ray.ood.y, b4 = n1.w * ray.idir.y - ray.ood.y;
+                const float a5 = n2.z * ray.idir.z - ray.ood.z, b5 = n2.w * ray.idir.z - ray.ood.z;
+                const float c1min = fmaxf(fmaxf(fminf(a3, b3), fminf(a4, b4)), fmaxf(fminf(a5, b5), ray.tmin));
+                const float c1max = fminf(fminf(fmaxf(a3, b3), fmaxf(a4, b4)), fminf(fmaxf(a5, b5), ray.tmax));
+                const bool h0 = need && c0min <= c0max, h1 = need && c1min <= c1max;
+                const int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
+                if (h0 && ch0 < 0) leaf(~ch0);
+                if (h1 && ch1 < 0 && !fin) leaf(~ch1);
+                const unsigned m0 = __ballot_sync(FULL, h0 && ch0 >= 0 && !fin);
+                const unsigned m1 = __ballot_sync(FULL, h1 && ch1 >= 0 && !fin);
+                if (m0 && m1) {
+                    // the nearer child for most of the lanes that reach both goes first
+                    const unsigned both = m0 & m1;
+                    const unsigned later = __ballot_sync(FULL, ((both >> lane) & 1u) && c1min < c0min);
+                    const bool swap = both ? 2 * __popc(later) > __popc(both) : false;
+                    if (sp >= STACK_DEPTH) {
+                        if (lane == 0) raise_error(w.status, RP_ERR_STACK_OVERFLOW);
+                        break;
+                    }
+                    if (lane == 0) {
+                        sn[sp] = swap ? ch0 : ch1;
+                        sm[sp] = swap ? m0 : m1;
+                    }
+                    __syncwarp();
+                    ++sp;
+                    node = swap ? ch1 : ch0;
+                    mask = swap ? m1 : m0;
+                } else if (m0) {
+                    node = ch0;
+                    mask = m0;
+                } else if (m1) {
+                    node = ch1;
+                    mask = m1;
+                } else {
+                    mask = 0;
+                }
+            }
+            __syncwarp();
+        }
+        if (!traced) continue;
+        const bool amb = EXACT && !st.clear && st.amb_t < INFINITY;
+        if (amb) {
+            const unsigned long long r = warp_append(&w.ctr->n_rerun);
+            if (r < w.rerun_cap) {
+                w.rerun[r] = item;
+                continue;
+            }
+        }
+        if (!st.blocked) {
+            unsigned long long j;
+            int gs, jb;
+            item_target(w, BATCH, item, jb, j, gs);
+            ++contrib;
+            shadow_contribution(w, acc, j, gs, f, dist);
+        }
+    }
+    acc_counters(acc, 0.0, 0.0, 0ull, 0ull, 0ull, shadow, contrib, 0ull, ts);
+    acc_flush(acc, w.stats, w.k.B, 1);
+}
+
 // FP64 decisions for the shadow rays whose FP32 visibility was rounding-sensitive
 __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_exact(TraceWork w, unsigned long long chunk)
 {
@@ -953,6 +1135,13 @@ void launch_shadow_b(const TraceWork &w, unsigned long long chunk, int blocks, c
 {
     const bool count = (w.k.flags & RP_FLAG_COUNT_VISITS) != 0;
     const bool exact = (w.k.flags & RP_FLAG_FP32_PATHS) == 0;
+    if (w.shadow_packets) {
+        if (count && exact) k_shadow_packet<true, true, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+        else if (count) k_shadow_packet<true, false, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+        else if (exact) k_shadow_packet<false, true, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+        else k_shadow_packet<false, false, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+        return;
+    }
     if (count && exact) k_shadow<true, true, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
     else if (count) k_shadow<true, false, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
     else if (exact) k_shadow<false, true, BATCH><<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
@@ -987,11 +1176,16 @@ int paths_occupancy(int flags)
 
 int shadow_occupancy(int flags)
 {
-    int n = 0;
-    if (flags & RP_FLAG_FP32_PATHS)
+    // the persistent grid must fit both shadow-ray kernels
+    int n = 0, m = 0;
+    if (flags & RP_FLAG_FP32_PATHS) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false, false, false>, SHADOW_THREADS, 0);
-    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_shadow_packet<false, false, false>, SHADOW_THREADS, 0);
+    } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_shadow<false, true, false>, SHADOW_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_shadow_packet<false, true, false>, SHADOW_THREADS, 0);
+    }
+    n = std::min(n, m);
     return n > 0 ? n : 1;
 }
 

@@ -34,6 +34,7 @@ STATUS = {
 RP_ERR = {v: k for k, v in STATUS.items()}
 RP_MEM_HOST, RP_MEM_DEVICE = 0, 1
 RP_FLAG_RAY_HASH, RP_FLAG_COUNT_VISITS, RP_FLAG_DEVICE_POSITIONS, RP_FLAG_FP32_PATHS = 1, 2, 4, 8
+RP_FLAG_SHADOW_PACKETS, RP_FLAG_SHADOW_LANES = 16, 32
 
 
 class rp_mesh_desc(C.Structure):
@@ -93,7 +94,7 @@ class rp_batch_item(C.Structure):
 
 class rp_batch_tuning(C.Structure):
     _fields_ = [("chunk_rays", C.c_int32), ("shadow_steps", C.c_int32), ("paths_blocks_per_sm", C.c_int32),
-                ("shadow_blocks_per_sm", C.c_int32)]
+                ("shadow_blocks_per_sm", C.c_int32), ("shadow_mode", C.c_int32)]
 
 
 class rp_batch_info(C.Structure):

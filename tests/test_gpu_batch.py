@@ -119,18 +119,30 @@ def test_autotune_applies_and_caches(ctx, tmp_path):
     b = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
     cache = str(tmp_path / "autotune.txt")
     t, ms = b.autotune(seed=3, cache_path=cache)
-    assert ms > 0 and t.shadow_steps in (4, 8, 16) and t.chunk_rays in (64, 256, 1024)
+    assert ms > 0 and t.shadow_steps in (4, 8, 16) and t.chunk_rays in (64, 256, 1024) and t.shadow_mode in (0, 1, 2)
     got = b.tuning()
     assert (got.chunk_rays, got.shadow_steps) == (t.chunk_rays, t.shadow_steps)
     assert os.path.exists(cache) and len(open(cache).read().splitlines()) == 1
     # a second batch of the same shape takes the cached entry without timing
     b2 = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
     t2, ms2 = b2.autotune(seed=3, cache_path=cache)
-    assert (t2.chunk_rays, t2.shadow_steps, t2.paths_blocks_per_sm) == (t.chunk_rays, t.shadow_steps,
-                                                                         t.paths_blocks_per_sm)
+    assert (t2.chunk_rays, t2.shadow_steps, t2.paths_blocks_per_sm, t2.shadow_mode) == (
+        t.chunk_rays, t.shadow_steps, t.paths_blocks_per_sm, t.shadow_mode)
     assert len(open(cache).read().splitlines()) == 1
     b2.run(seed=3)
     _check_items(b2, its, ctx, 3)
+
+
+@pytest.mark.parametrize("mode", [1, 2], ids=["packets", "lanes"])
+def test_batch_shadow_modes_agree(ctx, mode):
+    its = _items(ctx, n=4, seed=scenes.SEED_BATCHED + 21)
+    p = rpr.TraceParams(**P)
+    b = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    t = b.tuning()
+    t.shadow_mode = mode
+    b.set_tuning(t)
+    b.run(seed=13, use_graph=True)
+    _check_items(b, its, ctx, 13)
 
 
 def test_batch_rejects_bad_input(ctx):

@@ -91,10 +91,12 @@ def test_estimator_smoothing_state_and_edge_rows(ctx):
     np.testing.assert_allclose(state.cpu().numpy(), sto, rtol=1e-9, equal_nan=True)
 
 
-def test_medium_hall_parity_reduced_rays(ctx):
+@pytest.mark.parametrize("mode", [0, rpr.RP_FLAG_SHADOW_PACKETS, rpr.RP_FLAG_SHADOW_LANES],
+                         ids=["auto", "packets", "lanes"])
+def test_medium_hall_parity_reduced_rays(ctx, mode):
     sc = scenes.furnished_hall()
     p = rpr.TraceParams(num_rays=20000, max_order=64, sh_order=2, num_bins=2000, min_order=1,
-                        seed=scenes.PHILOX_KEY_BASE + 1)
+                        seed=scenes.PHILOX_KEY_BASE + 1, flags=mode)
     g = pu.run_gpu(ctx, sc, p)
     o = pu.run_oracle(sc, p)
     rep = pu.assert_parity(g, o, p.num_rays, check_params=False)
@@ -248,7 +250,8 @@ def test_error_paths(ctx):
         rpr.Scene(ctx, sc.verts, sc.tris, sc.tri_material, bada, sc.scattering)
     assert e.value.status == rpr.RP_ERR["RP_ERR_INVALID_ARG"]
     scene = rpr.Scene.from_scene(ctx, sc)
-    for kw in (dict(sh_order=4), dict(num_bins=0), dict(max_order=-1), dict(source_radius=0.0)):
+    for kw in (dict(sh_order=4), dict(num_bins=0), dict(max_order=-1), dict(source_radius=0.0),
+               dict(flags=rpr.RP_FLAG_SHADOW_PACKETS | rpr.RP_FLAG_SHADOW_LANES)):
         with pytest.raises(rpr.RprError) as e:
             rpr.trace(scene, rpr.TraceParams(**{**TINY, **kw}), sc.listener, sc.sources)
         assert e.value.status == rpr.RP_ERR["RP_ERR_INVALID_ARG"]
