@@ -46,10 +46,11 @@ WORKLOAD_NAME = ("medium: furnished hall 40x30x12 m + 2000 boxes (24,012 tris), 
                  "200k rays x 64 reflections, IR 2 s @ 1 kHz, SH order 2")
 FLOPS_PER_NODE = 24.0   # slab tests of two children
 FLOPS_PER_TRI = 27.0    # Moller-Trumbore
-# DRAM bytes (read + write) of one k_shadow launch in an ncu capture of the same
-# update at 30,000 primaries, and the shadow rays that launch traced; a full-size
-# launch is credited with the same bytes per shadow ray.
-NCU_SHADOW_DRAM = (560_882_432 + 43_546_624, 18_878_384)
+# DRAM bytes (read + write) of one shadow-ray launch (k_shadow_packet, the mode this
+# scene uses) in an ncu capture of the same update at 30,000 primaries, and the
+# shadow rays that launch traced; a full-size launch is credited with the same bytes
+# per shadow ray.
+NCU_SHADOW_DRAM = (97_133_568 + 19_801_088, 18_878_384)
 
 
 def _peaks():

@@ -80,14 +80,14 @@ __device__ __forceinline__ void acc_flush(BlockAcc &a, rp_trace_stats *st, int B
     if (t == 0) {
         if (a.mfp != 0.0) atomicAdd(&st->mfp_sum, a.mfp);
         if (a.mfp_np != 0.0) atomicAdd(&st->mfp_sum_np, a.mfp_np);
-        atomicAdd((unsigned long long *)&st->mfp_count, a.mfp_cnt);
-        atomicAdd((unsigned long long *)&st->mfp_count_np, a.mfp_cnt_np);
-        atomicAdd((unsigned long long *)&st->segments, a.segs);
-        atomicAdd((unsigned long long *)&st->shadow_rays, a.shadow);
-        atomicAdd((unsigned long long *)&st->contributions, a.contrib);
-        atomicAdd((unsigned long long *)&st->sphere_hits, a.sphere);
-        atomicAdd((unsigned long long *)&st->node_visits[which], a.nodes);
-        atomicAdd((unsigned long long *)&st->tri_tests[which], a.tris);
+        if (a.mfp_cnt) atomicAdd((unsigned long long *)&st->mfp_count, a.mfp_cnt);
+        if (a.mfp_cnt_np) atomicAdd((unsigned long long *)&st->mfp_count_np, a.mfp_cnt_np);
+        if (a.segs) atomicAdd((unsigned long long *)&st->segments, a.segs);
+        if (a.shadow) atomicAdd((unsigned long long *)&st->shadow_rays, a.shadow);
+        if (a.contrib) atomicAdd((unsigned long long *)&st->contributions, a.contrib);
+        if (a.sphere) atomicAdd((unsigned long long *)&st->sphere_hits, a.sphere);
+        if (a.nodes) atomicAdd((unsigned long long *)&st->node_visits[which], a.nodes);
+        if (a.tris) atomicAdd((unsigned long long *)&st->tri_tests[which], a.tris);
     }
 }
 
