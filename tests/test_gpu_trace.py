@@ -130,6 +130,56 @@ def test_random_triangle_soup_bvh_matches_brute_force(ctx):
     assert l1_0.max() <= 5e-3
 
 
+def test_degenerate_geometry_matches_brute_force(ctx):
+    """BVH edge cases: duplicated triangles (equal Morton codes and union areas), zero-area
+    slivers, many triangles sharing one centroid, and a large wall split into thin strips --
+    traced against the oracle's brute-force intersection."""
+    rng = np.random.default_rng(33)
+    bv, bt = scenes.box_mesh([0, 0, 0], [8, 6, 4])
+    parts_v, parts_t, mats = [bv], [bt], [np.zeros(12, np.int32)]
+    nv = 8
+
+    def add(v, m):
+        nonlocal nv
+        v = np.asarray(v, np.float32).reshape(-1, 3)
+        parts_v.append(v)
+        parts_t.append(np.arange(len(v)).reshape(-1, 3) + nv)
+        mats.append(np.full(len(v) // 3, m, np.int32))
+        nv += len(v)
+
+    tri = np.array([[3, 2, 1], [4, 2, 1], [3.5, 3, 2.5]], np.float32)
+    for _ in range(20):  # the same triangle 20 times
+        add(tri, 1)
+    for k in range(30):  # zero-area slivers (collinear vertices)
+        a = rng.uniform(1, 7, 3) * [1, 0.8, 0.6]
+        add([a, a + [0.5, 0, 0], a + [1.0, 0, 0]], 2)
+    c = np.array([5.0, 4.0, 2.0])
+    for k in range(40):  # 40 triangles with the same centroid, different orientations
+        q = rng.normal(size=(3, 3)) * 0.4
+        q -= q.mean(axis=0)
+        add(c + q, 3)
+    for k in range(64):  # a thin-strip wall at x = 6
+        y0 = 0.5 + k * 0.07
+        add([[6, y0, 0.5], [6, y0 + 0.07, 0.5], [6, y0, 3.0]], 1)
+        add([[6, y0 + 0.07, 0.5], [6, y0 + 0.07, 3.0], [6, y0, 3.0]], 1)
+    verts = np.concatenate(parts_v).astype(np.float32)
+    tris = np.concatenate(parts_t).astype(np.int32)
+    mat = np.concatenate(mats).astype(np.int32)
+    a = rng.uniform(0.05, 0.3, size=(4, 3)).astype(np.float32)
+    s = rng.uniform(0.2, 0.8, size=(4, 3)).astype(np.float32)
+    sc = scenes.Scene("degenerate", verts, tris, mat, a, s, np.array([1.0, 1.0, 1.0], np.float32),
+                      np.array([[7.5, 5.5, 3.5], [0.5, 5.5, 3.5]], np.float32))
+    p = rpr.TraceParams(num_rays=4000, max_order=10, sh_order=1, num_bins=300, seed=91)
+    g = pu.run_gpu(ctx, sc, p)
+    assert g["stats"]["error"] == 0
+    osc = oracle.OracleScene.from_scene(sc, use_bvh=False)  # brute force
+    Ho, sto, hh = oracle.trace(osc, pu.oracle_params(p), sc.listener, sc.sources, hash_cap=p.num_rays)
+    assert abs(g["stats"]["segments"] - sto["segments"]) <= 2e-3 * sto["segments"]
+    assert pu.divergence(g["hash"], hh) <= 2e-3  # grazing hits on coincident and strip geometry
+    l1_0, _ = pu.band_l1(g["H"], Ho)
+    assert l1_0.max() <= 5e-3
+
+
 @pytest.mark.parametrize("sh_order,bands", [(0, 1), (3, 8), (2, 3)])
 def test_orders_and_band_counts(ctx, sh_order, bands):
     sc = scenes.shoebox(bands=bands, num_sources=3)
