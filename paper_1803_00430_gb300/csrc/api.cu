@@ -281,7 +281,6 @@ int rp_create(rp_ctx **out, int device, void *cuda_stream)
     }
     cudaMemset(c->d_status, 0, sizeof(int));
     c->paths_blocks = c->num_sms * paths_occupancy(0);
-    c->shadow_steps = 8;
     c->shadow_blocks = c->num_sms * shadow_occupancy(0);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

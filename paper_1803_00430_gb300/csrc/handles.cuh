@@ -35,13 +35,15 @@ struct rp_ctx {
     int num_sms = 0;
     int *d_status = nullptr;
     int paths_blocks = 0, shadow_blocks = 0;
-    int shadow_steps = 8;
+    int shadow_steps = 8;  // node visits a shadow-ray lane makes between refills (one-ray-per-lane mode)
     unsigned long long ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
     // workspace
+    //   stored reflections (hit_*), their cell-ordered copy (shit_*) and order (hord_*),
+    //   contribution records and their counting sort, running histogram sums, positions,
+    //   counters, statistics, the host-buffer update's outputs, job tables
     Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, shit_p, shit_n, shit_ws, shit_rid, hord_cell, hord_perm, hord_cnt,
-        rec_key, rec_rid, rec_e, perm, rerun,
-        cnt, off, cur, Hs, He, src, ctr,
-        stats, H, direct, params, state, jobs, js, chunks, src_job;
+        rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, Hs, He, src, ctr, stats, H, direct, params, state, jobs,
+        js, chunks, src_job;
     // profiling
     bool prof = false;
     std::vector<ProfPair> pending;

@@ -16,10 +16,18 @@
 //                 Path state in FP64 (default) or FP32 (RP_FLAG_FP32_PATHS).
 //                 After a specular choice the next segment also tests the sources
 //                 as spheres (the specular image of the source).
-//   k_shadow      persistent over (reflection, source) pairs: the diffuse-rain
-//                 shadow ray of each stored reflection to each source; a visible
-//                 source emits a contribution record w_b s_b cos / (pi d^2) at
-//                 arrival time (L + d) / c.
+//   k_hit_cells, k_hit_scatter, k_hit_gather
+//                 order the stored reflections by spatial cell and copy them in
+//                 that order, so that neighbouring shadow items start close
+//                 together.
+//   k_shadow_packet / k_shadow
+//                 persistent over (reflection, source) pairs in tiles of 32
+//                 reflections x sources: the diffuse-rain shadow ray of each stored
+//                 reflection to each source, as warp packets (32 rays walk the BVH
+//                 together) or one ray per lane; a visible source emits a
+//                 contribution record w_b s_b cos / (pi d^2) at arrival time
+//                 (L + d) / c.  Rounding-sensitive visibilities go to
+//                 k_shadow_exact (FP64).
 //   k_direct      visibility and closed-form direct sound per source.
 #include "traverse.cuh"
 
@@ -30,9 +38,7 @@ constexpr int PATH_THREADS = 128;
 constexpr int SHADOW_THREADS = 128;
 // an FP32 arrival time within this many bins of a bin boundary is re-decided in FP64
 constexpr float BIN_GUARD = 2e-3f;
-// node visits a shadow-ray lane makes before the warp refills finished lanes
-constexpr int SHADOW_STEPS = 8;
-constexpr int SHADOW_WINDOW = 256;  // items a warp takes from the chunk at a time
+constexpr int SHADOW_WINDOW = 256;  // items a warp of k_shadow takes from the chunk at a time
 
 struct BlockAcc {
     double esc[MAXB], absb[MAXB], rem[MAXB], late[MAXB];
