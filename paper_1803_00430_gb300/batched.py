@@ -57,6 +57,8 @@ def main(argv=None):
     ap.add_argument("--autotune-cache", default="", help="text file of autotuned launch shapes ('' = none)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scene plain form")
+    ap.add_argument("--shadow-mode", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="shadow rays: 1 packets, 2 one per lane, 0 by scene size; -1 autotunes")
     a = ap.parse_args(argv)
     t_setup = time.time()
     ctx = rpr.Context(0, torch.cuda.current_stream())
@@ -68,7 +70,11 @@ def main(argv=None):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     setup_s = time.time() - t_setup
     tune_ms = None
-    if not a.no_autotune:
+    if a.shadow_mode >= 0:
+        t = b.tuning()
+        t.shadow_mode = a.shadow_mode
+        b.set_tuning(t)
+    elif not a.no_autotune:
         t, tune_ms = b.autotune(seed=scenes.PHILOX_KEY_BASE, cache_path=a.autotune_cache or None)
     tuning = b.tuning()
     for w in range(a.warmup):
@@ -89,7 +95,7 @@ def main(argv=None):
         "segments_per_step": st["segments"], "shadow_rays_per_step": st["shadow_rays"],
         "tuning": {"chunk_rays": tuning.chunk_rays, "shadow_steps": tuning.shadow_steps,
                    "paths_blocks_per_sm": tuning.paths_blocks_per_sm,
-                   "shadow_blocks_per_sm": tuning.shadow_blocks_per_sm},
+                   "shadow_blocks_per_sm": tuning.shadow_blocks_per_sm, "shadow_mode": tuning.shadow_mode},
         "autotune_best_ms": tune_ms, "setup_s": round(setup_s, 1),
         "l2": "flushed between timed steps (256 MiB write)",
     }

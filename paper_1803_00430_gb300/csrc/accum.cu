@@ -6,8 +6,10 @@
 // counting sort (count, exclusive scan, scatter of record indices).  Then one warp
 // owns one (source, bin): its 32 lanes own the B*K cells, 32 records at a time are
 // staged in shared memory (energies, and SH of the primary direction recomputed
-// from Philox), and every cell is summed with Kahan compensation in FP32.  Each
-// cell is written by exactly one warp, so no atomics touch H.  Chunks of records
+// from Philox), and every cell is summed in FP32: each group of 32 staged records
+// with plain fused multiply-adds (relative error at most 32 * 2^-24), the groups with
+// Kahan compensation.  Each cell is written by exactly one warp, so no atomics touch
+// H.  Chunks of records
 // (when the record buffer is smaller than one step's records) are merged into a
 // running (sum, error) pair with an error-free two-sum.
 #include "internal.cuh"
@@ -154,16 +156,20 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, u
                     if (kk < K) sy[wp][lane][kk] = Y[kk];
             }
             __syncwarp();
-            for (int j = 0; j < n; ++j) {
+            // the staged records in plain FP32, then one compensated add per group of 32
+            float part[ACC_SLOTS];
 #pragma unroll
-                for (int i = 0; i < ACC_SLOTS; ++i) {
-                    const int c = lane + 32 * i;
-                    if (c < BK) {
-                        const int b = c / K, kk = c - b * K;
-                        kahan_add(sum[i], err[i], se[wp][j][b] * sy[wp][j][kk]);
-                    }
+            for (int i = 0; i < ACC_SLOTS; ++i) part[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < ACC_SLOTS; ++i) {
+                const int c = lane + 32 * i;
+                if (c < BK) {
+                    const int b = c / K, kk = c - b * K;
+                    for (int j = 0; j < n; ++j) part[i] = fmaf(se[wp][j][b], sy[wp][j][kk], part[i]);
                 }
             }
+#pragma unroll
+            for (int i = 0; i < ACC_SLOTS; ++i) kahan_add(sum[i], err[i], part[i]);
             __syncwarp();
         }
         const int s = (int)(key / T), bin = (int)(key - (long long)s * T);

@@ -154,7 +154,7 @@ int reserve_batch(rp_batch *b)
     if ((r = grow(c, c->shit_n, z.hit_cap * sizeof(float4)))) return r;
     if ((r = grow(c, c->shit_ws, z.hit_cap * B * sizeof(float)))) return r;
     if ((r = grow(c, c->shit_rid, z.hit_cap * sizeof(uint32_t)))) return r;
-    const long long cells = std::max(1ll << 18, 8ll * b->max_jobs) + 1;  // >= hit_order_cells of any group
+    const long long cells = std::max(1ll << 22, 8ll * b->max_jobs) + 1;  // >= hit_order_cells of any group
     if ((r = grow(c, c->hord_cnt, (size_t)cells * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->rec_key, z.rec_cap * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->rec_rid, z.rec_cap * sizeof(uint32_t)))) return r;

@@ -1,6 +1,6 @@
 // estimate.cu -- reverberation-parameter estimation from the SH energy IR
-// (Section 4.2), in FP64.  One block per source, one warp per band; lane l owns a
-// contiguous run of bins.
+// (Section 4.2), in FP64.  One block per (source, band); thread l owns a contiguous
+// run of bins.
 //
 //   I_b(t)      = sqrt(4 pi) X_{b,00}(t)                    (Y_00 = 1/sqrt(4 pi))
 //   E_b(t)      = sum_{t' >= t} I_b(t')                     backward integration
@@ -14,6 +14,12 @@
 //   predelay    = first bin non-zero in any band, / rate
 //   X-bar_lm    = sum_t X_{b,lm}(t) / I_total              (Section 4.1)
 //   smoothing   = alpha * RT60 + (1 - alpha) * previous, alpha = 1 - exp(-dt / tau)
+//
+// The window ends come from counting the bins whose level is above each threshold
+// (the decay curve never increases).  A level is compared through the energy ratio
+// E(t) / E(0) against 10^(threshold / 10); only a ratio within a relative 1e-9 of a
+// threshold, where rounding of the logarithm could matter, takes the logarithm, so
+// every decision equals the one on L_b(t) and most bins need no FP64 logarithm.
 #include <cmath>
 
 #include "internal.cuh"
@@ -39,17 +45,54 @@ __device__ __forceinline__ int wmin_i(int v)
     return v;
 }
 
-__global__ void k_estimate(EstimateWork w)
+constexpr int EST_THREADS = 128;
+
+// block-wide sums (all threads get the result); `sh` holds EST_THREADS / 32 doubles
+__device__ __forceinline__ double bsum(double v, double *sh)
 {
-    __shared__ int first_nz[MAXB];
-    const int s = blockIdx.x;
-    const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = wsum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < EST_THREADS / 32; ++i) t += sh[i];
+    return t;
+}
+
+__device__ __forceinline__ int bsum_i(int v, int *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = wsum_i(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int t = 0;
+    for (int i = 0; i < EST_THREADS / 32; ++i) t += sh[i];
+    return t;
+}
+
+// whether 10 log10(ratio) > c (strict) or >= c, with thr = 10^(c / 10)
+__device__ __forceinline__ bool level_above(double ratio, double c, double thr, bool strict)
+{
+    if (ratio > thr * (1.0 + 1e-9)) return true;
+    if (ratio < thr * (1.0 - 1e-9)) return false;
+    const double L = ratio > 0.0 ? 10.0 * log10(ratio) : -INFINITY;
+    return strict ? L > c : L >= c;
+}
+
+__global__ void __launch_bounds__(EST_THREADS) k_estimate(EstimateWork w)
+{
+    __shared__ double shd[EST_THREADS / 32];
+    __shared__ int shi[EST_THREADS / 32];
+    __shared__ double scan[EST_THREADS];
+    const int s = blockIdx.x / w.B, b = blockIdx.x % w.B;
+    const int t = threadIdx.x;
     const int B = w.B, K = w.K, T = w.T;
     const double sq4pi = sqrt(4.0 * 3.14159265358979323846);
     const float *h0 = w.H + (((size_t)s * B + b) * K + 0) * T;
-    const int per = (T + 31) / 32;
-    const int j0 = min(T, lane * per), j1 = min(T, j0 + per);
-
+    const int per = (T + EST_THREADS - 1) / EST_THREADS;
+    const int j0 = min(T, t * per), j1 = min(T, j0 + per);
     // chunk total and first non-zero bin
     double tot = 0.0;
     int fnz = T;
@@ -58,46 +101,59 @@ __global__ void k_estimate(EstimateWork w)
         tot += I;
         if (I > 0.0 && fnz == T) fnz = j;
     }
-    fnz = wmin_i(fnz);
-    if (lane == 0) first_nz[b] = fnz;
-    // tail[l] = sum of the chunk totals of lanes > l (suffix scan)
-    double incl = tot;
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_down_sync(FULL, incl, o);
-        if (lane + o < 32) incl += y;
+    // tail = sum of the chunk totals of threads > t (inclusive suffix scan)
+    scan[t] = tot;
+    __syncthreads();
+    for (int o = 1; o < EST_THREADS; o <<= 1) {
+        const double y = t + o < EST_THREADS ? scan[t + o] : 0.0;
+        __syncthreads();
+        scan[t] += y;
+        __syncthreads();
     }
-    const double tail = incl - tot;
-    const double E0 = __shfl_sync(FULL, incl, 0);
-    const double itot = wsum(tot);
-
+    const double tail = scan[t] - tot;
+    const double E0 = scan[0];
+    const double itot = E0;
+    int first = fnz;
+    {
+        first = wmin_i(first);
+        __syncthreads();
+        if ((t & 31) == 0) shi[t >> 5] = first;
+        __syncthreads();
+        for (int i = 0; i < EST_THREADS / 32; ++i) first = min(first, shi[i]);
+        __syncthreads();
+    }
     // level of the last bin decides whether a floor is reached
     double Llast = -INFINITY;
     {
         const double Il = sq4pi * (double)h0[T - 1];
         if (E0 > 0.0 && Il > 0.0) Llast = 10.0 * log10(Il / E0);
     }
-
     static const double HI[3] = {-5.0, -5.0, 0.0};
     static const double LO[3] = {-35.0, -25.0, -10.0};
     int above_hi[3] = {0, 0, 0}, above_lo[3] = {0, 0, 0};
     if (E0 > 0.0) {
+        double thi[3], tlo[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            thi[r] = pow(10.0, HI[r] / 10.0);
+            tlo[r] = pow(10.0, LO[r] / 10.0);
+        }
         double suf = tail;
         for (int j = j1 - 1; j >= j0; --j) {
             suf += sq4pi * (double)h0[j];
-            const double Lj = suf > 0.0 ? 10.0 * log10(suf / E0) : -INFINITY;
+            const double ratio = suf / E0;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                above_hi[r] += Lj > HI[r];
-                above_lo[r] += Lj >= LO[r];
+                above_hi[r] += level_above(ratio, HI[r], thi[r], true);
+                above_lo[r] += level_above(ratio, LO[r], tlo[r], false);
             }
         }
     }
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        above_hi[r] = wsum_i(above_hi[r]);
-        above_lo[r] = wsum_i(above_lo[r]);
+        above_hi[r] = bsum_i(above_hi[r], shi);
+        above_lo[r] = bsum_i(above_lo[r], shi);
     }
-
     double rt = NAN, slope = NAN, icpt = NAN, r2 = NAN, fhi = 0.0, flo = 0.0;
     int kind = 0, nfit = 0, fa = -1, fz = -1;
     if (E0 > 0.0) {
@@ -116,7 +172,7 @@ __global__ void k_estimate(EstimateWork w)
                     if (j >= a && j <= z) sy += 10.0 * log10(suf / E0);
                 }
             }
-            sy = wsum(sy);
+            sy = bsum(sy, shd);
             const double my = sy / n;
             const double mx = 0.5 * (double)(a + z) / w.rate;
             double sxx = 0.0, sxy = 0.0, syy = 0.0;
@@ -133,9 +189,9 @@ __global__ void k_estimate(EstimateWork w)
                     }
                 }
             }
-            sxx = wsum(sxx);
-            sxy = wsum(sxy);
-            syy = wsum(syy);
+            sxx = bsum(sxx, shd);
+            sxy = bsum(sxy, shd);
+            syy = bsum(syy, shd);
             const double sl = sxy / sxx;
             if (!(sl < 0.0)) continue;
             slope = sl;
@@ -150,7 +206,6 @@ __global__ void k_estimate(EstimateWork w)
             flo = LO[r];
         }
     }
-
     // weighted average directivity: sum_t X_k(t) / I_total
     double xs[MAXK];
 #pragma unroll
@@ -159,13 +214,9 @@ __global__ void k_estimate(EstimateWork w)
         const float *hk = w.H + (((size_t)s * B + b) * K + kk) * T;
         double a = 0.0;
         for (int j = j0; j < j1; ++j) a += (double)hk[j];
-        xs[kk] = wsum(a);
+        xs[kk] = bsum(a, shd);
     }
-    __syncthreads();
-    int first = T;
-    for (int bb = 0; bb < B; ++bb) first = min(first, first_nz[bb]);
-
-    if (lane == 0) {
+    if (t == 0) {
         rp_reverb_params o;
         o.rt60_raw = rt;
         o.fit_hi_db = fhi;
@@ -181,7 +232,8 @@ __global__ void k_estimate(EstimateWork w)
         else if (ed > 0.0) o.drr_db = INFINITY;
         else if (itot > 0.0) o.drr_db = -INFINITY;
         else o.drr_db = NAN;
-        o.predelay_s = first < T ? (double)first / w.rate : NAN;
+        // this band's first non-zero bin; k_predelay turns it into the source's predelay
+        o.predelay_s = (double)first;
         o.range_kind = kind;
         o.n_fit = nfit;
         o.fit_j0 = fa;
@@ -201,12 +253,27 @@ __global__ void k_estimate(EstimateWork w)
     }
 }
 
+// predelay of every source: its earliest non-zero bin over the bands (Section 4.2,
+// "for all frequency bands"), from the per-band first bins k_estimate left in
+// predelay_s
+__global__ void k_predelay(EstimateWork w)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= w.S) return;
+    rp_reverb_params *o = w.out + (size_t)s * w.B;
+    double first = (double)w.T;
+    for (int b = 0; b < w.B; ++b) first = fmin(first, o[b].predelay_s);
+    const double p = first < (double)w.T ? first / w.rate : NAN;
+    for (int b = 0; b < w.B; ++b) o[b].predelay_s = p;
+}
+
 }  // namespace
 
 void launch_estimate(const EstimateWork &w, cudaStream_t st)
 {
     if (w.S <= 0) return;
-    k_estimate<<<w.S, 32 * w.B, 0, st>>>(w);
+    k_estimate<<<w.S * w.B, EST_THREADS, 0, st>>>(w);
+    k_predelay<<<(w.S + 127) / 128, 128, 0, st>>>(w);
 }
 
 }  // namespace rp

@@ -155,11 +155,12 @@ struct HitOrder {
     int ncells;      // njobs x 2^(3 bits)
 };
 
-// grid bits per axis for njobs jobs: about 2^18 cells in all, 1..6 bits
+// grid bits per axis for njobs jobs: at most 2^22 cells in all, 1..6 bits (a 64^3
+// grid per scene up to 16 scenes, 16^3 for 512)
 inline int hit_order_bits(int njobs)
 {
     int bits = 6;
-    while (bits > 1 && (long long)njobs << (3 * bits) > (1ll << 18)) --bits;
+    while (bits > 1 && (long long)njobs << (3 * bits) > (1ll << 22)) --bits;
     return bits;
 }
 inline long long hit_order_cells(int njobs) { return (long long)std::max(njobs, 1) << (3 * hit_order_bits(njobs)); }

@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
 // answer is the single-ray answer of any_hit_steps.  Items of different jobs in one
 // packet walk their own BVHs one after the other.
 template <bool COUNT, bool EXACT, bool BATCH>
-__global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_packet(TraceWork w, unsigned long long chunk)
+__global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w, unsigned long long chunk)
 {
     __shared__ int pnode[SHADOW_THREADS / 32][STACK_DEPTH];
     __shared__ unsigned pmask[SHADOW_THREADS / 32][STACK_DEPTH];
@@ -902,7 +902,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_packet(TraceWork w, u
             const int jl = __shfl_sync(FULL, job, leader);
             const unsigned grp = __ballot_sync(FULL, traced && job == jl) & todo;
             todo &= ~grp;
-            const SceneView &sc = BATCH ? w.jobs[jl].sc : w.job0.sc;
+            const SceneView sc = BATCH ? w.jobs[jl].sc : w.job0.sc;  // in registers for the walk
             auto leaf = [&](int tri) {  // the lane's any-hit test of one triangle
                 if (COUNT) ts.tris++;
                 if ((unsigned)tri >= (unsigned)sc.num_tris) {
