@@ -50,7 +50,7 @@ FLOPS_PER_TRI = 27.0    # Moller-Trumbore
 # scene uses) in an ncu capture of the same update at 30,000 primaries, and the
 # shadow rays that launch traced; a full-size launch is credited with the same bytes
 # per shadow ray.
-NCU_SHADOW_DRAM = (97_133_568 + 19_801_088, 18_878_384)
+NCU_SHADOW_DRAM = (96_999_424 + 18_942_720, 18_878_384)
 
 
 def _peaks():
