@@ -323,7 +323,10 @@ def main():
     # roofline of the dominant kernel: BVH traversal is bound by FP32 issue, not HBM
     name = max(kt, key=lambda k: kt[k][1])
     n_l, tot = kt[name]
-    avg_s = tot / n_l / 1000.0
+    # the kernel's time per update: an update may launch it once per record chunk
+    # (chunks past the update's work return at once), so the work of one update is
+    # set against all of its launches in that update
+    avg_s = tot / args.steps / 1000.0
     idx = 1 if name == "shadow" else 0
     flops = stc["node_visits"][idx] * FLOPS_PER_NODE + stc["tri_tests"][idx] * FLOPS_PER_TRI
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -351,8 +354,9 @@ def main():
                 "tri_tests_per_shadow_ray": stc["tri_tests"][1] / max(1, stc["shadow_rays"])},
         "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                     "traffic_note": "DRAM bytes per launch, from an ncu capture at 30k primaries scaled by "
-                                     "shadow rays" if traffic else None,
+                     "traffic_note": "DRAM bytes per update (one launch here), from an ncu capture at 30k "
+                                     "primaries scaled by shadow rays" if traffic else None,
+                     "launches_per_update": n_l / args.steps,
                      "peak_note": f"FP32 FMA peak 152 SMs x 128 lanes x 2 at the median sampled SM clock "
                                   f"{sm_mhz:.0f} MHz (derived, not measured)",
                      "algorithmic": f"{FLOPS_PER_NODE:.0f} flop/node visit + {FLOPS_PER_TRI:.0f} flop/triangle test, "

@@ -229,7 +229,8 @@ int rp_destroy(rp_ctx *ctx);
 int rp_set_stream(rp_ctx *ctx, void *cuda_stream);
 
 /* Copy the mesh to the device and build its BVH (Morton codes, radix sort,
- * hierarchy, bottom-up bounds, all on the device).  Non-finite vertices or
+ * clustering of mutual nearest neighbours in Morton order, all on the device).
+ * Non-finite vertices or
  * materials give RP_ERR_NAN_INPUT, zero triangles RP_ERR_EMPTY_SCENE, an index out
  * of range RP_ERR_INVALID_ARG.  Synchronises the stream before returning. */
 int rp_scene_create(rp_ctx *ctx, const rp_mesh_desc *mesh, rp_scene **out);

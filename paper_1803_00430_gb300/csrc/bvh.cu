@@ -2,7 +2,7 @@
 //
 // The paper's ray tracer leaves its acceleration structure unspecified (Section 6
 // "Performance" only states that cost grows logarithmically with scene size).  This
-// file builds a linear BVH entirely on the GPU:
+// file builds the BVH entirely on the GPU:
 //   1. per-triangle bounds and centroids, checked for non-finite values;
 //   2. 30-bit Morton codes of the centroids;
 //   3. a stable LSD radix sort (8-bit digits) of (code, triangle) pairs;
