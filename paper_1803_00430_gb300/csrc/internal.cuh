@@ -65,9 +65,7 @@ struct JobState {
     unsigned long long wave_count;  // primaries of the current wave
     unsigned long long item_off;    // first shadow item of the job
     unsigned long long hit_prefix;  // stored reflections of the earlier jobs
-    unsigned long long segments;    // closest-hit rays traced
-    unsigned long long mfp_count;
-    double mfp_sum;
+    unsigned long long segments;    // closest-hit rays traced (single-job steps, for the refill)
 };
 
 // A run of consecutive primaries of one job; the batched paths kernel hands out
@@ -84,7 +82,7 @@ struct TraceCounters {
     unsigned long long n_records;    // contribution records in the current chunk
     unsigned long long next_item;    // shadow items fetched in the current chunk
     unsigned long long n_rerun;      // shadow items queued for an FP64 decision (current chunk)
-    unsigned long long total_items; // shadow items of the step (sum over jobs of hits x sources)
+    unsigned long long total_items; // shadow items of the step (sum over jobs of shadow_items(hits, S))
     unsigned long long total_hits;  // stored reflections of the step (sum over jobs)
     unsigned long long pad[2];
 };
@@ -154,6 +152,13 @@ struct HitOrder {
     int bits;        // grid bits per axis
     int ncells;      // njobs x 2^(3 bits)
 };
+
+// shadow items of a job with h stored reflections and S sources: tiles of 32
+// reflections x S sources, a short last tile padded to 32 per source
+__host__ __device__ inline unsigned long long shadow_items(unsigned long long h, int S)
+{
+    return ((h + 31ull) / 32ull) * 32ull * (unsigned long long)S;
+}
 
 // grid bits per axis for njobs jobs: at most 2^22 cells in all, 1..6 bits (a 64^3
 // grid per scene up to 16 scenes, 16^3 for 512)

@@ -137,13 +137,14 @@ StepSizes step_sizes(const unsigned long long *rays, const int *sources, int njo
     for (int j = 0; j < njobs; ++j) {
         const unsigned long long h = rays[j] * (unsigned long long)std::max(M, 0);
         z.hit_cap += h;
-        z.items += h * (unsigned long long)sources[j];
+        z.items += shadow_items(h, sources[j]);
         z.S += sources[j];
     }
     z.hit_cap = std::max(1ull, z.hit_cap);
     z.sph_cap = z.hit_cap / 2 + 4096;
     const unsigned long long room = rec_budget > z.sph_cap + 1 ? rec_budget - z.sph_cap : 1ull << 20;
-    z.items_per_chunk = std::max(1ull, std::min(std::max(z.items, 1ull), room));
+    // a multiple of 32, so that a warp's 32 consecutive items stay one run of a tile
+    z.items_per_chunk = std::max(32ull, std::min(std::max(z.items, 1ull), room) / 32ull * 32ull);
     z.n_chunks = (std::max(z.items, 1ull) + z.items_per_chunk - 1) / z.items_per_chunk;
     z.rec_cap = z.sph_cap + z.items_per_chunk;
     z.rerun_cap = z.rec_cap / 8 + 4096;

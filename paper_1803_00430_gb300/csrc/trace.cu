@@ -188,7 +188,7 @@ __global__ void k_item_prefix(TraceWork w)
         w.js[j].item_off = acc;
         w.js[j].hit_prefix = hits;
         const unsigned long long h = min(w.js[j].n_hits, w.jobs[j].hit_cap);
-        acc += h * (unsigned long long)w.jobs[j].S;
+        acc += shadow_items(h, w.jobs[j].S);
         hits += h;
     }
     w.ctr->total_items = acc;
@@ -299,47 +299,11 @@ __device__ __forceinline__ unsigned long long warp_append_job(unsigned long long
     return base + (unsigned long long)__popc(peers & ((1u << lane) - 1u));
 }
 
-// per-job path statistics kept per lane and flushed when the lane changes job
-struct JobAcc {
-    int job;
-    unsigned long long segs, mc;
-    double mfp;
-};
-
-__device__ __forceinline__ void job_flush(const TraceWork &w, JobAcc &a)
+// closest-hit segments of a single-job step, for the next wave's refill
+__device__ __forceinline__ void wave_segments_flush(const TraceWork &w, unsigned long long segs)
 {
-    if (a.job >= 0 && (a.segs || a.mc)) {
-        JobState &s = w.js[a.job];
-        atomicAdd(&s.segments, a.segs);
-        atomicAdd(&s.mfp_count, a.mc);
-        atomicAdd(&s.mfp_sum, a.mfp);
-    }
-    a.segs = a.mc = 0;
-    a.mfp = 0.0;
-}
-
-// final flush: whole warps that share a job reduce first
-__device__ __forceinline__ void job_flush_final(const TraceWork &w, JobAcc &a)
-{
-    const int lane = threadIdx.x & 31;
-    const int j0 = __shfl_sync(FULL, a.job, 0);
-    if (__all_sync(FULL, a.job == j0)) {
-        unsigned long long segs = a.segs, mc = a.mc;
-        double mfp = a.mfp;
-        for (int o = 16; o > 0; o >>= 1) {
-            segs += __shfl_xor_sync(FULL, segs, o);
-            mc += __shfl_xor_sync(FULL, mc, o);
-            mfp += __shfl_xor_sync(FULL, mfp, o);
-        }
-        if (lane == 0) {
-            a.segs = segs;
-            a.mc = mc;
-            a.mfp = mfp;
-            job_flush(w, a);
-        }
-    } else {
-        job_flush(w, a);
-    }
+    for (int o = 16; o > 0; o >>= 1) segs += __shfl_xor_sync(FULL, segs, o);
+    if ((threadIdx.x & 31) == 0 && segs) atomicAdd(&w.js[0].segments, segs);
 }
 
 // Path state in precision R.  The default carries the origin, direction and path
@@ -423,7 +387,6 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
     unsigned long long mcnp = 0, sphere = 0, contrib = 0, reruns = 0, segs_all = 0, mc_all = 0;
     double mfp_all = 0.0;
     TravStats ts = {0u, 0u};
-    JobAcc ja = {BATCH ? -1 : 0, 0ull, 0ull, 0.0};
 
     // path state
     bool have = false, done = vtotal == 0;
@@ -461,10 +424,6 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     got = true;
                 }
                 if (got) {
-                    if (BATCH && job != ja.job) {
-                        job_flush(w, ja);
-                        ja.job = job;
-                    }
                     const SceneJob &J = BATCH ? w.jobs[job] : w.job0;
                     have = true;
                     o = from4<R>(__ldg(w.pos + J.lis));
@@ -486,7 +445,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
         if (!have) continue;
 
         const SceneJob &J = BATCH ? w.jobs[job] : w.job0;
-        const SceneView sc = J.sc;
+        const SceneView &sc = J.sc;
         // ---- one segment: closest hit (FP32 traversal) ----
         const float3 of = to_f3(o), df = to_f3(d);
         const float Lf = (float)L;
@@ -512,7 +471,6 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
             tri = traverse<false, COUNT, false>(sc, of, df, sc.tmin, INFINITY, prev, sstack + threadIdx.x, tf, ts,
                                                 w.status);
         }
-        ++ja.segs;
         ++segs_all;
         if (spec_prev && h - 1 >= k.min_order) {
             // the job's sources as spheres of radius r_s, seen through the specular bounce
@@ -575,8 +533,6 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
             }
             L += t;
             const V3<R> p = o + d * t;
-            ja.mfp += (double)t;
-            ++ja.mc;
             mfp_all += (double)t;
             ++mc_all;
             if (h > 1) {
@@ -663,7 +619,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
             have = false;
         }
     }
-    job_flush_final(w, ja);
+    if (!BATCH) wave_segments_flush(w, segs_all);
     acc_counters(acc, mfp_all, mfp_np, mc_all, mcnp, segs_all, 0ull, contrib, sphere, ts);
     for (int o = 16; o > 0; o >>= 1) reruns += __shfl_xor_sync(FULL, reruns, o);
     if (lane == 0 && reruns) atomicAdd((unsigned long long *)&w.stats->fp64_reruns, reruns);
@@ -706,24 +662,42 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
     }
 }
 
-// (job, reflection in the cell-ordered copy, global source) of shadow item q.  A job's items come in
-// tiles of 32 reflections (consecutive in cell order) x its S sources, source-major
-// inside a tile: 32 consecutive items are rays from nearby points to one source.
-__device__ __forceinline__ void item_target(const TraceWork &w, bool batch, unsigned long long q, int &job,
-                                            unsigned long long &j, int &gs)
+// (reflection in the cell-ordered copy, global source) of shadow item q of job `job`;
+// false for a hole.  A job's items come in tiles of 32 reflections (consecutive in
+// cell order) x its S sources, source-major inside a tile: each run of 32 items is
+// rays from nearby points to one source.  The last tile of a job may hold fewer than
+// 32 reflections; its runs keep 32 slots and the slots past its reflections are
+// holes, so that every job's items and every run start at a multiple of 32 and a
+// warp's 32 consecutive items are one run.
+__device__ __forceinline__ bool item_slot(const TraceWork &w, bool batch, int job, unsigned long long q,
+                                          unsigned long long &j, int &gs)
 {
-    job = batch ? job_of_item(w, q) : 0;
     const SceneJob &J = batch ? w.jobs[job] : w.job0;
     const JobState &js = w.js[job];
     const unsigned long long local = q - (batch ? js.item_off : 0ull);
     const unsigned long long n = min(js.n_hits, J.hit_cap);
-    const unsigned long long per_tile = 32ull * (unsigned long long)J.S;
-    const unsigned long long tile = local / per_tile;
-    const unsigned r = (unsigned)(local - tile * per_tile);
-    const unsigned tsz = (unsigned)min(32ull, n - tile * 32ull);
-    const unsigned s = r / tsz;
-    j = js.hit_prefix + tile * 32ull + (r - s * tsz);  // index into the cell-ordered copy
-    gs = J.src_off + (int)s;
+    const unsigned long long run = local >> 5;  // tile * S + source
+    const unsigned long long tile = run / (unsigned long long)J.S;
+    const unsigned r = (unsigned)(local & 31u);
+    j = js.hit_prefix + tile * 32ull + r;
+    gs = J.src_off + (int)(run - tile * (unsigned long long)J.S);
+    return tile * 32ull + r < n;
+}
+
+// (job, reflection, global source) of shadow item q; false for a hole
+__device__ __forceinline__ bool item_target(const TraceWork &w, bool batch, unsigned long long q, int &job,
+                                            unsigned long long &j, int &gs)
+{
+    job = batch ? job_of_item(w, q) : 0;
+    return item_slot(w, batch, job, q, j, gs);
+}
+
+// job of item q, given a job `from` whose first item is <= q (items of later jobs
+// follow in job order)
+__device__ __forceinline__ int job_from(const TraceWork &w, int from, unsigned long long q)
+{
+    while (from + 1 < w.njobs && w.js[from + 1].item_off <= q) ++from;
+    return from;
 }
 
 // Shadow rays of one chunk of the step's items q = (reflection, source) pairs,
@@ -781,15 +755,16 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
                     item = q0 + my;
                     unsigned long long j;
                     int gs;
-                    item_target(w, BATCH, item, job, j, gs);
+                    const bool real = item_target(w, BATCH, item, job, j, gs);
                     const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
-                    const float4 P = w.shits.p[j], N = w.shits.n[j];
+                    const float4 P = real ? w.shits.p[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 N = real ? w.shits.n[j] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const float3 p = xyz(P);
                     const float3 v = xyz(__ldg(w.pos + gs)) - p;
                     const float dist2 = dot(v, v);
                     dist = sqrtf(dist2);
                     const float cth = dot(xyz(N), v) / dist;
-                    if (cth > 0.f) {
+                    if (real && cth > 0.f) {
                         ++shadow;
                         dir = v * (1.0f / dist);
                         ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
@@ -826,8 +801,8 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
         }
         if (!st.blocked) {
             unsigned long long j;
-            int gs, jb;
-            item_target(w, BATCH, item, jb, j, gs);
+            int gs;
+            item_slot(w, BATCH, job, item, j, gs);
             ++contrib;
             shadow_contribution(w, acc, j, gs, f, dist);
         }
@@ -869,7 +844,8 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
         if (b0 >= items) break;
         const unsigned long long item = q0 + b0 + lane;
         bool traced = false;  // this lane traces a shadow ray
-        int job = 0;
+        // the job of the batch's first item (warp-uniform), then each lane's own
+        int job = BATCH ? job_of_item(w, q0 + b0) : 0;
         AnyRay ray;
         float3 dir = mk3(0.f, 0.f, 0.f);
         float f = 0.f, dist = 0.f;
@@ -877,15 +853,17 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
         if (b0 + lane < items) {
             unsigned long long j;
             int gs;
-            item_target(w, BATCH, item, job, j, gs);
+            if (BATCH) job = job_from(w, job, item);
+            const bool real = item_slot(w, BATCH, job, item, j, gs);
             const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
-            const float4 P = w.shits.p[j], N = w.shits.n[j];
+            const float4 P = real ? w.shits.p[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 N = real ? w.shits.n[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float3 p = xyz(P);
             const float3 v = xyz(__ldg(w.pos + gs)) - p;
             const float dist2 = dot(v, v);
             dist = sqrtf(dist2);
             const float cth = dot(xyz(N), v) / dist;
-            if (cth > 0.f) {
+            if (real && cth > 0.f) {
                 ++shadow;
                 dir = v * (1.0f / dist);
                 ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
@@ -955,13 +933,13 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 const float a0 = n0.x * ray.idir.x - ray.ood.x, b0 = n0.y * ray.idir.x - ray.ood.x;
                 const float a1 = n0.z * ray.idir.y - ray.ood.y, b1 = n0.w * ray.idir.y - ray.ood.y;
                 const float a2 = n2.x * ray.idir.z - ray.ood.z, b2 = n2.y * ray.idir.z - ray.ood.z;
-                const float c0min = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fmaxf(fminf(a2, b2), ray.tmin));
-                const float c0max = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fminf(fmaxf(a2, b2), ray.tmax));
+                const float c0min = slab_in(a0, b0, a1, b1, a2, b2, ray.tmin);
+                const float c0max = slab_out(a0, b0, a1, b1, a2, b2, ray.tmax);
                 const float a3 = n1.x * ray.idir.x - ray.ood.x, b3 = n1.y * ray.idir.x - ray.ood.x;
                 const float a4 = n1.z * ray.idir.y - ray.ood.y, b4 = n1.w * ray.idir.y - ray.ood.y;
                 const float a5 = n2.z * ray.idir.z - ray.ood.z, b5 = n2.w * ray.idir.z - ray.ood.z;
-                const float c1min = fmaxf(fmaxf(fminf(a3, b3), fminf(a4, b4)), fmaxf(fminf(a5, b5), ray.tmin));
-                const float c1max = fminf(fminf(fmaxf(a3, b3), fmaxf(a4, b4)), fminf(fmaxf(a5, b5), ray.tmax));
+                const float c1min = slab_in(a3, b3, a4, b4, a5, b5, ray.tmin);
+                const float c1max = slab_out(a3, b3, a4, b4, a5, b5, ray.tmax);
                 const bool h0 = need && c0min <= c0max, h1 = need && c1min <= c1max;
                 const int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
                 if (h0 && ch0 < 0) leaf(~ch0);
@@ -1008,8 +986,8 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
         }
         if (!st.blocked) {
             unsigned long long j;
-            int gs, jb;
-            item_target(w, BATCH, item, jb, j, gs);
+            int gs;
+            item_slot(w, BATCH, job, item, j, gs);
             ++contrib;
             shadow_contribution(w, acc, j, gs, f, dist);
         }
