@@ -203,6 +203,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp32-paths", action="store_true", help="time the all-FP32 path precision form")
+    ap.add_argument("--shadow-mode", default="auto", choices=["auto", "packets", "lanes"],
+                    help="shadow rays as warp packets or one per lane (auto: by scene size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--rays", type=int, default=0, help="primaries per update (default: the workload's 200k; "
@@ -241,6 +243,7 @@ def main():
     info = scene.info()
     S, B = sc.num_sources, sc.num_bands
     flags = rpr.RP_FLAG_DEVICE_POSITIONS | (rpr.RP_FLAG_FP32_PATHS if args.fp32_paths else 0)
+    flags |= {"auto": 0, "packets": rpr.RP_FLAG_SHADOW_PACKETS, "lanes": rpr.RP_FLAG_SHADOW_LANES}[args.shadow_mode]
     base = rpr.TraceParams(**WORKLOAD, flags=flags, scene_id=rank)
     K, T = base.K, base.num_bins
     out = rpr.DeviceTrace(S, B, K, T)
@@ -356,6 +359,7 @@ def main():
         "config": {"workload": WORKLOAD_NAME, "triangles": sc.num_tris, "sources": S, "bands": B,
                    "rays": WORKLOAD["num_rays"], "max_order": WORKLOAD["max_order"], "bins": T, "sh_coeffs": K,
                    "path_precision": "fp32" if args.fp32_paths else "fp64 path state, fp32 traversal",
+                   "shadow_rays": args.shadow_mode,
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
         "updates_per_s": ws * 1000.0 / ms_step,
         "closest_hit_segments_per_step": st["segments"], "shadow_rays_per_step": st["shadow_rays"],

@@ -83,11 +83,9 @@ enum {
     RP_FLAG_SHADOW_PACKETS = 16, /* trace shadow rays as warp packets (32 rays from nearby
                                     reflections to one source walk the BVH together) */
     RP_FLAG_SHADOW_LANES = 32    /* trace shadow rays one per lane, each lane taking a new
-                                    ray as soon as its own ends.  Neither flag: packets when
-                                    the scene has fewer than 2^19 triangles, lanes otherwise
-                                    (long, mostly blocked rays in large scenes leave packet
-                                    lanes idle).  Both flags: RP_ERR_INVALID_ARG.  The two
-                                    modes give the same answers. */
+                                    ray as soon as its own ends.  Neither flag: packets.
+                                    Both flags: RP_ERR_INVALID_ARG.  The two modes give the
+                                    same answers. */
 };
 
 typedef struct rp_ctx rp_ctx;
@@ -295,8 +293,8 @@ typedef struct {
     int32_t shadow_steps;          /* BVH nodes a shadow-ray lane visits between refills, 1..64 */
     int32_t paths_blocks_per_sm;   /* persistent grid of the paths kernel, 1..occupancy */
     int32_t shadow_blocks_per_sm;  /* persistent grid of the shadow-ray kernel, 1..occupancy */
-    int32_t shadow_mode;           /* 0: by scene size (see RP_FLAG_SHADOW_LANES), 1: packets,
-                                      2: one ray per lane */
+    int32_t shadow_mode;           /* 0: the default (packets, see RP_FLAG_SHADOW_LANES),
+                                      1: packets, 2: one ray per lane */
 } rp_batch_tuning;
 
 typedef struct {

@@ -58,7 +58,7 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scene plain form")
     ap.add_argument("--shadow-mode", type=int, default=-1, choices=[-1, 0, 1, 2],
-                    help="shadow rays: 1 packets, 2 one per lane, 0 by scene size; -1 autotunes")
+                    help="shadow rays: 1 packets, 2 one per lane, 0 the default (packets); -1 autotunes")
     a = ap.parse_args(argv)
     t_setup = time.time()
     ctx = rpr.Context(0, torch.cuda.current_stream())

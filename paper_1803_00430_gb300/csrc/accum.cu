@@ -48,55 +48,113 @@ __global__ void k_count(TraceWork w, unsigned long long chunk)
         atomicAdd(&w.cnt[w.rec.key[i]], 1u);
 }
 
-// exclusive scan of cnt[0..n) into off[0..n], off[n] = total; one block of 1024
-// exclusive scan of cnt[0..n) into off[0..n] (off[n] = total; off may be cnt): one
-// block of 1024 threads walks the array in tiles of 4096, each thread taking 4
-// consecutive counts, with the running total carried from tile to tile.  With a gate,
-// the scan is skipped when *gate_total <= gate_q0 (an empty record chunk).
+// Exclusive scan of cnt[0..n) into off[0..n] (off[n] = total; off may be cnt).  A
+// block of 1024 threads scans tiles of SCAN_TILE = 4096 counts, each thread taking 4
+// consecutive ones.  Short arrays take one block that walks the tiles carrying the
+// running total; long ones take two launches: the tile sums, then every tile scanned
+// in parallel from its carry, which its block adds up from the sums of the tiles
+// before it.  With a gate, the scan is skipped when *gate_total <= gate_q0 (an empty
+// record chunk).
+__device__ __forceinline__ bool scan_gated(const unsigned long long *gate_total, unsigned long long gate_q0)
+{
+    return gate_total && gate_q0 > 0 && *gate_total <= gate_q0;
+}
+
+// scan of the tile at `base` from `carry`; returns the tile's total (every thread)
+__device__ __forceinline__ uint32_t scan_tile(const uint32_t *cnt, uint32_t *off, int n, int base, uint32_t carry,
+                                              uint32_t *warp_sums)
+{
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int i0 = base + 4 * t;
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = i0 + k < n ? cnt[i0 + k] : 0u;
+        s += v[k];
+    }
+    uint32_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t ws = warp_sums[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, ws, o);
+            if (lane >= o) ws += y;
+        }
+        warp_sums[lane] = ws;
+    }
+    __syncthreads();
+    uint32_t run = carry + x - s + (wid > 0 ? warp_sums[wid - 1] : 0u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (i0 + k < n) off[i0 + k] = run;
+        run += v[k];
+    }
+    const uint32_t total = warp_sums[31];
+    __syncthreads();  // every thread has read warp_sums
+    return total;
+}
+
 __global__ void __launch_bounds__(1024) k_scan(const uint32_t *cnt, uint32_t *off, int n,
                                                const unsigned long long *gate_total, unsigned long long gate_q0)
 {
-    if (gate_total && gate_q0 > 0 && *gate_total <= gate_q0) return;
+    if (scan_gated(gate_total, gate_q0)) return;
     __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t carry;
+    uint32_t carry = 0;
+    for (int base = 0; base < n; base += SCAN_TILE) carry += scan_tile(cnt, off, n, base, carry, warp_sums);
+    if (threadIdx.x == 0) off[n] = carry;
+}
+
+// sum of part[0..m) over the block (every thread gets it)
+__device__ __forceinline__ uint32_t block_sum(const uint32_t *part, int m, uint32_t *warp_sums)
+{
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    if (t == 0) carry = 0;
+    uint32_t s = 0;
+    for (int i = t; i < m; i += blockDim.x) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) warp_sums[wid] = s;
     __syncthreads();
-    for (int base = 0; base < n; base += 4096) {
-        const int i0 = base + 4 * t;
-        uint32_t v[4], s = 0;
+    uint32_t tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_sums[w];
+    __syncthreads();  // warp_sums is reused
+    return tot;
+}
+
+// sum of each tile
+__global__ void __launch_bounds__(1024) k_scan_part(const uint32_t *cnt, int n, uint32_t *part,
+                                                    const unsigned long long *gate_total, unsigned long long gate_q0)
+{
+    if (scan_gated(gate_total, gate_q0)) return;
+    __shared__ uint32_t warp_sums[32];
+    const int i0 = blockIdx.x * SCAN_TILE + 4 * threadIdx.x;
+    uint32_t v[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[k] = i0 + k < n ? cnt[i0 + k] : 0u;
-            s += v[k];
-        }
-        uint32_t x = s;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_sums[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-            uint32_t ws = warp_sums[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, ws, o);
-                if (lane >= o) ws += y;
-            }
-            warp_sums[lane] = ws;
-        }
-        __syncthreads();
-        uint32_t run = carry + x - s + (wid > 0 ? warp_sums[wid - 1] : 0u);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (i0 + k < n) off[i0 + k] = run;
-            run += v[k];
-        }
-        __syncthreads();  // every thread has read carry and warp_sums
-        if (t == 1023) carry = run;
-        __syncthreads();
+    for (int k = 0; k < 4; ++k) v[k] = i0 + k < n ? cnt[i0 + k] : 0u;
+    // the four counts of each thread, then the block
+    __shared__ uint32_t sums[1024];
+    sums[threadIdx.x] = v[0] + v[1] + v[2] + v[3];
+    __syncthreads();
+    const uint32_t tot = block_sum(sums, 1024, warp_sums);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// every tile from its carry, the sum of the tiles before it (part: the tile sums)
+__global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t *cnt, uint32_t *off, int n,
+                                                     const uint32_t *part, int nparts,
+                                                     const unsigned long long *gate_total, unsigned long long gate_q0)
+{
+    if (scan_gated(gate_total, gate_q0)) return;
+    __shared__ uint32_t warp_sums[32];
+    const uint32_t carry = block_sum(part, blockIdx.x, warp_sums);
+    if (blockIdx.x == 0) {
+        const uint32_t total = block_sum(part, nparts, warp_sums);
+        if (threadIdx.x == 0) off[n] = total;
     }
-    if (t == 0) off[n] = carry;
+    scan_tile(cnt, off, n, blockIdx.x * SCAN_TILE, carry, warp_sums);
 }
 
 __global__ void k_scatter(TraceWork w, unsigned long long chunk)
@@ -225,6 +283,18 @@ __global__ void k_direct_add(TraceWork w)
     w.H[((unsigned long long)w.src_base * B * K + i) * T + dd.bin] += dd.sh[kk];
 }
 
+void scan_u32(const uint32_t *cnt, uint32_t *off, int n, uint32_t *part, const unsigned long long *gate_total,
+              unsigned long long gate_q0, cudaStream_t st)
+{
+    const int nparts = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (!part || nparts <= 2) {
+        k_scan<<<1, 1024, 0, st>>>(cnt, off, n, gate_total, gate_q0);
+        return;
+    }
+    k_scan_part<<<nparts, 1024, 0, st>>>(cnt, n, part, gate_total, gate_q0);
+    k_scan_apply<<<nparts, 1024, 0, st>>>(cnt, off, n, part, nparts, gate_total, gate_q0);
+}
+
 }  // namespace
 
 void launch_clear_counts(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
@@ -237,14 +307,14 @@ void launch_count(const TraceWork &w, unsigned long long chunk, int blocks, cuda
     k_count<<<blocks, 256, 0, st>>>(w, chunk);
 }
 
-void launch_scan_u32(const uint32_t *cnt, uint32_t *off, int n, cudaStream_t st)
+void launch_scan_u32(const uint32_t *cnt, uint32_t *off, int n, uint32_t *part, cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(cnt, off, n, nullptr, 0ull);
+    scan_u32(cnt, off, n, part, nullptr, 0ull, st);
 }
 
 void launch_scan(const TraceWork &w, unsigned long long chunk, cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(w.cnt, w.off, w.k.S * w.k.T, &w.ctr->total_items, chunk * w.items_per_chunk);
+    scan_u32(w.cnt, w.off, w.k.S * w.k.T, w.scan_part, &w.ctr->total_items, chunk * w.items_per_chunk, st);
 }
 
 void launch_scatter(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)

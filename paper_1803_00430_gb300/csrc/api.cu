@@ -134,6 +134,9 @@ int reserve(rp_ctx *c, const StepSizes &z, int B, int njobs, int total_sources, 
     if ((r = ensure(c, c->cnt, z.keys * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->cur, z.keys * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->off, (z.keys + 1) * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->scan_part,
+                    scan_parts(std::max<unsigned long long>(z.keys, hit_order_cells(njobs))) * sizeof(uint32_t))))
+        return r;
     if ((r = ensure(c, c->Hs, z.cells * sizeof(float)))) return r;
     if ((r = ensure(c, c->He, z.cells * sizeof(float)))) return r;
     if ((r = ensure(c, c->src, (size_t)(total_sources + njobs) * sizeof(float4)))) return r;
@@ -157,6 +160,7 @@ void bind_workspace(rp_ctx *c, const StepSizes &z, TraceWork &w)
     w.status = c->d_status;
     w.cnt = (uint32_t *)c->cnt.p;
     w.off = (uint32_t *)c->off.p;
+    w.scan_part = (uint32_t *)c->scan_part.p;
     w.cur = (uint32_t *)c->cur.p;
     w.perm = (uint32_t *)c->perm.p;
     w.Hs = (float *)c->Hs.p;
@@ -300,7 +304,8 @@ int rp_destroy(rp_ctx *c)
     for (Buf *b : {&c->hit_p, &c->hit_plo, &c->hit_n, &c->hit_ws, &c->hit_rid, &c->shit_p, &c->hord_perm,
                    &c->shit_n, &c->shit_ws, &c->shit_rid, &c->hord_cell, &c->hord_cnt, &c->rec_key, &c->rec_rid,
                    &c->rec_e, &c->perm, &c->rerun,
-                   &c->cnt, &c->off, &c->cur, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H, &c->direct,
+                   &c->cnt, &c->off, &c->cur, &c->scan_part, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H,
+                   &c->direct,
                    &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job})
         free_buf(*b);
     for (auto &p : c->pending) {
@@ -519,7 +524,7 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
     w.H = H;
     w.direct = direct;
     w.shadow_steps = c->shadow_steps;
-    w.shadow_packets = shadow_packets_for(p->flags, sc->num_tris);
+    w.shadow_packets = shadow_packets_for(p->flags);
 
     StepLaunch L;
     L.w = w;

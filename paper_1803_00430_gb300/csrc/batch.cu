@@ -164,6 +164,8 @@ int reserve_batch(rp_batch *b)
     if ((r = grow(c, c->cnt, z.keys * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->cur, z.keys * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->off, (z.keys + 1) * sizeof(uint32_t)))) return r;
+    if ((r = grow(c, c->scan_part, scan_parts(std::max<unsigned long long>(z.keys, cells)) * sizeof(uint32_t))))
+        return r;
     if ((r = grow(c, c->Hs, z.cells * sizeof(float)))) return r;
     if ((r = grow(c, c->He, z.cells * sizeof(float)))) return r;
     if ((r = grow(c, c->js, (size_t)b->max_jobs * sizeof(JobState)))) return r;
@@ -185,6 +187,7 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
     w.status = c->d_status;
     w.cnt = (uint32_t *)c->cnt.p;
     w.off = (uint32_t *)c->off.p;
+    w.scan_part = (uint32_t *)c->scan_part.p;
     w.cur = (uint32_t *)c->cur.p;
     w.perm = (uint32_t *)c->perm.p;
     w.Hs = (float *)c->Hs.p;
@@ -226,10 +229,8 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
     w.direct = b->direct;
     w.shadow_steps = b->tuning.shadow_steps;
     {
-        int max_tris = 0;
-        for (int j = g.job_begin; j < g.job_end; ++j) max_tris = std::max(max_tris, b->h_jobs[j].sc.num_tris);
         const int mode = b->tuning.shadow_mode;
-        w.shadow_packets = mode == 1 ? 1 : mode == 2 ? 0 : shadow_packets_for(b->common.flags, max_tris);
+        w.shadow_packets = mode == 1 ? 1 : mode == 2 ? 0 : shadow_packets_for(b->common.flags);
     }
     L.n_rec_chunks = g.z.n_chunks;
     L.refill = 0;

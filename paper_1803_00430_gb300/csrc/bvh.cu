@@ -495,8 +495,8 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
             const int nb = (c + 255) / 256;
             k_ploc_nn<<<nb, 256, 0, st>>>(c, clo[cur], chi[cur], nn);
             k_ploc_flags<<<nb, 256, 0, st>>>(c, nn, keep, merge);
-            launch_scan_u32(keep, kpos, c, st);
-            launch_scan_u32(merge, mpos, c, st);
+            launch_scan_u32(keep, kpos, c, nullptr, st);
+            launch_scan_u32(merge, mpos, c, nullptr, st);
             k_ploc_merge<<<nb, 256, 0, st>>>(c, cref[cur], clo[cur], chi[cur], nn, keep, kpos, merge, mpos, child,
                                              nlo, nhi, pint, pleaf, cref[1 - cur], clo[1 - cur], chi[1 - cur]);
             uint32_t next = 0;

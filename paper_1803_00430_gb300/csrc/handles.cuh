@@ -42,8 +42,8 @@ struct rp_ctx {
     //   contribution records and their counting sort, running histogram sums, positions,
     //   counters, statistics, the host-buffer update's outputs, job tables
     Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, shit_p, shit_n, shit_ws, shit_rid, hord_cell, hord_perm, hord_cnt,
-        rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, Hs, He, src, ctr, stats, H, direct, params, state, jobs,
-        js, chunks, src_job;
+        rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, scan_part, Hs, He, src, ctr, stats, H, direct, params,
+        state, jobs, js, chunks, src_job;
     // profiling
     bool prof = false;
     std::vector<ProfPair> pending;

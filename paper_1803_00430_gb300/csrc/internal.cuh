@@ -149,9 +149,13 @@ struct HitOrder {
     uint32_t *cell;  // [total hits] cell of the flattened reflection f
     uint32_t *perm;  // [total hits] slot in Hits of the i-th reflection in cell order
     uint32_t *cnt;   // [ncells + 1] counts, then cursors
-    int bits;        // grid bits per axis
-    int ncells;      // njobs x 2^(3 bits)
+    int bits;        // code bits per job (near-cubic cells over the job's scene box)
+    int ncells;      // njobs x 2^bits
 };
+
+// counts per tile of the scans, and the tile sums a scan of n counts needs
+constexpr int SCAN_TILE = 4096;
+inline unsigned long long scan_parts(unsigned long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 // shadow items of a job with h stored reflections and S sources: tiles of 32
 // reflections x S sources, a short last tile padded to 32 per source
@@ -160,24 +164,22 @@ __host__ __device__ inline unsigned long long shadow_items(unsigned long long h,
     return ((h + 31ull) / 32ull) * 32ull * (unsigned long long)S;
 }
 
-// grid bits per axis for njobs jobs: at most 2^22 cells in all, 1..6 bits (a 64^3
-// grid per scene up to 16 scenes, 16^3 for 512)
-inline int hit_order_bits(int njobs)
+// Code bits per job of the reflection order (cells = njobs << bits): the cells of all
+// jobs together stay within 2^cells_log2, with at least 3 bits per job.  22 gives a
+// job alone 2^22 cells (about 0.15 m cubes over a 40 x 30 x 12 m hall).
+inline int hit_order_bits(int njobs, int cells_log2 = 22)
 {
-    int bits = 6;
-    while (bits > 1 && (long long)njobs << (3 * bits) > (1ll << 22)) --bits;
-    return bits;
+    int lg = 0;
+    while ((1ll << lg) < (long long)std::max(njobs, 1)) ++lg;
+    return std::max(3, cells_log2 - lg);
 }
-inline long long hit_order_cells(int njobs) { return (long long)std::max(njobs, 1) << (3 * hit_order_bits(njobs)); }
+inline long long hit_order_cells(int njobs, int cells_log2 = 22)
+{
+    return (long long)std::max(njobs, 1) << hit_order_bits(njobs, cells_log2);
+}
 
-// shadow-ray mode of a step: the flags, else packets below PACKET_MAX_TRIS triangles
-constexpr int PACKET_MAX_TRIS = 1 << 19;
-inline int shadow_packets_for(int flags, int max_tris)
-{
-    if (flags & RP_FLAG_SHADOW_PACKETS) return 1;
-    if (flags & RP_FLAG_SHADOW_LANES) return 0;
-    return max_tris < PACKET_MAX_TRIS ? 1 : 0;
-}
+// shadow-ray mode of a step: packets unless the flags ask for one ray per lane
+inline int shadow_packets_for(int flags) { return (flags & RP_FLAG_SHADOW_LANES) ? 0 : 1; }
 
 struct TraceWork {
     SceneJob job0;         // the first (in single-job steps the only) job, by value
@@ -202,6 +204,7 @@ struct TraceWork {
     int *status;
     // accumulation
     uint32_t *cnt, *off, *cur, *perm;
+    uint32_t *scan_part;  // tile sums of the multi-block scans (scan_parts of the longest scan)
     float *Hs, *He;  // running compensated sums [S][B][K][T] of the group
     float *H;        // output, [global source][B][K][T]
     rp_direct *direct;  // [global sources]
@@ -226,7 +229,8 @@ void launch_direct(const TraceWork &w, cudaStream_t st);
 void launch_clear_counts(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_count(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_scan(const TraceWork &w, unsigned long long chunk, cudaStream_t st);
-void launch_scan_u32(const uint32_t *cnt, uint32_t *off, int n, cudaStream_t st);
+// exclusive scan; `part` (scan_parts(n) entries, or null for one block) holds tile sums
+void launch_scan_u32(const uint32_t *cnt, uint32_t *off, int n, uint32_t *part, cudaStream_t st);
 void launch_scatter(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_accum(const TraceWork &w, int first_chunk, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_finalize(const TraceWork &w, cudaStream_t st);

@@ -35,6 +35,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[RP_NOALLOC_SCRA
 namespace {
 
 constexpr int MAX_DEVICES = 64;
+// cells of the reflection order (2^18: 1 MiB of counts, so that the scratch holds
+// useful problem sizes)
+constexpr int NOALLOC_CELLS_LOG2 = 18;
 std::mutex g_mu;
 void *g_scratch_ptr[MAX_DEVICES] = {};
 
@@ -107,12 +110,14 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     const unsigned long long o_hp = cv.take<float4>(z.hit_cap), o_hl = cv.take<float4>(z.hit_cap),
                              o_hn = cv.take<float4>(z.hit_cap), o_hw = cv.take<float>(z.hit_cap * B),
                              o_hr = cv.take<uint32_t>(z.hit_cap), o_hc = cv.take<uint32_t>(z.hit_cap),
-                             o_hk = cv.take<uint32_t>((unsigned long long)hit_order_cells(1) + 1);
+                             o_hk = cv.take<uint32_t>((unsigned long long)hit_order_cells(1, NOALLOC_CELLS_LOG2) + 1);
     const unsigned long long o_sp = cv.take<float4>(z.hit_cap), o_sq = cv.take<uint32_t>(z.hit_cap),
                              o_sn = cv.take<float4>(z.hit_cap), o_sw = cv.take<float>(z.hit_cap * B),
                              o_sr = cv.take<uint32_t>(z.hit_cap);
     const unsigned long long o_cnt = cv.take<uint32_t>(z.keys), o_off = cv.take<uint32_t>(z.keys + 1),
                              o_cur = cv.take<uint32_t>(z.keys);
+    const unsigned long long o_part = cv.take<uint32_t>(
+        scan_parts(std::max<unsigned long long>(z.keys, hit_order_cells(1, NOALLOC_CELLS_LOG2))));
     const unsigned long long o_hs = cv.take<float>(z.cells), o_he = cv.take<float>(z.cells);
     if (cv.off >= RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
     // the rest holds contribution records (key, ray, energies, sort index) and the
@@ -193,6 +198,7 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.status = c->d_status;
     w.cnt = (uint32_t *)(base + o_cnt);
     w.off = (uint32_t *)(base + o_off);
+    w.scan_part = (uint32_t *)(base + o_part);
     w.cur = (uint32_t *)(base + o_cur);
     w.perm = (uint32_t *)(base + o_pm);
     w.Hs = (float *)(base + o_hs);
@@ -204,11 +210,11 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.rerun_cap = z.rerun_cap;
     w.num_sms = c->num_sms;
     w.shadow_steps = c->shadow_steps;
-    w.shadow_packets = shadow_packets_for(p->flags, sc->num_tris);
+    w.shadow_packets = shadow_packets_for(p->flags);
     w.shits = {(float4 *)(base + o_sp), nullptr, (float4 *)(base + o_sn), (float *)(base + o_sw),
                (uint32_t *)(base + o_sr), z.hit_cap};
-    w.horder = {(uint32_t *)(base + o_hc), (uint32_t *)(base + o_sq), (uint32_t *)(base + o_hk), hit_order_bits(1),
-                (int)hit_order_cells(1)};
+    w.horder = {(uint32_t *)(base + o_hc), (uint32_t *)(base + o_sq), (uint32_t *)(base + o_hk),
+                hit_order_bits(1, NOALLOC_CELLS_LOG2), (int)hit_order_cells(1, NOALLOC_CELLS_LOG2)};
 
     StepLaunch L;
     L.w = w;

@@ -207,14 +207,36 @@ __device__ __forceinline__ int job_of_hit(const TraceWork &w, unsigned long long
     return lo;
 }
 
-__device__ __forceinline__ uint32_t spread3(uint32_t x)  // bits 0..9 to every third bit
+// Cell of a point in its job's box with `bits` code bits: the bits go one at a time to
+// the axis whose cells are then longest (ties to the lower axis), so the cells come out
+// near-cubic whatever the box's proportions, and the code interleaves the axes' bits from
+// the top, an axis taking part from its own highest bit on (a Morton order on unequal
+// bit depths; on a cube it is the plain Morton code).
+__device__ __forceinline__ uint32_t cell_code(const SceneView &sc, float3 p, int bits)
 {
-    x &= 0x3ffu;
-    x = (x | (x << 16)) & 0x030000ffu;
-    x = (x | (x << 8)) & 0x0300f00fu;
-    x = (x | (x << 4)) & 0x030c30c3u;
-    x = (x | (x << 2)) & 0x09249249u;
-    return x;
+    int nb[3] = {0, 0, 0};
+    float ce[3] = {fmaxf(sc.ext[0], 0.f), fmaxf(sc.ext[1], 0.f), fmaxf(sc.ext[2], 0.f)};
+    for (int i = 0; i < bits; ++i) {
+        const int a = (ce[0] >= ce[1] && ce[0] >= ce[2]) ? 0 : (ce[1] >= ce[2] ? 1 : 2);
+        ++nb[a];
+        ce[a] *= 0.5f;
+    }
+    const float pc[3] = {p.x, p.y, p.z};
+    uint32_t q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float n = (float)(1u << nb[a]);
+        const float e = sc.ext[a] > 0.f ? sc.ext[a] : 1.f;
+        q[a] = (uint32_t)fminf(fmaxf((pc[a] - sc.lo[a]) / e * n, 0.f), n - 1.f);
+    }
+    const int top = max(nb[0], max(nb[1], nb[2]));
+    uint32_t code = 0;
+    for (int i = top - 1; i >= 0; --i) {
+#pragma unroll
+        for (int a = 2; a >= 0; --a)
+            if (i < nb[a]) code = (code << 1) | ((q[a] >> i) & 1u);
+    }
+    return code;
 }
 
 // cell of every stored reflection, and the cell counts
@@ -222,22 +244,13 @@ __global__ void k_hit_cells(TraceWork w)
 {
     const unsigned long long n = w.ctr->total_hits;
     const int bits = w.horder.bits;
-    const float cells = (float)(1 << bits);
     for (unsigned long long f = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; f < n;
          f += (unsigned long long)gridDim.x * blockDim.x) {
         const int job = w.njobs > 1 ? job_of_hit(w, f) : 0;
         const SceneJob &J = w.njobs > 1 ? w.jobs[job] : w.job0;
         const unsigned long long slot = J.hit_off + (f - (w.njobs > 1 ? w.js[job].hit_prefix : 0ull));
         const float4 P = w.hits.p[slot];
-        const float pc[3] = {P.x, P.y, P.z};
-        uint32_t code = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float e = J.sc.ext[a] > 0.f ? J.sc.ext[a] : 1.f;
-            const float q = fminf(fmaxf((pc[a] - J.sc.lo[a]) / e * cells, 0.f), cells - 1.f);
-            code |= spread3((uint32_t)q) << (2 - a);
-        }
-        const uint32_t cell = ((uint32_t)job << (3 * bits)) | code;
+        const uint32_t cell = ((uint32_t)job << bits) | cell_code(J.sc, xyz(P), bits);
         w.horder.cell[f] = cell;
         atomicAdd(&w.horder.cnt[cell], 1u);
     }
@@ -1086,7 +1099,7 @@ void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st)
 {
     cudaMemsetAsync(w.horder.cnt, 0, sizeof(uint32_t) * ((size_t)w.horder.ncells + 1), st);
     k_hit_cells<<<blocks, 256, 0, st>>>(w);
-    launch_scan_u32(w.horder.cnt, w.horder.cnt, w.horder.ncells, st);
+    launch_scan_u32(w.horder.cnt, w.horder.cnt, w.horder.ncells, w.scan_part, st);
     k_hit_scatter<<<blocks, 256, 0, st>>>(w);
     k_hit_gather<<<blocks, 256, 0, st>>>(w);
 }
