@@ -57,11 +57,12 @@ ALU_OPS_PER_TRI = 7.0
 ALU_LANES_PER_SM = 64
 FLOPS_PER_NODE = 24.0   # FMA-pipe flops of a visit (12 FMA), reported beside
 FLOPS_PER_TRI = 27.0    # Moller-Trumbore arithmetic
-# DRAM bytes (read + write) of one shadow-ray launch (k_shadow_packet, the mode this
-# scene uses) in an ncu capture of the same update at 30,000 primaries, and the
-# shadow rays that launch traced; a full-size launch is credited with the same bytes
-# per shadow ray.
-NCU_SHADOW_DRAM = (96_999_424 + 18_942_720, 18_878_384)
+# DRAM bytes (read + write) of the shadow-ray launch (k_shadow_packet, the default
+# mode) of one update in an ncu capture at fewer primaries -- medium at 30,000, large
+# at 20,000 -- and the shadow rays that launch traced; a full-size update is credited
+# with the same bytes per shadow ray.
+NCU_SHADOW_DRAM = {"medium": (95_201_024 + 18_004_480, 18_878_384),
+                   "large": (23_693_056 + 1_536, 8_495_384)}
 
 
 def _peaks():
@@ -348,8 +349,9 @@ def main():
     peak_tops = 152 * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     achieved = ops / avg_s / 1e12
     fma_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    traffic = (NCU_SHADOW_DRAM[0] * st["shadow_rays"] / NCU_SHADOW_DRAM[1]
-               if name == "shadow" and not args.fp32_paths and args.workload == "medium" else None)
+    dram = NCU_SHADOW_DRAM[args.workload]
+    traffic = (dram[0] * st["shadow_rays"] / dram[1]
+               if name == "shadow" and not args.fp32_paths and args.shadow_mode != "lanes" else None)
     shares = {k: round(v[1] / sum(x[1] for x in kt.values()), 4) for k, v in kt.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -371,8 +373,9 @@ def main():
                 "tri_tests_per_shadow_ray": stc["tri_tests"][1] / max(1, stc["shadow_rays"])},
         "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tops, "traffic": traffic,
-                     "traffic_note": "DRAM bytes per update (one launch here), from an ncu capture at 30k "
-                                     "primaries scaled by shadow rays" if traffic else None,
+                     "traffic_note": ("DRAM bytes per update of the shadow-ray kernel, from an ncu capture at "
+                                      f"{'30k' if args.workload == 'medium' else '20k'} primaries scaled by "
+                                      "shadow rays") if traffic else None,
                      "launches_per_update": n_l / args.steps,
                      "peak_note": f"ALU pipe (FP32 min/max/compare): 152 SMs x {ALU_LANES_PER_SM} lanes at the "
                                   f"median sampled SM clock {sm_mhz:.0f} MHz (derived, not measured)",

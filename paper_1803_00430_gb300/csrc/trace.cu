@@ -407,7 +407,12 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
     uint32_t rid = 0;
     V3<R> o = v3<R>(0, 0, 0), d = o;
     R L = 0;
-    float wgt[MAXB], absorbed[MAXB];
+    // the path's band weights and absorbed weights, in the lane's own column of shared
+    // memory (band b at [b * PATH_THREADS], no bank conflicts): in registers they made
+    // the kernel spill at its 128-register bound
+    __shared__ float swgt[MAXB][PATH_THREADS], sabs[MAXB][PATH_THREADS];
+    float *const wgt = &swgt[0][threadIdx.x];
+    float *const absorbed = &sabs[0][threadIdx.x];
     int prev = -1, h = 1;
     bool spec_prev = false;
     uint64_t hash = FNV_OFFSET;
@@ -444,8 +449,8 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     L = 0;
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b) {
-                        wgt[b] = 1.0f;
-                        absorbed[b] = 0.0f;
+                        wgt[b * PATH_THREADS] = 1.0f;
+                        absorbed[b * PATH_THREADS] = 0.0f;
                     }
                     prev = -1;
                     h = 1;
@@ -501,7 +506,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                 ++contrib;
                 float e[MAXB];
 #pragma unroll
-                for (int b = 0; b < MAXB; ++b) e[b] = wgt[b] * inv_pi_rs2;
+                for (int b = 0; b < MAXB; ++b) e[b] = wgt[b * PATH_THREADS] * inv_pi_rs2;
                 float binf;
                 const float x = ((Lf + tsph) / k.c) * k.rate;
                 if (fabsf(x - rintf(x)) < BIN_GUARD) {
@@ -531,7 +536,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
         if (tri < 0) {
 #pragma unroll
             for (int b = 0; b < MAXB; ++b)
-                if (b < B) atomicAdd(&acc.esc[b], (double)wgt[b]);
+                if (b < B) atomicAdd(&acc.esc[b], (double)wgt[b * PATH_THREADS]);
             end_ray = true;
         } else {
             const float4 ta = __ldg(sc.tris + 3 * tri), tb = __ldg(sc.tris + 3 * tri + 1),
@@ -561,8 +566,8 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
             for (int b = 0; b < MAXB; ++b) {
                 if (b < B) {
                     const float a = __ldg(al + b);
-                    absorbed[b] += wgt[b] * a;
-                    wgt[b] *= (1.0f - a);
+                    absorbed[b * PATH_THREADS] += wgt[b * PATH_THREADS] * a;
+                    wgt[b * PATH_THREADS] *= (1.0f - a);
                 }
             }
             if (h >= k.min_order && J.S > 0) {
@@ -578,7 +583,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     const float *sb = sc.scat + mat * B;
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b)
-                        if (b < B) w.hits.ws[j * B + b] = wgt[b] * __ldg(sb + b);
+                        if (b < B) w.hits.ws[j * B + b] = wgt[b * PATH_THREADS] * __ldg(sb + b);
                     w.hits.rid[j] = rid;
                 } else {
                     raise_error(w.status, RP_ERR_CAPACITY);
@@ -587,7 +592,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
             if (h == M) {
 #pragma unroll
                 for (int b = 0; b < MAXB; ++b)
-                    if (b < B) atomicAdd(&acc.rem[b], (double)wgt[b]);
+                    if (b < B) atomicAdd(&acc.rem[b], (double)wgt[b * PATH_THREADS]);
                 end_ray = true;
             } else {
                 const U4 r = philox4x32_10(rid, J.scene_id, (uint32_t)h, 0u, key0, key1);
@@ -607,7 +612,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     const float *wd = sc.wdiff + mat * B;
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b)
-                        if (b < B) wgt[b] *= __ldg(wd + b);
+                        if (b < B) wgt[b * PATH_THREADS] *= __ldg(wd + b);
                     spec_prev = false;
                 } else {
                     d = d - n * ((R)2 * dot3(d, n));
@@ -615,7 +620,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     const float *wsp = sc.wspec + mat * B;
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b)
-                        if (b < B) wgt[b] *= __ldg(wsp + b);
+                        if (b < B) wgt[b * PATH_THREADS] *= __ldg(wsp + b);
                     spec_prev = true;
                 }
                 o = p;
@@ -626,7 +631,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
         if (end_ray) {
 #pragma unroll
             for (int b = 0; b < MAXB; ++b)
-                if (b < B) atomicAdd(&acc.absb[b], (double)absorbed[b]);
+                if (b < B) atomicAdd(&acc.absb[b], (double)absorbed[b * PATH_THREADS]);
             if (HASH && w.ray_hash && rid >= J.first_ray && rid - J.first_ray < J.num_rays)
                 w.ray_hash[rid - J.first_ray] = hash;
             have = false;
