@@ -11,8 +11,11 @@
 namespace rp {
 
 // Records kept in device memory at once (one chunk of next-event work plus the
-// records of source-sphere hits).  40 bytes each at 8 bands.
-constexpr unsigned long long REC_BUDGET = 1ull << 28;
+// records of source-sphere hits): 2^30, 44 bytes each at 8 bands with the sort index
+// (47 GB at most; a problem takes only what its worst case needs).  Record chunks
+// are sized for the worst case and every chunk launches its kernels, so fewer,
+// larger chunks save launches on problems whose worst case is far above their work.
+constexpr unsigned long long REC_BUDGET = 1ull << 30;
 
 struct Buf {
     void *p = nullptr;

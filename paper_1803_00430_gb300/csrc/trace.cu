@@ -727,15 +727,16 @@ __device__ __forceinline__ int job_from(const TraceWork &w, int from, unsigned l
 template <bool COUNT, bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsigned long long chunk)
 {
+    const unsigned long long total = w.ctr->total_items;
+    const unsigned long long q0 = chunk * w.items_per_chunk;
+    const unsigned long long items = total > q0 ? min(w.items_per_chunk, total - q0) : 0ull;
+    if (items == 0) return;  // a record chunk past the step's items (the whole block)
     __shared__ int sstack[SMEM_STACK * SHADOW_THREADS];
     __shared__ BlockAcc acc;
     acc_init(acc);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    const unsigned long long total = w.ctr->total_items;
-    const unsigned long long q0 = chunk * w.items_per_chunk;
-    const unsigned long long items = total > q0 ? min(w.items_per_chunk, total - q0) : 0ull;
     const int steps_per_visit = w.shadow_steps;
     const float inv_pi = 1.0f / PI_F;
     int lstack[LOCAL_STACK];
@@ -839,6 +840,10 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
 template <bool COUNT, bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w, unsigned long long chunk)
 {
+    const unsigned long long total = w.ctr->total_items;
+    const unsigned long long q0 = chunk * w.items_per_chunk;
+    const unsigned long long items = total > q0 ? min(w.items_per_chunk, total - q0) : 0ull;
+    if (items == 0) return;  // a record chunk past the step's items (the whole block)
     __shared__ int pnode[SHADOW_THREADS / 32][STACK_DEPTH];
     __shared__ unsigned pmask[SHADOW_THREADS / 32][STACK_DEPTH];
     __shared__ BlockAcc acc;
@@ -846,9 +851,6 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
     __syncthreads();
 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned long long total = w.ctr->total_items;
-    const unsigned long long q0 = chunk * w.items_per_chunk;
-    const unsigned long long items = total > q0 ? min(w.items_per_chunk, total - q0) : 0ull;
     const float inv_pi = 1.0f / PI_F;
     unsigned long long shadow = 0, contrib = 0;
     TravStats ts = {0u, 0u};
@@ -1017,11 +1019,12 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
 // FP64 decisions for the shadow rays whose FP32 visibility was rounding-sensitive
 __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_exact(TraceWork w, unsigned long long chunk)
 {
+    const unsigned long long n = min(w.ctr->n_rerun, w.rerun_cap);
+    if (n == 0) return;  // nothing queued (the whole grid)
     __shared__ int sstack[SMEM_STACK * SHADOW_THREADS];
     __shared__ BlockAcc acc;
     acc_init(acc);
     __syncthreads();
-    const unsigned long long n = min(w.ctr->n_rerun, w.rerun_cap);
     unsigned long long contrib = 0;
     (void)chunk;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
