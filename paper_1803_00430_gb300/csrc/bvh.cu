@@ -360,7 +360,15 @@ __global__ void k_pack_nodes(int n, const uint32_t *__restrict__ order, const fl
     nodes[4 * i + 0] = make_float4(l0.x - pad, h0.x + pad, l0.y - pad, h0.y + pad);
     nodes[4 * i + 1] = make_float4(l1.x - pad, h1.x + pad, l1.y - pad, h1.y + pad);
     nodes[4 * i + 2] = make_float4(l0.z - pad, h0.z + pad, l1.z - pad, h1.z + pad);
-    nodes[4 * i + 3] = make_float4(__int_as_float(c.x), __int_as_float(c.y), 0.f, 0.f);
+    // split code: the axis along which the children's centres lie farthest apart (bits
+    // 0-1) and whether the first child's centre is the higher one on it (bit 2); a
+    // packet of shadow rays walks first the child on the side its rays come from
+    const float d[3] = {(l1.x + h1.x) - (l0.x + h0.x), (l1.y + h1.y) - (l0.y + h0.y),
+                        (l1.z + h1.z) - (l0.z + h0.z)};
+    const float ax = fabsf(d[0]), ay = fabsf(d[1]), az = fabsf(d[2]);
+    const int axis = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    const int split = axis | (d[axis] < 0.f ? 4 : 0);
+    nodes[4 * i + 3] = make_float4(__int_as_float(c.x), __int_as_float(c.y), __int_as_float(split), 0.f);
 }
 
 __global__ void k_pack_tris(int nt, const uint32_t *__restrict__ order, const float *__restrict__ verts,

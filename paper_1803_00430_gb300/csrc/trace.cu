@@ -901,6 +901,9 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
             const unsigned grp = __ballot_sync(FULL, traced && job == jl) & todo;
             todo &= ~grp;
             const SceneView sc = BATCH ? w.jobs[jl].sc : w.job0.sc;  // in registers for the walk
+            // direction signs of the leader's ray (the packet's rays are nearly parallel)
+            const unsigned dsign = __shfl_sync(
+                FULL, (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u), leader);
             auto leaf = [&](int tri) {  // the lane's any-hit test of one triangle
                 if (COUNT) ts.tris++;
                 if ((unsigned)tri >= (unsigned)sc.num_tris) {
@@ -967,10 +970,10 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 const unsigned m0 = __ballot_sync(FULL, h0 && ch0 >= 0 && !fin);
                 const unsigned m1 = __ballot_sync(FULL, h1 && ch1 >= 0 && !fin);
                 if (m0 && m1) {
-                    // the nearer child for most of the lanes that reach both goes first
-                    const unsigned both = m0 & m1;
-                    const unsigned later = __ballot_sync(FULL, ((both >> lane) & 1u) && c1min < c0min);
-                    const bool swap = both ? 2 * __popc(later) > __popc(both) : false;
+                    // the child on the side the rays head to goes first: on the node's
+                    // split axis, the higher child for rays heading up the axis
+                    const int split = __float_as_int(n3.z);
+                    const bool swap = (((dsign >> (split & 3)) ^ (unsigned)(split >> 2)) & 1u) == 0u;
                     if (sp >= STACK_DEPTH) {
                         if (lane == 0) raise_error(w.status, RP_ERR_STACK_OVERFLOW);
                         break;

@@ -3,8 +3,9 @@
 // Stack-based while-while traversal in the style of Aila & Laine (HPG 2009): each
 // node fetch is four 16-byte loads through the read-only path; both children's boxes
 // are slab-tested together; leaf children (one triangle each) are intersected as soon
-// as their box is hit; of two internal children the nearer is visited first and the
-// farther is pushed.  The stack keeps its first SMEM_STACK entries in shared memory
+// as their box is hit; of two internal children a closest-hit query visits the nearer
+// first, a resumable shadow-ray query (any_hit_steps) the one it enters later, and the
+// other is pushed.  The stack keeps its first SMEM_STACK entries in shared memory
 // (one column per thread, conflict-free) and the rest in a small per-thread array.
 //
 // Closest hit: the nearest t in (tmin, tmax); equal t goes to the smaller original
@@ -405,18 +406,20 @@ __device__ __forceinline__ bool any_hit_steps(const SceneView &sc, const AnyRay 
             h1 = false;
         }
         if (h0 && h1) {
-            const bool swap = c1min < c0min;
-            const int nearc = swap ? ch1 : ch0, farc = swap ? ch0 : ch1;
+            // the child the ray enters later goes first: a shadow ray leaves a surface,
+            // and what blocks it lies more often towards the source than around its origin
+            const bool swap = c1min > c0min;
+            const int first = swap ? ch1 : ch0, second = swap ? ch0 : ch1;
             if (q.sp < SMEM_STACK) {
-                sstack[q.sp * stride] = farc;
+                sstack[q.sp * stride] = second;
             } else if (q.sp < STACK_DEPTH) {
-                lstack[q.sp - SMEM_STACK] = farc;
+                lstack[q.sp - SMEM_STACK] = second;
             } else {
                 raise_error(status, RP_ERR_STACK_OVERFLOW);
                 return true;
             }
             ++q.sp;
-            q.node = nearc;
+            q.node = first;
         } else if (h0) {
             q.node = ch0;
         } else if (h1) {
