@@ -211,7 +211,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp32-paths", action="store_true", help="time the all-FP32 path precision form")
     ap.add_argument("--shadow-mode", default="auto", choices=["auto", "packets", "lanes"],
-                    help="shadow rays as warp packets or one per lane (auto: by scene size)")
+                    help="shadow rays as warp packets or one per lane (auto: the library default, packets)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--rays", type=int, default=0, help="primaries per update (default: the workload's 200k; "
