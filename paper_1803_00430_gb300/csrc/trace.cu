@@ -931,16 +931,8 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
             }
             const int iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
             int node = 0, sp = 0, iters = 0;
-            unsigned mask = grp;
-            while (true) {
-                mask &= ~__ballot_sync(FULL, fin);
-                if (mask == 0) {
-                    if (sp == 0) break;
-                    --sp;
-                    node = sn[sp];
-                    mask = sm[sp];
-                    continue;
-                }
+            unsigned mask = grp;  // lanes of the group that reach `node` and have no answer yet
+            while (mask) {
                 if (++iters > iter_cap) {
                     if (lane == 0) raise_error(w.status, RP_ERR_TIMEOUT);
                     break;
@@ -993,7 +985,14 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                     node = ch1;
                     mask = m1;
                 } else {
+                    // pop until an entry still has lanes without an answer
+                    const unsigned answered = __ballot_sync(FULL, fin);
                     mask = 0;
+                    while (mask == 0 && sp > 0) {
+                        --sp;
+                        node = sn[sp];
+                        mask = sm[sp] & ~answered;
+                    }
                 }
             }
             __syncwarp();
