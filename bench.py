@@ -61,8 +61,8 @@ FLOPS_PER_TRI = 27.0    # Moller-Trumbore arithmetic
 # mode) of one update in an ncu capture at fewer primaries -- medium at 30,000, large
 # at 20,000 -- and the shadow rays that launch traced; a full-size update is credited
 # with the same bytes per shadow ray.
-NCU_SHADOW_DRAM = {"medium": (94_484_480 + 17_776_640, 18_878_384),
-                   "large": (21_494_784 + 256, 8_495_384)}
+NCU_SHADOW_DRAM = {"medium": (94_667_776 + 17_925_632, 18_878_384),
+                   "large": (21_502_464 + 0, 8_495_384)}
 
 
 def _peaks():
