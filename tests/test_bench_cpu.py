@@ -1,0 +1,35 @@
+"""The benchmark's CPU-side contract: the reference arm (the oracle timed on the host
+cores) prints one JSON line with the keys the driver reads, and the CPU baseline sizes
+its ray sample to the requested time."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_json_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 0
+    assert d["value"] > 0 and d["unit"] == "ray segments/s" and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("medium")
+
+
+def test_cpu_baseline_scales_the_sample_to_the_target():
+    sys.path.insert(0, ROOT)
+    import bench
+    out = bench.cpu_baseline(target_s=2.0)
+    assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] == (os.cpu_count() or 1)
+    rays = int(out["sample"].split(" ")[0])
+    wall = float(out["sample"].rsplit(", ", 1)[1].split(" ")[0])
+    # grown past the 400-ray probe until the sample takes about the target (or the workload)
+    assert rays > 400 and (wall >= 1.0 or rays == bench.WORKLOAD["num_rays"])
