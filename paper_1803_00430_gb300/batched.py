@@ -20,6 +20,9 @@ import numpy as np
 from . import rpr, scenes
 
 TRACE = dict(max_order=64, sh_order=2, num_bins=2000, min_order=1, ir_rate_hz=1000.0)
+# the large workload's update (procedural city): 1M primaries x 200 reflections per listener
+CITY_TRACE = dict(max_order=200, sh_order=3, num_bins=3000, min_order=1, ir_rate_hz=1000.0)
+CITY_RAYS = 1_000_000
 
 
 def build(ctx: rpr.Context, n_scenes: int, bands: int = 8):
@@ -29,6 +32,16 @@ def build(ctx: rpr.Context, n_scenes: int, bands: int = 8):
     scs = [scenes.room_or_corridor(sd, tris, bands=bands, num_sources=S) for sd, tris, S, _ in specs]
     rs = [rpr.Scene.from_scene(ctx, sc) for sc in scs]
     return rs, scs, [r for *_, r in specs]
+
+
+def build_city(ctx: rpr.Context, n_listeners: int):
+    """The large workload as a batch: the city's one BVH, its 256 sources, and
+    n_listeners listeners (one update each, 1M primaries x 200 reflections)."""
+    import dataclasses
+    city = scenes.city()
+    r = rpr.Scene.from_scene(ctx, city)
+    scs = [dataclasses.replace(city, listener=l) for l in scenes.city_listeners(city, n_listeners)]
+    return [r] * len(scs), scs, [CITY_RAYS] * len(scs)
 
 
 def _events_ms(fn, steps: int, flush) -> float:
@@ -57,13 +70,16 @@ def main(argv=None):
     ap.add_argument("--autotune-cache", default="", help="text file of autotuned launch shapes ('' = none)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scene plain form")
+    ap.add_argument("--city", type=int, default=0, metavar="K",
+                    help="the large workload instead: the city with K listeners (1M primaries x 200 reflections each)")
     ap.add_argument("--shadow-mode", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="shadow rays: 1 packets, 2 one per lane, 0 the default (packets); -1 autotunes")
     a = ap.parse_args(argv)
     t_setup = time.time()
     ctx = rpr.Context(0, torch.cuda.current_stream())
-    rs, scs, rays = build(ctx, a.scenes)
-    p = rpr.TraceParams(**TRACE)
+    trace = CITY_TRACE if a.city else TRACE
+    rs, scs, rays = build_city(ctx, a.city) if a.city else build(ctx, a.scenes)
+    p = rpr.TraceParams(**trace)
     items = [(rs[i], scs[i].listener, scs[i].sources, rays[i], i) for i in range(len(rs))]
     b = rpr.Batch(ctx, items, p)
     info = b.info()
@@ -88,8 +104,9 @@ def main(argv=None):
     st = b.stats_dict()
     work = float(st["segments"] + st["shadow_rays"])
     out = {
-        "form": "batched", "scenes": len(rs), "total_sources": b.S, "total_rays": int(info.total_rays),
-        "groups": int(info.num_groups), "triangles_total": int(sum(len(sc.tris) for sc in scs)),
+        "form": "batched", "workload": f"city x {a.city} listeners" if a.city else "rooms and corridors",
+        "scenes": len(rs), "total_sources": b.S, "total_rays": int(info.total_rays),
+        "groups": int(info.num_groups), "triangles_total": int(sum(len(sc.tris) for sc in {id(r): sc for r, sc in zip(rs, scs)}.values())),
         "ms_per_step": ms_batched, "updates_per_s": len(rs) * 1000.0 / ms_batched,
         "ray_segments_per_s": work * 1000.0 / ms_batched,
         "segments_per_step": st["segments"], "shadow_rays_per_step": st["shadow_rays"],
@@ -110,12 +127,12 @@ def main(argv=None):
         pos = [(torch.tensor(sc.listener, device="cuda"), torch.tensor(sc.sources, device="cuda")) for sc in scs]
         ep = rpr.rp_estimate_params(p.ir_rate_hz, 0.0, 0.0)
         for i, r in enumerate(rs):  # size the workspace once, outside the timed region
-            q = rpr.TraceParams(**TRACE, num_rays=rays[i], scene_id=i)
+            q = rpr.TraceParams(**trace, num_rays=rays[i], scene_id=i)
             rpr.check(ctx.lib.rp_trace_reserve(r.h, rpr.C.byref(q.c()), scs[i].num_sources), "reserve")
 
         def plain_step(k):
             for i, r in enumerate(rs):
-                q = rpr.TraceParams(**TRACE, num_rays=rays[i], scene_id=i,
+                q = rpr.TraceParams(**trace, num_rays=rays[i], scene_id=i,
                                     seed=scenes.PHILOX_KEY_BASE + 100 + k, flags=rpr.RP_FLAG_DEVICE_POSITIONS)
                 S = scs[i].num_sources
                 rpr.check(ctx.lib.rp_trace(r.h, rpr.C.byref(q.c()), rpr._ptr(pos[i][0]), rpr._ptr(pos[i][1]), S,

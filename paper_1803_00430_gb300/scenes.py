@@ -351,6 +351,19 @@ def city(seed: int = SEED_LARGE, grid: int = 64, tess: int = 7, ground_tess: int
                  room_hi=np.array([extent, extent, 60.0]))
 
 
+def city_listeners(sc: Scene, n: int, seed: int = SEED_LARGE + 1) -> np.ndarray:
+    """n listener positions for the city: its own listener, then seeded free points
+    (1-20 m above the ground, at least 1 m from buildings, sources and each other)."""
+    if n <= 1:
+        return sc.listener[None, :].astype(np.float32)
+    rng = np.random.default_rng(seed)
+    lo = np.array([0.0, 0.0, 1.0])
+    hi = np.array([sc.room_hi[0], sc.room_hi[1], 20.0])
+    extra = _free_points(rng, n - 1, lo, hi, sc.boxes, 0.0, 1.0, min_sep=1.0,
+                         avoid=[sc.listener, *sc.sources])
+    return np.concatenate([sc.listener[None, :], extra]).astype(np.float32)
+
+
 def batched_specs(seed: int = SEED_BATCHED, n_scenes: int = 512, bands: int = 8):
     """Per-scene sizes of the batched workload: triangle count log-uniform in
     [12, 40k], source count log-uniform over 1..64, ray count log-uniform in
