@@ -41,6 +41,13 @@ LARGE = dict(num_rays=1_000_000, max_order=200, sh_order=3, num_bins=3000, min_o
              speed_of_sound=343.0, source_radius=0.5)
 LARGE_NAME = ("large: procedural city, 64x64 buildings + ground (2,015,232 tris), 8 bands, 256 sources, "
               "1M rays x 200 reflections, IR 3 s @ 1 kHz, SH order 3")
+# the paper's operating point (Sec. 5 and 6): 50 primaries x 200 reflections with the unused
+# segment budget refilled (10,000 segments per frame), 4 bands, IR at 100 Hz, SH order 1,
+# reflections below order 3 left to the early-reflection path; city-like scene, 13 sources
+PAPER = dict(num_rays=50, max_order=200, sh_order=1, num_bins=300, min_order=3, ir_rate_hz=100.0,
+             speed_of_sound=343.0, source_radius=0.5, budget_refill=1)
+PAPER_NAME = ("paper operating point: procedural city, 64x64 buildings + ground (1,032,192 tris), 4 bands, "
+              "13 sources, 50 rays x 200 reflections with budget refill, IR 3 s @ 100 Hz, SH order 1, min order 3")
 SCENE = "furnished_hall"
 WORKLOAD_NAME = ("medium: furnished hall 40x30x12 m + 2000 boxes (24,012 tris), 8 bands, 16 sources, "
                  "200k rays x 64 reflections, IR 2 s @ 1 kHz, SH order 2")
@@ -151,7 +158,8 @@ def cpu_sample(rays: int, threads: int):
     osc = oracle.OracleScene.from_scene(sc)
     p = oracle.TraceParams(num_rays=rays, max_order=WORKLOAD["max_order"], sh_order=WORKLOAD["sh_order"],
                            num_bins=WORKLOAD["num_bins"], min_order=WORKLOAD["min_order"],
-                           ir_rate_hz=WORKLOAD["ir_rate_hz"], seed=0x5EED)
+                           ir_rate_hz=WORKLOAD["ir_rate_hz"], seed=0x5EED,
+                           budget_refill=WORKLOAD.get("budget_refill", 0))
     t0 = time.perf_counter()
     H, st, _ = oracle.trace_parallel(osc, p, sc.listener, sc.sources, threads=threads)
     dd = oracle.direct(osc, p, sc.listener, sc.sources)
@@ -162,7 +170,7 @@ def cpu_sample(rays: int, threads: int):
 
 def cpu_baseline(target_s: float = 15.0):
     threads = os.cpu_count() or 1
-    probe_rays = 400
+    probe_rays = min(400, WORKLOAD["num_rays"])
     dt, work = cpu_sample(probe_rays, threads)
     rays = probe_rays
     # the probe's fixed costs (thread start-up, the estimator) overstate the time per
@@ -183,7 +191,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     threads = os.cpu_count() or 1
-    rays = 1500
+    rays = min(1500, WORKLOAD["num_rays"])
     for _ in range(args.warmup):
         cpu_sample(rays, threads)
     total_t, total_w = 0.0, 0.0
@@ -216,14 +224,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--rays", type=int, default=0, help="primaries per update (default: the workload's 200k; "
                     "smaller values make a small case for profilers)")
-    ap.add_argument("--workload", default="medium", choices=["medium", "large"],
-                    help="medium: the furnished hall (default); large: the procedural city")
+    ap.add_argument("--workload", default="medium", choices=["medium", "large", "paper"],
+                    help="medium: the furnished hall (default); large: the procedural city; paper: the "
+                         "paper's operating point on a city-like scene")
     args = ap.parse_args()
     global SCENE, WORKLOAD_NAME
     if args.workload == "large":
         WORKLOAD.clear()
         WORKLOAD.update(LARGE)
         WORKLOAD_NAME, SCENE = LARGE_NAME, "city"
+    elif args.workload == "paper":
+        WORKLOAD.clear()
+        WORKLOAD.update(PAPER)
+        WORKLOAD_NAME, SCENE = PAPER_NAME, "paper_city"
     if args.rays:
         WORKLOAD["num_rays"] = args.rays
     if args.impl == "reference":
@@ -355,9 +368,9 @@ def main():
     peak_tops = 152 * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     achieved = ops / avg_s / 1e12
     fma_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    dram = NCU_SHADOW_DRAM[args.workload]
+    dram = NCU_SHADOW_DRAM.get(args.workload)
     traffic = (dram[0] * st["shadow_rays"] / dram[1]
-               if name == "shadow" and not args.fp32_paths and args.shadow_mode != "lanes" else None)
+               if dram and name == "shadow" and not args.fp32_paths and args.shadow_mode != "lanes" else None)
     shares = {k: round(v[1] / sum(x[1] for x in kt.values()), 4) for k, v in kt.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -37,6 +37,8 @@ struct Hook {
     }
 };
 
+constexpr int REFILL_BATCH = 16;  // refill waves enqueued between host checks
+
 #define CKS(x)                                    \
     do {                                          \
         const cudaError_t e_ = (x);               \
@@ -61,17 +63,23 @@ cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, vo
         launch_paths(w, L.paths_blocks, st);
     }
     if (L.refill && w.k.M > 0 && w.njobs == 1) {
-        for (int wave = 1; wave < 4096; ++wave) {
-            {
-                Hook h(hook, hook_ctx, "setup");
-                launch_setup(w, wave, st);
+        // Refill waves go out REFILL_BATCH at a time with no host synchronisation in
+        // between: a wave whose budget is spent has no rays, its setup leaves the state
+        // as it is and its paths launch returns at once.  The host reads the last wave's
+        // size after each batch and stops once it is zero.
+        for (int wave = 1; wave < 4096; wave += REFILL_BATCH) {
+            for (int k = 0; k < REFILL_BATCH; ++k) {
+                {
+                    Hook h(hook, hook_ctx, "setup");
+                    launch_setup(w, wave + k, st);
+                }
+                Hook h(hook, hook_ctx, "paths");
+                launch_paths(w, L.paths_blocks, st);
             }
             unsigned long long cnt = 0;
             CKS(cudaMemcpyAsync(&cnt, &w.js[0].wave_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
             CKS(cudaStreamSynchronize(st));
             if (cnt == 0) break;
-            Hook h(hook, hook_ctx, "paths");
-            launch_paths(w, L.paths_blocks, st);
         }
     }
     {

@@ -351,6 +351,13 @@ def city(seed: int = SEED_LARGE, grid: int = 64, tess: int = 7, ground_tess: int
                  room_hi=np.array([extent, extent, 60.0]))
 
 
+def paper_city(seed: int = SEED_LARGE + 2) -> Scene:
+    """The paper's operating point on a city-like scene: the procedural city with 5 x 5
+    quads per face (1,032,192 triangles, against the paper's City of 1,001,860), 4 bands
+    and 13 sources."""
+    return city(seed=seed, tess=5, bands=4, num_sources=13)
+
+
 def city_listeners(sc: Scene, n: int, seed: int = SEED_LARGE + 1) -> np.ndarray:
     """n listener positions for the city: its own listener, then seeded free points
     (1-20 m above the ground, at least 1 m from buildings, sources and each other)."""
