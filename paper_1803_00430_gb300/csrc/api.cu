@@ -306,7 +306,7 @@ int rp_destroy(rp_ctx *c)
                    &c->rec_e, &c->perm, &c->rerun,
                    &c->cnt, &c->off, &c->cur, &c->scan_part, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H,
                    &c->direct,
-                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job})
+                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->plan_seg})
         free_buf(*b);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
@@ -525,6 +525,13 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
     w.direct = direct;
     w.shadow_steps = c->shadow_steps;
     w.shadow_packets = shadow_packets_for(p->flags);
+    w.plan = 0;
+    w.plan_seg = nullptr;
+    const unsigned long long budget = p->num_rays * (unsigned long long)std::max(p->max_order, 0);
+    if (p->budget_refill && budget > 0 && budget <= PLAN_MAX_RAYS) {
+        if ((rc = ensure(c, c->plan_seg, budget * sizeof(uint32_t)))) return rc;
+        w.plan_seg = (uint32_t *)c->plan_seg.p;
+    }
 
     StepLaunch L;
     L.w = w;

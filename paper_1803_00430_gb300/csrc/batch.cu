@@ -205,6 +205,8 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
                 hit_order_bits(w.njobs), (int)hit_order_cells(w.njobs)};
     w.js = (JobState *)c->js.p;
     w.wave_mode = 0;
+    w.plan = 0;
+    w.plan_seg = nullptr;
     w.chunks = b->d_chunks + g.chunk_begin;
     w.nchunks = g.nchunks;
     w.chunk_rays = b->tuning.chunk_rays;

@@ -10,6 +10,10 @@
 
 namespace rp {
 
+// Refill budgets N M up to this many segments are planned (one u32 per candidate ray);
+// larger ones run as host-checked waves.
+constexpr unsigned long long PLAN_MAX_RAYS = 1ull << 28;
+
 // Records kept in device memory at once (one chunk of next-event work plus the
 // records of source-sphere hits): 2^30, 44 bytes each at 8 bands with the sort index
 // (47 GB at most; a problem takes only what its worst case needs).  Record chunks
@@ -46,7 +50,7 @@ struct rp_ctx {
     //   counters, statistics, the host-buffer update's outputs, job tables
     Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, shit_p, shit_n, shit_ws, shit_rid, hord_cell, hord_perm, hord_cnt,
         rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, scan_part, Hs, He, src, ctr, stats, H, direct, params,
-        state, jobs, js, chunks, src_job;
+        state, jobs, js, chunks, src_job, plan_seg;
     // profiling
     bool prof = false;
     std::vector<ProfPair> pending;

@@ -84,7 +84,9 @@ struct TraceCounters {
     unsigned long long n_rerun;      // shadow items queued for an FP64 decision (current chunk)
     unsigned long long total_items; // shadow items of the step (sum over jobs of shadow_items(hits, S))
     unsigned long long total_hits;  // stored reflections of the step (sum over jobs)
-    unsigned long long pad[2];
+    // planned refill: candidate rays still needed (0 = planned), primaries and waves
+    unsigned long long plan_need, plan_rays, plan_waves;
+    unsigned long long pad[3];
 };
 
 // Contribution records: key = (global source - first source of the group) * T + bin,
@@ -187,6 +189,8 @@ struct TraceWork {
     int njobs;
     JobState *js;          // [njobs], device
     int wave_mode;         // 1: one job, rays js[0].wave_begin + v (waves / refill)
+    int plan;              // 1: the paths kernel only counts each path's segments (planned refill)
+    uint32_t *plan_seg;    // [N M] segments of candidate ray first_ray + i, or null (refill in waves)
     const RayChunk *chunks;  // [nchunks] in LPT order (wave_mode == 0)
     int nchunks;
     int chunk_rays;
@@ -220,6 +224,9 @@ struct TraceWork {
 };
 
 void launch_setup(const TraceWork &w, int wave, cudaStream_t st);
+void launch_plan_block(const TraceWork &w, unsigned long long begin, unsigned long long count, cudaStream_t st);
+void launch_refill_plan(const TraceWork &w, unsigned long long candidates, cudaStream_t st);
+void launch_plan_apply(const TraceWork &w, cudaStream_t st);
 void launch_paths(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_item_prefix(const TraceWork &w, cudaStream_t st);
 void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st);

@@ -170,6 +170,8 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.njobs = 1;
     w.js = (JobState *)(base + o_js);
     w.wave_mode = 1;
+    w.plan = 0;
+    w.plan_seg = nullptr;  // refill runs as waves here: the scratch holds no plan
     w.chunks = nullptr;
     w.nchunks = 0;
     w.chunk_rays = 1;

@@ -1,7 +1,7 @@
 // step.cu -- the launch sequence of one trace step (one group of jobs), shared by
 // rp_trace, rp_trace_noalloc and the batched entry points.
 //
-//   setup -> paths (-> refill waves) -> shadow-item prefix -> direct sound ->
+//   setup -> (planned refill ->) paths (-> refill waves) -> shadow-item prefix -> direct sound ->
 //   per record chunk: shadow rays -> FP64 re-decisions -> count -> scan -> scatter
 //   -> compensated accumulation
 //   -> finalize (normalise by primaries, bin direct sound) -> status copy
@@ -45,6 +45,36 @@ constexpr int REFILL_BATCH = 16;  // refill waves enqueued between host checks
         if (e_ != cudaSuccess) return e_;         \
     } while (0)
 
+// Planned refill: counting passes over candidate ray ids (4 N or 4096 at first, then
+// twice as many while the waves reach past them), then the waves' sizes.  The host
+// reads whether more candidates are needed after each pass.
+cudaError_t plan_refill(const TraceWork &w, int blocks, cudaStream_t st, ProfHook hook, void *hook_ctx)
+{
+    const unsigned long long N = w.job0.num_rays, budget = N * (unsigned long long)w.k.M;
+    TraceWork wp = w;
+    wp.plan = 1;
+    wp.ray_hash = nullptr;
+    wp.k.flags &= ~RP_FLAG_COUNT_VISITS;
+    unsigned long long done = 0, cand = std::min(budget, std::max(4ull * N, 4096ull));
+    for (int pass = 0; pass < 64; ++pass) {
+        {
+            Hook h(hook, hook_ctx, "paths");
+            launch_plan_block(w, done, cand - done, st);
+            launch_paths(wp, blocks, st);
+        }
+        done = cand;
+        launch_refill_plan(w, done, st);
+        unsigned long long need = 0;
+        CKS(cudaMemcpyAsync(&need, &w.ctr->plan_need, sizeof(need), cudaMemcpyDeviceToHost, st));
+        CKS(cudaStreamSynchronize(st));
+        if (need == 0) break;
+        cand = std::min(budget, std::max(2 * cand, need));
+        if (cand <= done) return cudaErrorUnknown;  // cannot happen: the waves hold at most N M rays
+    }
+    launch_plan_apply(w, st);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, void *hook_ctx)
@@ -58,11 +88,13 @@ cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, vo
         Hook h(hook, hook_ctx, "setup");
         launch_setup(w, 0, st);
     }
+    const bool planned = L.refill && w.k.M > 0 && w.njobs == 1 && w.plan_seg;
+    if (planned) CKS(plan_refill(w, L.paths_blocks, st, hook, hook_ctx));
     if (w.k.M > 0) {
         Hook h(hook, hook_ctx, "paths");
         launch_paths(w, L.paths_blocks, st);
     }
-    if (L.refill && w.k.M > 0 && w.njobs == 1) {
+    if (L.refill && w.k.M > 0 && w.njobs == 1 && !planned) {
         // Refill waves go out REFILL_BATCH at a time with no host synchronisation in
         // between: a wave whose budget is spent has no rays, its setup leaves the state
         // as it is and its paths launch returns at once.  The host reads the last wave's

@@ -178,6 +178,68 @@ __global__ void k_setup(TraceWork w, int wave)
     }
 }
 
+// Planned refill (one job).  The waves of the segment-budget refill are sized by the
+// segments of the rays before them, so traced as waves they run one after another.
+// Instead a counting pass of the paths kernel traces candidate ray ids and records each
+// path's segments; k_refill_plan then finds the waves' sizes, and one wave of all their
+// rays is traced.  The rays, paths and results are those of the waves.
+
+// candidate rays first_ray + begin .. first_ray + begin + count for the counting pass
+__global__ void k_plan_block(TraceWork w, unsigned long long begin, unsigned long long count)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    w.js[0].wave_begin = w.jobs[0].first_ray + begin;
+    w.js[0].wave_count = count;
+    w.ctr->next_ray = 0;
+}
+
+// The waves from the candidates' segment counts: wave 1 is the N primaries; each later
+// wave takes floor(unused / M) further ray ids, unused being the budget N M less the
+// segments of all rays so far (as k_setup's later waves).  One warp sums each wave.
+// plan_need > 0: the waves reach past the candidates traced so far.
+__global__ void k_refill_plan(TraceWork w, unsigned long long cand)
+{
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const unsigned long long N = w.jobs[0].num_rays, M = (unsigned long long)w.k.M, budget = N * M;
+    unsigned long long r = 0, used = 0, waves = 0, count = N, need = 0;
+    while (count > 0) {  // r grows by count >= 1 each time and stays <= cand
+        if (r + count > cand) {
+            need = r + count;
+            break;
+        }
+        unsigned long long seg = 0;
+        for (unsigned long long i = r + lane; i < r + count; i += 32) seg += w.plan_seg[i];
+        for (int o = 16; o > 0; o >>= 1) seg += __shfl_xor_sync(FULL, seg, o);
+        used += seg;
+        r += count;
+        ++waves;
+        const unsigned long long unused = budget > used ? budget - used : 0ull;
+        count = (M > 0 && unused >= M) ? unused / M : 0ull;
+    }
+    if (lane == 0) {
+        w.ctr->plan_need = need;
+        w.ctr->plan_rays = r;
+        w.ctr->plan_waves = waves;
+    }
+}
+
+// the planned waves as one: every ray of them, with the waves' primaries and count
+__global__ void k_plan_apply(TraceWork w)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    JobState &s = w.js[0];
+    const SceneJob &J = w.jobs[0];
+    const unsigned long long K = w.ctr->plan_rays;
+    s.wave_begin = J.first_ray;
+    s.wave_count = K;
+    s.primaries = K;
+    s.segments = 0;
+    w.stats->primaries += K - J.num_rays;
+    w.stats->waves = w.ctr->plan_waves;
+    w.ctr->next_ray = 0;
+}
+
 // first shadow item of every job (sum over earlier jobs of stored reflections x
 // sources) and first reflection in the flattened order of the step
 __global__ void k_item_prefix(TraceWork w)
@@ -395,6 +457,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
     const unsigned long long wave_count = BATCH ? 0ull : w.js[0].wave_count;
     const unsigned long long vtotal = BATCH ? (unsigned long long)w.nchunks * w.chunk_rays : wave_count;
     const float inv_pi_rs2 = 1.0f / (PI_F * k.rs * k.rs);
+    const bool plan = !BATCH && w.plan;  // count each path's segments only (planned refill)
 
     double mfp_np = 0.0;
     unsigned long long mcnp = 0, sphere = 0, contrib = 0, reruns = 0, segs_all = 0, mc_all = 0;
@@ -490,7 +553,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                                                 w.status);
         }
         ++segs_all;
-        if (spec_prev && h - 1 >= k.min_order) {
+        if (!plan && spec_prev && h - 1 >= k.min_order) {
             // the job's sources as spheres of radius r_s, seen through the specular bounce
             for (int s = 0; s < J.S; ++s) {
                 const int gs = J.src_off + s;
@@ -570,7 +633,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     wgt[b * PATH_THREADS] *= (1.0f - a);
                 }
             }
-            if (h >= k.min_order && J.S > 0) {
+            if (!plan && h >= k.min_order && J.S > 0) {
                 const unsigned long long jl =
                     BATCH ? warp_append_job(&w.js[job].n_hits, job) : warp_append(&w.js[0].n_hits);
                 if (jl < J.hit_cap) {
@@ -634,9 +697,11 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                 if (b < B) atomicAdd(&acc.absb[b], (double)absorbed[b * PATH_THREADS]);
             if (HASH && w.ray_hash && rid >= J.first_ray && rid - J.first_ray < J.num_rays)
                 w.ray_hash[rid - J.first_ray] = hash;
+            if (plan) w.plan_seg[rid - J.first_ray] = (uint32_t)h;  // the path's segments
             have = false;
         }
     }
+    if (plan) return;  // the counting pass leaves the statistics to the real one
     if (!BATCH) wave_segments_flush(w, segs_all);
     acc_counters(acc, mfp_all, mfp_np, mc_all, mcnp, segs_all, 0ull, contrib, sphere, ts);
     for (int o = 16; o > 0; o >>= 1) reruns += __shfl_xor_sync(FULL, reruns, o);
@@ -1104,6 +1169,18 @@ void launch_setup(const TraceWork &w, int wave, cudaStream_t st)
 }
 
 void launch_item_prefix(const TraceWork &w, cudaStream_t st) { k_item_prefix<<<1, 32, 0, st>>>(w); }
+
+void launch_plan_block(const TraceWork &w, unsigned long long begin, unsigned long long count, cudaStream_t st)
+{
+    k_plan_block<<<1, 32, 0, st>>>(w, begin, count);
+}
+
+void launch_refill_plan(const TraceWork &w, unsigned long long candidates, cudaStream_t st)
+{
+    k_refill_plan<<<1, 32, 0, st>>>(w, candidates);
+}
+
+void launch_plan_apply(const TraceWork &w, cudaStream_t st) { k_plan_apply<<<1, 32, 0, st>>>(w); }
 
 void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st)
 {
