@@ -139,7 +139,12 @@ typedef struct {
     float source_radius;      /* r_s, m, > 0 */
     uint32_t scene_id;        /* Philox counter word 1 */
     int32_t budget_refill;    /* 1: spend the unused part of the N*M segment budget on
-                                 extra primaries, in deterministic waves (Section 5) */
+                                 extra primaries, in deterministic waves (Section 5).
+                                 rp_trace synchronises the stream while it sizes the
+                                 waves (N*M <= 2^28: a counting pass over candidate
+                                 rays, then all waves as one; larger budgets: waves
+                                 checked every 16), so such a call cannot be captured
+                                 into a CUDA graph */
     int32_t flags;            /* RP_FLAG_* */
 } rp_trace_params;
 
