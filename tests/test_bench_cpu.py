@@ -33,3 +33,12 @@ def test_cpu_baseline_scales_the_sample_to_the_target():
     wall = float(out["sample"].rsplit(", ", 1)[1].split(" ")[0])
     # grown past the 400-ray probe until the sample takes about the target (or the workload)
     assert rays > 400 and (wall >= 1.0 or rays == bench.WORKLOAD["num_rays"])
+
+
+def test_reference_arm_at_the_papers_operating_point():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "paper", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["config"]["workload"].startswith("paper operating point") and d["config"]["sample_rays_per_step"] == 50
