@@ -8,6 +8,9 @@
 //   k_setup       sets each job's first wave; with budget refill (one job) later
 //                 waves spend the unused part of the N*M segment budget on
 //                 floor(unused / M) extra primaries (Section 5).
+//   k_plan_block, k_refill_plan, k_plan_apply
+//                 planned refill: a counting pass of k_paths over candidate rays,
+//                 the waves' sizes from their segment counts, then all waves as one.
 //   k_paths       persistent: each warp takes 32 primaries at a time from a global
 //                 counter; each thread follows its path bounce by bounce: closest
 //                 hit, absorption, storage of the reflection for next-event
@@ -17,14 +20,15 @@
 //                 After a specular choice the next segment also tests the sources
 //                 as spheres (the specular image of the source).
 //   k_hit_cells, k_hit_scatter, k_hit_gather
-//                 order the stored reflections by spatial cell and copy them in
-//                 that order, so that neighbouring shadow items start close
-//                 together.
+//                 order the stored reflections by spatial cell (near-cubic cells,
+//                 up to 2^22 per scene) and copy them in that order, so that
+//                 neighbouring shadow items start close together.
 //   k_shadow_packet / k_shadow
 //                 persistent over (reflection, source) pairs in tiles of 32
 //                 reflections x sources: the diffuse-rain shadow ray of each stored
 //                 reflection to each source, as warp packets (32 rays walk the BVH
-//                 together) or one ray per lane; a visible source emits a
+//                 together, the child towards the source first) or one ray per
+//                 lane; a visible source emits a
 //                 contribution record w_b s_b cos / (pi d^2) at arrival time
 //                 (L + d) / c.  Rounding-sensitive visibilities go to
 //                 k_shadow_exact (FP64).
