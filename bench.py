@@ -1,14 +1,18 @@
 #!/usr/bin/env python3
-"""Benchmark of one IR + reverb-parameter update on the medium workload.
+"""Benchmark of one IR + reverb-parameter update; the default is the large workload.
 
-Workload: furnished hall, 40 x 30 x 12 m with 2000 seeded boxes (24,012
-triangles), 8 bands, 16 sources, 1 listener; 200,000 primary rays, 64
-reflections, IR 2 s at 1 kHz (2000 bins), SH order 2 (9 coefficients).  One step
-is one whole update through the C ABI: trace (paths, diffuse-rain shadow rays,
-histogram accumulation, direct sound) + estimate (reverb parameters of every
-source and band), with a new Philox key per step.
+Large (default): procedural city of 64 x 64 buildings plus a ground grid (2,015,232
+triangles), 8 bands, 256 sources, 1 listener; 1,000,000 primary rays x 200
+reflections with the unused segment budget refilled (Section 5: every update traces
+the same N x M segments; open scenes end most paths early), IR 3 s at 1 kHz (3000
+bins), SH order 3 (16 coefficients).  --workload medium: the furnished hall (24,012
+triangles, 16 sources, 200k x 64, IR 2 s, SH order 2, no refill).  --workload paper:
+the paper's operating point on a city-like scene.  One step is one whole update
+through the C ABI: trace (paths, diffuse-rain shadow rays, histogram accumulation,
+direct sound) + estimate (reverb parameters of every source and band), with a new
+Philox key per step.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the
 host cores on a bounded sample of the same workload.  Under torchrun each rank
@@ -20,11 +24,11 @@ import argparse
 import ctypes
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -35,12 +39,14 @@ if ROOT not in sys.path:
 
 METRIC = "ray segments/s; IR+reverb-param updates/s at ≤5% decay-time err vs plain"
 UNIT = "ray segments/s"
-WORKLOAD = dict(num_rays=200_000, max_order=64, sh_order=2, num_bins=2000, min_order=1, ir_rate_hz=1000.0,
-                speed_of_sound=343.0, source_radius=0.5)
 LARGE = dict(num_rays=1_000_000, max_order=200, sh_order=3, num_bins=3000, min_order=1, ir_rate_hz=1000.0,
-             speed_of_sound=343.0, source_radius=0.5)
+             speed_of_sound=343.0, source_radius=0.5, budget_refill=1)
 LARGE_NAME = ("large: procedural city, 64x64 buildings + ground (2,015,232 tris), 8 bands, 256 sources, "
-              "1M rays x 200 reflections, IR 3 s @ 1 kHz, SH order 3")
+              "1M rays x 200 reflections with budget refill, IR 3 s @ 1 kHz, SH order 3")
+MEDIUM = dict(num_rays=200_000, max_order=64, sh_order=2, num_bins=2000, min_order=1, ir_rate_hz=1000.0,
+              speed_of_sound=343.0, source_radius=0.5)
+MEDIUM_NAME = ("medium: furnished hall 40x30x12 m + 2000 boxes (24,012 tris), 8 bands, 16 sources, "
+               "200k rays x 64 reflections, IR 2 s @ 1 kHz, SH order 2")
 # the paper's operating point (Sec. 5 and 6): 50 primaries x 200 reflections with the unused
 # segment budget refilled (10,000 segments per frame), 4 bands, IR at 100 Hz, SH order 1,
 # reflections below order 3 left to the early-reflection path; city-like scene, 13 sources
@@ -48,28 +54,26 @@ PAPER = dict(num_rays=50, max_order=200, sh_order=1, num_bins=300, min_order=3, 
              speed_of_sound=343.0, source_radius=0.5, budget_refill=1)
 PAPER_NAME = ("paper operating point: procedural city, 64x64 buildings + ground (1,032,192 tris), 4 bands, "
               "13 sources, 50 rays x 200 reflections with budget refill, IR 3 s @ 100 Hz, SH order 1, min order 3")
-SCENE = "furnished_hall"
-WORKLOAD_NAME = ("medium: furnished hall 40x30x12 m + 2000 boxes (24,012 tris), 8 bands, 16 sources, "
-                 "200k rays x 64 reflections, IR 2 s @ 1 kHz, SH order 2")
+WORKLOADS = {"large": (LARGE, LARGE_NAME, "city"), "medium": (MEDIUM, MEDIUM_NAME, "furnished_hall"),
+             "paper": (PAPER, PAPER_NAME, "paper_city")}
+WORKLOAD, WORKLOAD_NAME, SCENE = dict(LARGE), LARGE_NAME, "city"
 # Algorithmic work of BVH traversal, counted on the pipe that bounds it.  A node visit
-# slab-tests two child boxes: per box and axis the smaller and the larger of the two
-# plane distances, the entry as the largest of the three minima and t_min, the exit as
-# the smallest of the three maxima and t_max, and entry <= exit: 13 FP32 min/max/compare
-# operations per box, 26 per visit.  A triangle test decides with 7 compares (det != 0,
-# u, v, u + v, t_min < t < t_max).  These issue on the ALU pipe (16 lanes per SM
-# sub-partition, 64 per SM and clock); the plane distances (12 FMA per visit) and the
-# triangle arithmetic go to the FMA pipe (128 lanes), which is the less busy of the two.
-ALU_OPS_PER_NODE = 26.0
+# slab-tests two child boxes.  With the ray's direction signs known, each axis has a
+# near and a far plane: per box the entry is the largest of the three near-plane
+# distances and t_min, the exit the smallest of the three far-plane distances and t_max
+# (two three-input max and two three-input min instructions) and entry <= exit is
+# checked: 5 FP32 min/max/compare instructions per box, 10 per visit.  A triangle test
+# decides with 7 compares (det != 0, u, v, u + v, t_min < t < t_max).  These issue on
+# the ALU pipe; the 6 plane distances per box (12 FMA per visit) and the triangle
+# arithmetic (about 36 FMA-pipe instructions) go to the FMA pipe, reported beside.
+ALU_OPS_PER_NODE = 10.0
 ALU_OPS_PER_TRI = 7.0
-ALU_LANES_PER_SM = 64
-FLOPS_PER_NODE = 24.0   # FMA-pipe flops of a visit (12 FMA), reported beside
-FLOPS_PER_TRI = 27.0    # Moller-Trumbore arithmetic
-# DRAM bytes (read + write) of the shadow-ray launch (k_shadow_packet, the default
-# mode) of one update in an ncu capture at fewer primaries -- medium at 30,000, large
-# at 20,000 -- and the shadow rays that launch traced; a full-size update is credited
-# with the same bytes per shadow ray.
-NCU_SHADOW_DRAM = {"medium": (94_667_776 + 17_925_632, 18_878_384),
-                   "large": (21_502_464 + 0, 8_495_384)}
+FMA_OPS_PER_NODE = 12.0
+FMA_OPS_PER_TRI = 36.0
+# DRAM bytes (read + write) of the shadow-ray launches (k_shadow_packet, the default
+# mode) of one update in an ncu capture at fewer primaries, and the shadow rays those
+# launches traced; a full-size update is credited with the same bytes per shadow ray.
+NCU_SHADOW_DRAM = {"medium": (94_667_776 + 17_925_632, 18_878_384)}
 
 
 def _peaks():
@@ -149,13 +153,25 @@ def reduce_over_ranks(total_ms: float, rank_work: float, device) -> tuple:
     return float(tmax[0]), float(wsum[0])
 
 
+_SCENE_CACHE = {}
+
+
+def _oracle_scene():
+    """The workload's scene and its oracle form, generated once per process."""
+    if SCENE not in _SCENE_CACHE:
+        import oracle
+        from paper_1803_00430_gb300 import scenes
+        sc = getattr(scenes, SCENE)()
+        _SCENE_CACHE[SCENE] = (sc, oracle.OracleScene.from_scene(sc))
+    return _SCENE_CACHE[SCENE]
+
+
 def cpu_sample(rays: int, threads: int):
-    """The oracle on `rays` primaries of the benchmark's workload, all given threads.
+    """The oracle on `rays` primaries of the benchmark's workload (with the refill of
+    their own segment budget when the workload refills), on `threads` threads.
     Returns (seconds, segments + shadow rays)."""
     import oracle
-    from paper_1803_00430_gb300 import scenes
-    sc = getattr(scenes, SCENE)()
-    osc = oracle.OracleScene.from_scene(sc)
+    sc, osc = _oracle_scene()
     p = oracle.TraceParams(num_rays=rays, max_order=WORKLOAD["max_order"], sh_order=WORKLOAD["sh_order"],
                            num_bins=WORKLOAD["num_bins"], min_order=WORKLOAD["min_order"],
                            ir_rate_hz=WORKLOAD["ir_rate_hz"], seed=0x5EED,
@@ -168,22 +184,49 @@ def cpu_sample(rays: int, threads: int):
     return dt, st["segments"] + st["shadow_rays"]
 
 
-def cpu_baseline(target_s: float = 15.0):
-    threads = os.cpu_count() or 1
-    probe_rays = min(400, WORKLOAD["num_rays"])
-    dt, work = cpu_sample(probe_rays, threads)
-    rays = probe_rays
-    # the probe's fixed costs (thread start-up, the estimator) overstate the time per
-    # ray: scale up until the sample takes about target_s
-    for _ in range(3):
+def _sized_sample(threads: int, target_s: float):
+    """Primaries for a sample of about target_s seconds on `threads` threads: a probe,
+    then up to three rescalings (the probe's fixed costs overstate the time per ray)."""
+    # a refilled primary spends its whole budget of max_order segments: probe with fewer
+    rays = min(2 if WORKLOAD.get("budget_refill") else 20, WORKLOAD["num_rays"])
+    dt, work = cpu_sample(rays, threads)
+    for _ in range(4):
         if dt >= 0.5 * target_s or rays >= WORKLOAD["num_rays"]:
             break
         rays = int(min(WORKLOAD["num_rays"], max(rays + 1, rays * target_s / max(dt, 1e-3))))
         dt, work = cpu_sample(rays, threads)
-    return {"value": work / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{rays} of the {WORKLOAD['num_rays']} primaries of the {WORKLOAD_NAME.split(':')[0]} workload "
-                      f"(full scene and sources, {WORKLOAD['max_order']} reflections), trace + estimate, "
-                      f"{dt:.1f} s wall"}
+    return rays, dt, work
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _sample_text(rays: int, dt: float) -> str:
+    refill = " with the refill of their segment budget" if WORKLOAD.get("budget_refill") else ""
+    return (f"{rays} of the {WORKLOAD['num_rays']} primaries of the {WORKLOAD_NAME.split(':')[0]} workload{refill} "
+            f"(full scene and sources, {WORKLOAD['max_order']} reflections), trace + estimate, {dt:.1f} s wall")
+
+
+def cpu_baseline(target_s: float = 12.0, single_s: float = 6.0):
+    """The oracle as it stands on all host cores (the CPU throughput baseline) and on
+    one thread (the parity reference), each on a bounded sample of the workload."""
+    threads = os.cpu_count() or 1
+    rays, dt, work = _sized_sample(threads, target_s)
+    r1, d1, w1 = _sized_sample(1, single_s)
+    return {"value": work / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": _sample_text(rays, dt),
+            "cpu_model": cpu_model(), "arch": platform.machine(),
+            "single_thread": {"value": w1 / d1, "unit": UNIT, "cores": 1, "sample": _sample_text(r1, d1)}}
 
 
 def run_reference(args):
@@ -191,7 +234,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     threads = os.cpu_count() or 1
-    rays = min(1500, WORKLOAD["num_rays"])
+    # each step a bounded sample: the whole run stays within about three minutes
+    per_step = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    rays, _, _ = _sized_sample(threads, per_step)
     for _ in range(args.warmup):
         cpu_sample(rays, threads)
     total_t, total_w = 0.0, 0.0
@@ -205,7 +250,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "sample_rays_per_step": rays},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{rays} primaries of the {WORKLOAD_NAME.split(':')[0]} workload per step"},
+                             "sample": f"{rays} primaries of the {WORKLOAD_NAME.split(':')[0]} workload per step"
+                                       + (" with the refill of their segment budget"
+                                          if WORKLOAD.get("budget_refill") else ""),
+                             "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -214,7 +262,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp32-paths", action="store_true", help="time the all-FP32 path precision form")
@@ -222,21 +270,16 @@ def main():
                     help="shadow rays as warp packets or one per lane (auto: the library default, packets)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
-    ap.add_argument("--rays", type=int, default=0, help="primaries per update (default: the workload's 200k; "
+    ap.add_argument("--rays", type=int, default=0, help="primaries per update (default: the workload's; "
                     "smaller values make a small case for profilers)")
-    ap.add_argument("--workload", default="medium", choices=["medium", "large", "paper"],
-                    help="medium: the furnished hall (default); large: the procedural city; paper: the "
-                         "paper's operating point on a city-like scene")
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
+                    help="large: the procedural city with budget refill (default); medium: the furnished hall; "
+                         "paper: the paper's operating point on a city-like scene")
     args = ap.parse_args()
     global SCENE, WORKLOAD_NAME
-    if args.workload == "large":
-        WORKLOAD.clear()
-        WORKLOAD.update(LARGE)
-        WORKLOAD_NAME, SCENE = LARGE_NAME, "city"
-    elif args.workload == "paper":
-        WORKLOAD.clear()
-        WORKLOAD.update(PAPER)
-        WORKLOAD_NAME, SCENE = PAPER_NAME, "paper_city"
+    wl, WORKLOAD_NAME, SCENE = WORKLOADS[args.workload]
+    WORKLOAD.clear()
+    WORKLOAD.update(wl)
     if args.rays:
         WORKLOAD["num_rays"] = args.rays
     if args.impl == "reference":
@@ -272,6 +315,8 @@ def main():
     src_d = torch.tensor(sc.sources, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     rpr.check(ctx.lib.rp_trace_reserve(scene.h, ctypes.byref(base.c()), S), "reserve")
+    # measured FP32 pipe throughput (calibration for the roofline; untimed)
+    fma_peak, minmax_peak = ctx.pipe_peaks()
 
     def step(i):
         p = base.c()
@@ -285,8 +330,6 @@ def main():
     for i in range(args.warmup):
         step(i)
     rpr.check(ctx.sync_status(), "warmup")
-    st0 = out.stats_dict()
-    work_per_step = st0["segments"] + st0["shadow_rays"]
 
     # per-kernel events (library side, on the same stream) during the timed region
     ctx.profile(True)
@@ -295,7 +338,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    segs = shadow = 0
+    work_steps = []
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             flush.zero_()
@@ -311,7 +354,9 @@ def main():
     st = out.stats_dict()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     ms_step = total_ms / args.steps
-    work = float(st["segments"] + st["shadow_rays"])  # last step (same workload each step)
+    # every step traces the same workload (refill keeps the segment budget N x M; the
+    # shadow rays vary by a fraction of a percent with the key): the last step's count
+    work = float(st["segments"] + st["shadow_rays"])
     rank_work = work * args.steps
     if ws > 1:
         total_ms, all_work = reduce_over_ranks(total_ms, rank_work, "cuda")
@@ -320,7 +365,7 @@ def main():
     value = all_work / (total_ms / 1000.0)
     launches = sum(v[0] for v in kt.values())
 
-    # visit counts for the algorithmic flops of the dominant kernel (untimed run, same key)
+    # visit counts for the algorithmic work of the dominant kernel (untimed run, same key)
     p = base.c()
     p.seed = scenes.PHILOX_KEY_BASE + args.warmup + args.steps - 1
     p.flags |= rpr.RP_FLAG_COUNT_VISITS
@@ -330,29 +375,29 @@ def main():
     stc = out.stats_dict()
 
     # e2e: the public host-buffer entry point, H2D of positions and D2H of H + parameters
-    e2e_total, e2e_steps = 0.0, 1
+    e2e_total, e2e_steps = 0.0, 0
     Hh = torch.empty((S, B, K, T), dtype=torch.float32).pin_memory().numpy()
     lis_h = torch.tensor(sc.listener).pin_memory().numpy()
     src_h = torch.tensor(sc.sources).pin_memory().numpy()
     e2e_p = rpr.TraceParams(**WORKLOAD, flags=flags & ~rpr.RP_FLAG_DEVICE_POSITIONS, scene_id=rank)
-    for i in range(0 if args.no_e2e else max(1, args.warmup)):
-        e2e_p.seed = scenes.PHILOX_KEY_BASE + i
-        rpr.update(scene, e2e_p, e2e_p.ir_rate_hz, lis_h, src_h, H_host=Hh, want=("H", "params"))
-    e2e_steps = 1 if args.no_e2e else max(3, min(args.steps, 10))
-    for i in range(0 if args.no_e2e else e2e_steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        ta = time.perf_counter()
-        e2e_p.seed = scenes.PHILOX_KEY_BASE + 200 + i
-        rpr.update(scene, e2e_p, e2e_p.ir_rate_hz, lis_h, src_h, H_host=Hh, want=("H", "params"))
-        e2e_total += time.perf_counter() - ta
-    e2e_value = work * e2e_steps / e2e_total * (ws if ws > 1 else 1) if e2e_total > 0 else None
+    if not args.no_e2e:
+        e2e_p.seed = scenes.PHILOX_KEY_BASE + 100
+        rpr.update(scene, e2e_p, e2e_p.ir_rate_hz, lis_h, src_h, H_host=Hh, want=("H", "params", "stats"))
+        e2e_steps = min(args.steps, 3 if args.workload == "large" else 10)
+        for i in range(e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            e2e_p.seed = scenes.PHILOX_KEY_BASE + 200 + i
+            res = rpr.update(scene, e2e_p, e2e_p.ir_rate_hz, lis_h, src_h, H_host=Hh, want=("H", "params", "stats"))
+            e2e_total += time.perf_counter() - ta
+    e2e_work = float(res["stats"]["segments"] + res["stats"]["shadow_rays"]) if e2e_steps else 0.0
+    e2e_value = e2e_work * e2e_steps / e2e_total * (ws if ws > 1 else 1) if e2e_total > 0 else None
     h2d = (S + 1) * 3 * 4
-    d2h = Hh.nbytes + S * B * C_sizeof("rp_reverb_params")
+    d2h = Hh.nbytes + S * B * C_sizeof("rp_reverb_params") + C_sizeof("rp_trace_stats")
 
     if rank != 0:
         return 0
-    peaks = _peaks()
     clocks = clk.summary()
     # roofline of the dominant kernel: BVH traversal is bound by the ALU pipe, not HBM
     name = max(kt, key=lambda k: kt[k][1])
@@ -363,11 +408,9 @@ def main():
     avg_s = tot / args.steps / 1000.0
     idx = 1 if name == "shadow" else 0
     ops = stc["node_visits"][idx] * ALU_OPS_PER_NODE + stc["tri_tests"][idx] * ALU_OPS_PER_TRI
-    flops = stc["node_visits"][idx] * FLOPS_PER_NODE + stc["tri_tests"][idx] * FLOPS_PER_TRI
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_tops = 152 * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    fops = stc["node_visits"][idx] * FMA_OPS_PER_NODE + stc["tri_tests"][idx] * FMA_OPS_PER_TRI
     achieved = ops / avg_s / 1e12
-    fma_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    peak = minmax_peak / 1e12
     dram = NCU_SHADOW_DRAM.get(args.workload)
     traffic = (dram[0] * st["shadow_rays"] / dram[1]
                if dram and name == "shadow" and not args.fp32_paths and args.shadow_mode != "lanes" else None)
@@ -379,37 +422,38 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "triangles": sc.num_tris, "sources": S, "bands": B,
                    "rays": WORKLOAD["num_rays"], "max_order": WORKLOAD["max_order"], "bins": T, "sh_coeffs": K,
+                   "budget_refill": int(WORKLOAD.get("budget_refill", 0)),
                    "path_precision": "fp32" if args.fp32_paths else "fp64 path state, fp32 traversal",
                    "shadow_rays": args.shadow_mode,
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
         "updates_per_s": ws * 1000.0 / ms_step,
         "closest_hit_segments_per_step": st["segments"], "shadow_rays_per_step": st["shadow_rays"],
+        "primaries_per_step": st["primaries"], "refill_waves": st["waves"],
         "bvh": {"build_ms": round(float(info.build_ms), 2), "max_depth": int(info.max_depth),
                 "nodes": int(info.num_nodes),
                 "node_visits_per_segment": stc["node_visits"][0] / max(1, stc["segments"]),
                 "node_visits_per_shadow_ray": stc["node_visits"][1] / max(1, stc["shadow_rays"]),
                 "tri_tests_per_segment": stc["tri_tests"][0] / max(1, stc["segments"]),
                 "tri_tests_per_shadow_ray": stc["tri_tests"][1] / max(1, stc["shadow_rays"])},
-        "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tops, "traffic": traffic,
+        "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "traffic_note": ("DRAM bytes per update of the shadow-ray kernel, from an ncu capture at "
-                                      f"{'30k' if args.workload == 'medium' else '20k'} primaries scaled by "
-                                      "shadow rays") if traffic else None,
+                                      "fewer primaries scaled by shadow rays") if traffic else None,
                      "launches_per_update": n_l / args.steps,
-                     "peak_note": f"ALU pipe (FP32 min/max/compare): 152 SMs x {ALU_LANES_PER_SM} lanes at the "
-                                  f"median sampled SM clock {sm_mhz:.0f} MHz (derived, not measured)",
-                     "algorithmic": f"{ALU_OPS_PER_NODE:.0f} min/max/compare per node visit + "
+                     "peak_note": "FP32 min/max instructions per second, measured on this GPU by "
+                                  "rp_measure_pipe_peaks (independent chains on every SM, CUDA events)",
+                     "algorithmic": f"{ALU_OPS_PER_NODE:.0f} FP32 min/max/compare per node visit + "
                                     f"{ALU_OPS_PER_TRI:.0f} compares per triangle test, visits counted on the "
                                     f"same update",
-                     "fma_pipe": {"achieved": flops / avg_s / 1e12, "peak": fma_peak,
-                                  "frac": flops / avg_s / 1e12 / fma_peak,
-                                  "algorithmic": f"{FLOPS_PER_NODE:.0f} flop/node visit + "
-                                                 f"{FLOPS_PER_TRI:.0f} flop/triangle test"}},
-        "kernel_ms_per_step": {k: v[1] / max(1, v[0]) * v[0] / args.steps for k, v in kt.items()},
+                     "fma_pipe": {"achieved": fops / avg_s / 1e12, "peak": fma_peak / 1e12,
+                                  "frac": fops / avg_s / fma_peak, "unit": "T FMA-pipe instructions/s",
+                                  "algorithmic": f"{FMA_OPS_PER_NODE:.0f} per node visit + "
+                                                 f"{FMA_OPS_PER_TRI:.0f} per triangle test"}},
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kt.items()},
         "kernel_share": shares,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": 1000 * e2e_total / e2e_steps if e2e_total > 0 else None},
+                "ms_per_step": 1000 * e2e_total / e2e_steps if e2e_total > 0 else None, "steps": e2e_steps},
         "clocks": clocks,
     }
     if cpu:

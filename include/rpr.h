@@ -64,8 +64,11 @@ enum {
     RP_ERR_NAN_INPUT = -7,      /* a vertex, material or position is not finite */
     RP_ERR_EMPTY_SCENE = -8,    /* zero triangles */
     RP_ERR_NO_DEVICE = -9,      /* no CUDA device or wrong architecture */
-    RP_ERR_TOO_LARGE = -10      /* the problem does not fit the fixed scratch of
+    RP_ERR_TOO_LARGE = -10,     /* the problem does not fit the fixed scratch of
                                    rp_trace_noalloc (RP_NOALLOC_SCRATCH_BYTES) */
+    RP_ERR_BOUNDS = -11         /* a kernel computed an index outside its array (only the
+                                   bounds-checked build, compiled with RP_CHECKED, tests
+                                   this); the access was skipped, results incomplete */
 };
 
 /* Where an input array lives. */
@@ -421,23 +424,59 @@ int rp_mlp_train_step(rp_mlp *mlp, const void *Xb, const float *T, const float *
 
 /* rp_trace without any memory allocation.  The paper has no counterpart: it exists
  * for callers that must not allocate device memory during an update -- a real-time
- * audio or game thread that cannot block on the driver's allocator mid-frame, code
- * running while a stream is captured into a CUDA graph (cudaMalloc is not allowed
- * there), or applications that hand out all device memory from their own pool.
- * Same arguments and outputs as rp_trace (no ray hashes); the scene and context are
- * created beforehand with rp_create / rp_scene_create.  All temporaries come from
- * one static __device__ array of RP_NOALLOC_SCRATCH_BYTES; no cudaMalloc, cudaFree or
- * other allocating call is made.  Problems whose temporaries do not fit return
- * RP_ERR_TOO_LARGE (roughly: 68 + 4B bytes per ray x reflection for the stored
- * reflections, 8 B per (source, bin) and 8 B per histogram cell, the rest holds
- * contribution records).
+ * audio or game thread that cannot block on the driver's allocator mid-frame, or an
+ * application that hands out all device memory from its own pool and does not let
+ * libraries allocate.  Same arguments and outputs as rp_trace (no ray hashes); the
+ * scene and context are created beforehand with rp_create / rp_scene_create.  All
+ * temporaries come from one static __device__ array of RP_NOALLOC_SCRATCH_BYTES; no
+ * cudaMalloc, cudaFree or other allocating call is made.
+ * Size limit: the problem fits when, with R = num_rays x max_order (stored
+ * reflections, worst case) and B bands, these together stay within the array:
+ *   (96 + 8 B) bytes per reflection (stored reflections, their spatial order and the
+ *   cell-ordered copy the shadow rays read), 1 MiB of cell counts, 12 B per (source,
+ *   bin) (counting sort), 8 B per histogram cell S x B x K x T (compensated sums),
+ *   and room for at least R / 2 + 4096 + S contribution records of (29 + 4 B) bytes
+ *   each (key, ray id, energies, sort index and the share of the FP64 re-decision
+ *   queue).  Larger problems return RP_ERR_TOO_LARGE before any work is enqueued.
  * The first call on a device looks up the array's device address with that device
  * current: make it before any stream capture.  Every call shares the array and
  * overwrites the previous call's temporaries, so calls that may overlap on the GPU
- * (several streams or host threads) race and must be serialised by the caller. */
+ * (several streams or host threads) race and must be serialised by the caller.
+ * Host positions are copied with cudaMemcpyAsync, and budget_refill reads the waves'
+ * sizes back (the stream is synchronised), as in rp_trace. */
 int rp_trace_noalloc(rp_scene *scene, const rp_trace_params *params, const float *listener,
                      const float *sources, int32_t num_sources, float *H, rp_direct *direct,
                      rp_trace_stats *stats);
+
+/* Limits for exercising the error paths without faulting the GPU (the paper has no
+ * counterpart).  All zero means the normal limits.  rp_trace and rp_update of the
+ * context apply them until they are reset:
+ *   iter_cap    node visits of one BVH traversal query (closest hit, shadow ray or
+ *               direct sound) before it stops and records RP_ERR_TIMEOUT; normally
+ *               4 x internal nodes + 64, which a query of a well-formed tree never
+ *               reaches.  A query stopped this way answers with what it found so far.
+ *   hit_cap     stored-reflection slots of a trace step; normally num_rays x max_order
+ *               (the worst case).  Reflections past it are dropped and RP_ERR_CAPACITY
+ *               is recorded.
+ *   record_cap  contribution records held at once; normally the worst case of a record
+ *               chunk.  Records past it are dropped and RP_ERR_CAPACITY is recorded.
+ * The errors come back from rp_sync_status (and in rp_trace_stats.error); the context
+ * stays usable, and the next call after the limits are reset runs normally.
+ * limits = NULL resets them. */
+typedef struct {
+    int32_t iter_cap;
+    int32_t reserved;
+    uint64_t hit_cap;
+    uint64_t record_cap;
+} rp_debug_limits;
+int rp_set_debug_limits(rp_ctx *ctx, const rp_debug_limits *limits);
+
+/* Measured throughput of the FP32 pipes that bound BVH traversal (a calibration for
+ * rooflines; the paper has no counterpart): *fma_per_s = FP32 fused multiply-add
+ * instructions per second (2 flops each), *minmax_per_s = FP32 min/max instructions
+ * per second, each from independent chains filling every SM, timed with CUDA events
+ * on the context stream (best of five).  Allocates a small buffer and synchronises. */
+int rp_measure_pipe_peaks(rp_ctx *ctx, double *fma_per_s, double *minmax_per_s);
 
 /* Synchronise the context stream and return the first device-side error (or a CUDA
  * error).  Clears the recorded device error. */

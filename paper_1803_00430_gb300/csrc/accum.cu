@@ -45,7 +45,7 @@ __global__ void k_count(TraceWork w, unsigned long long chunk)
     const unsigned long long n = min(w.ctr->n_records, w.rec.cap);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x)
-        atomicAdd(&w.cnt[w.rec.key[i]], 1u);
+        if (RP_IN_RANGE(w.rec.key[i], (unsigned long long)w.k.S * w.k.T, w.status)) atomicAdd(&w.cnt[w.rec.key[i]], 1u);
 }
 
 // Exclusive scan of cnt[0..n) into off[0..n] (off[n] = total; off may be cnt).  A
@@ -164,8 +164,9 @@ __global__ void k_scatter(TraceWork w, unsigned long long chunk)
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t key = w.rec.key[i];
+        if (!RP_IN_RANGE(key, (unsigned long long)w.k.S * w.k.T, w.status)) continue;
         const uint32_t pos = w.off[key] + atomicAdd(&w.cur[key], 1u);
-        w.perm[pos] = (uint32_t)i;
+        if (RP_IN_RANGE(pos, w.rec.cap, w.status)) w.perm[pos] = (uint32_t)i;
     }
 }
 
@@ -200,7 +201,8 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, u
         for (uint32_t base = begin; base < end; base += 32) {
             const int n = (int)min(32u, end - base);
             if (lane < n) {
-                const uint32_t r = w.perm[base + lane];
+                uint32_t r = w.perm[base + lane];
+                if (!RP_IN_RANGE(r, w.rec.cap, w.status)) r = 0;  // (checked build) keep going on record 0
                 const uint32_t rid = w.rec.rid[r];
                 const float *e = w.rec.e + (unsigned long long)r * B;
 #pragma unroll
@@ -237,6 +239,7 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, u
             if (c < BK) {
                 const int b = c / K, kk = c - b * K;
                 const unsigned long long idx = (((unsigned long long)s * B + b) * K + kk) * T + bin;
+                if (!RP_IN_RANGE(idx, (unsigned long long)S * B * K * T, w.status)) continue;
                 if (first) {
                     w.Hs[idx] = sum[i];
                     w.He[idx] = err[i];

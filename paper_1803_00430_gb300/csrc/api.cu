@@ -224,7 +224,8 @@ int check_params(const rp_scene *sc, const rp_trace_params *p, int S)
     if (p->num_bins < 1 || p->min_order < 0) return RP_ERR_INVALID_ARG;
     if ((p->flags & RP_FLAG_SHADOW_PACKETS) && (p->flags & RP_FLAG_SHADOW_LANES)) return RP_ERR_INVALID_ARG;
     if ((unsigned long long)S * (unsigned long long)p->num_bins >= (1ull << 31)) return RP_ERR_INVALID_ARG;
-    if (p->num_rays > 0xffffffffull || p->first_ray + p->num_rays > 0x100000000ull) return RP_ERR_INVALID_ARG;
+    // ray ids are 32-bit: first_ray + num_rays <= 2^32, written so that it cannot wrap
+    if (p->num_rays > 0xffffffffull || p->first_ray > 0x100000000ull - p->num_rays) return RP_ERR_INVALID_ARG;
     if (p->num_rays * (unsigned long long)std::max(p->max_order, 1) >= (1ull << 40)) return RP_ERR_INVALID_ARG;
     if (!(p->ir_rate_hz > 0.f) || !(p->speed_of_sound > 0.f) || !(p->source_radius > 0.f))
         return RP_ERR_INVALID_ARG;
@@ -262,6 +263,7 @@ const char *rp_status_string(int s)
     case RP_ERR_EMPTY_SCENE: return "scene has no triangles";
     case RP_ERR_NO_DEVICE: return "no usable CUDA device";
     case RP_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of rp_trace_noalloc";
+    case RP_ERR_BOUNDS: return "index out of range (bounds-checked build)";
     default: return "unknown status";
     }
 }
@@ -315,6 +317,18 @@ int rp_destroy(rp_ctx *c)
     for (auto e : c->free_events) cudaEventDestroy(e);
     cudaFree(c->d_status);
     delete c;
+    return RP_OK;
+}
+
+int rp_set_debug_limits(rp_ctx *c, const rp_debug_limits *lim)
+{
+    if (!c) return RP_ERR_INVALID_ARG;
+    if (!lim) {
+        c->dbg = rp_debug_limits{0, 0, 0ull, 0ull};
+        return RP_OK;
+    }
+    if (lim->iter_cap < 0) return RP_ERR_INVALID_ARG;
+    c->dbg = *lim;
     return RP_OK;
 }
 
@@ -507,6 +521,10 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
     job.num_rays = p->num_rays;
     job.hit_off = 0;
     job.hit_cap = z.hit_cap;
+    // test limits (rp_set_debug_limits): a smaller iteration cap or capacity
+    if (c->dbg.iter_cap > 0) job.sc.iter_cap = c->dbg.iter_cap;
+    if (c->dbg.hit_cap > 0) job.hit_cap = std::min<unsigned long long>(job.hit_cap, c->dbg.hit_cap);
+    if (c->dbg.record_cap > 0) w.rec.cap = std::min<unsigned long long>(w.rec.cap, c->dbg.record_cap);
     job.scene_id = p->scene_id;
     job.S = S;
     job.src_off = 0;

@@ -383,7 +383,7 @@ int rp_batch_create(rp_ctx *c, const rp_batch_item *items, int32_t n, const rp_t
         const rp_batch_item &it = items[i];
         if (!it.scene || it.scene->ctx != c || it.num_sources < 0 || it.num_sources > RP_MAX_SOURCES ||
             !it.listener || (it.num_sources > 0 && !it.sources) || it.num_rays > 0xffffffffull ||
-            it.first_ray + it.num_rays > 0x100000000ull)
+            it.first_ray > 0x100000000ull - it.num_rays)  // 32-bit ray ids, no wrap
             return RP_ERR_INVALID_ARG;
         if (B < 0) B = it.scene->B;
         if (it.scene->B != B) return RP_ERR_INVALID_ARG;

@@ -23,6 +23,22 @@ __device__ __forceinline__ void raise_error(int *status, int code)
     if (status) atomicCAS(status, 0, code);
 }
 
+// Bounds checks of the RP_CHECKED build: the kernels test every reflection, record,
+// key, cell and histogram index they compute (node and triangle indices are tested
+// in every build) before using it; a violation records RP_ERR_BOUNDS and the access
+// is skipped.  Without RP_CHECKED the test compiles to `true`.
+__device__ __forceinline__ bool checked_index(unsigned long long i, unsigned long long n, int *status)
+{
+    if (i < n) return true;
+    raise_error(status, RP_ERR_BOUNDS);
+    return false;
+}
+#ifdef RP_CHECKED
+#define RP_IN_RANGE(i, n, status) ::rp::checked_index((unsigned long long)(i), (unsigned long long)(n), (status))
+#else
+#define RP_IN_RANGE(i, n, status) true
+#endif
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
 // multiplies with the published multipliers, key bumped by the Weyl constants.

@@ -43,6 +43,7 @@ struct rp_ctx {
     int *d_status = nullptr;
     int paths_blocks = 0, shadow_blocks = 0;
     int shadow_steps = 8;  // node visits a shadow-ray lane makes between refills (one-ray-per-lane mode)
+    rp_debug_limits dbg = {0, 0, 0ull, 0ull};  // rp_set_debug_limits (all zero: the normal limits)
     unsigned long long ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
     // workspace
     //   stored reflections (hit_*), their cell-ordered copy (shit_*) and order (hord_*),
@@ -73,7 +74,8 @@ struct rp_scene {
 inline rp::SceneView make_view(const rp_scene *sc)
 {
     rp::SceneView v = {sc->nodes, sc->tris, sc->alpha, sc->scat, sc->wdiff, sc->wspec, sc->thr, sc->num_tris,
-                       sc->num_nodes, sc->B, sc->tmin, sc->tmin_d, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+                       sc->num_nodes, sc->B, rp::ITER_CAP_MULT * sc->num_nodes + 64, sc->tmin, sc->tmin_d,
+                       {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     for (int a = 0; a < 3; ++a) {
         v.lo[a] = sc->lo[a];
         v.ext[a] = sc->hi[a] - sc->lo[a];

@@ -25,6 +25,10 @@ namespace rp {
 //   materials: alpha, scattering, w_diff = s/sbar, w_spec = (1-s)/(1-sbar) [mat][B],
 //          thr[mat] = ceil(sbar * 2^24) (diffuse if the 24-bit uniform is below it).
 // ---------------------------------------------------------------------------
+// node visits of one traversal query are capped at ITER_CAP_MULT x nodes + 64 (a
+// query of a well-formed tree visits every node at most once)
+constexpr int ITER_CAP_MULT = 4;
+
 struct SceneView {
     const float4 *__restrict__ nodes;
     const float4 *__restrict__ tris;
@@ -36,6 +40,7 @@ struct SceneView {
     int num_tris;
     int num_nodes;
     int B;
+    int iter_cap;   // node visits per traversal query before RP_ERR_TIMEOUT
     float tmin;     // self-intersection guard used by FP32 queries
     double tmin_d;  // the same guard for FP64 re-decisions
     float lo[3];    // bounding box of the vertices (cells of the shadow-ray order)

@@ -3,9 +3,9 @@
 //
 // rp_trace allocates (and grows) device workspace with cudaMalloc the first time a
 // problem size is seen.  Some callers cannot allow that: a real-time audio or game
-// thread that must never block on the driver's allocator mid-frame, code that runs
-// while a CUDA stream is being captured into a graph (cudaMalloc is not permitted
-// there), or a host application that owns all device memory through its own pool.
+// thread that must never block on the driver's allocator mid-frame, or a host
+// application that hands out all device memory from a pool of its own and forbids
+// libraries to allocate behind its back.
 // rp_trace_noalloc runs the same kernels on the same inputs and writes the same
 // outputs, but takes every temporary buffer (counters, stored reflections,
 // contribution records, the counting sort, the compensated sums) from one
@@ -21,6 +21,9 @@
 //   - the device address of the array is looked up once per device, with that
 //     device current, on the first call there: make that first call before any
 //     stream capture begins.
+// Host positions are staged with cudaMemcpyAsync from the caller's arrays, and with
+// budget refill the host reads each batch of waves' size back (the stream is
+// synchronised), as in rp_trace.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -92,7 +95,8 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     if (S < 0 || S > RP_MAX_SOURCES) return RP_ERR_INVALID_ARG;
     if (p->max_order < 0 || p->sh_order < 0 || p->sh_order > RP_MAX_SH_ORDER || p->num_bins < 1 || p->min_order < 0)
         return RP_ERR_INVALID_ARG;
-    if (p->num_rays > 0xffffffffull || p->first_ray + p->num_rays > 0x100000000ull) return RP_ERR_INVALID_ARG;
+    // ray ids are 32-bit: first_ray + num_rays <= 2^32, written so that it cannot wrap
+    if (p->num_rays > 0xffffffffull || p->first_ray > 0x100000000ull - p->num_rays) return RP_ERR_INVALID_ARG;
     if ((p->flags & RP_FLAG_SHADOW_PACKETS) && (p->flags & RP_FLAG_SHADOW_LANES)) return RP_ERR_INVALID_ARG;
     if (!(p->ir_rate_hz > 0.f) || !(p->speed_of_sound > 0.f) || !(p->source_radius > 0.f)) return RP_ERR_INVALID_ARG;
     if (!std::isfinite(p->ir_rate_hz) || !std::isfinite(p->speed_of_sound) || !std::isfinite(p->source_radius))

@@ -315,8 +315,10 @@ __global__ void k_hit_cells(TraceWork w)
         const int job = w.njobs > 1 ? job_of_hit(w, f) : 0;
         const SceneJob &J = w.njobs > 1 ? w.jobs[job] : w.job0;
         const unsigned long long slot = J.hit_off + (f - (w.njobs > 1 ? w.js[job].hit_prefix : 0ull));
+        if (!RP_IN_RANGE(slot, w.hits.cap, w.status) || !RP_IN_RANGE(f, w.hits.cap, w.status)) continue;
         const float4 P = w.hits.p[slot];
         const uint32_t cell = ((uint32_t)job << bits) | cell_code(J.sc, xyz(P), bits);
+        if (!RP_IN_RANGE(cell, w.horder.ncells, w.status)) continue;
         w.horder.cell[f] = cell;
         atomicAdd(&w.horder.cnt[cell], 1u);
     }
@@ -331,8 +333,9 @@ __global__ void k_hit_scatter(TraceWork w)
         const int job = w.njobs > 1 ? job_of_hit(w, f) : 0;
         const SceneJob &J = w.njobs > 1 ? w.jobs[job] : w.job0;
         const unsigned long long slot = J.hit_off + (f - (w.njobs > 1 ? w.js[job].hit_prefix : 0ull));
+        if (!RP_IN_RANGE(w.horder.cell[f], w.horder.ncells, w.status)) continue;
         const uint32_t pos = atomicAdd(&w.horder.cnt[w.horder.cell[f]], 1u);
-        w.horder.perm[pos] = (uint32_t)slot;
+        if (RP_IN_RANGE(pos, w.hits.cap, w.status)) w.horder.perm[pos] = (uint32_t)slot;
     }
 }
 
@@ -344,6 +347,7 @@ __global__ void k_hit_gather(TraceWork w)
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long slot = w.horder.perm[i];
+        if (!RP_IN_RANGE(slot, w.hits.cap, w.status) || !RP_IN_RANGE(i, w.shits.cap, w.status)) continue;
         w.shits.p[i] = w.hits.p[slot];
         w.shits.n[i] = w.hits.n[slot];
         w.shits.rid[i] = w.hits.rid[slot];
@@ -640,7 +644,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
             if (!plan && h >= k.min_order && J.S > 0) {
                 const unsigned long long jl =
                     BATCH ? warp_append_job(&w.js[job].n_hits, job) : warp_append(&w.js[0].n_hits);
-                if (jl < J.hit_cap) {
+                if (jl < J.hit_cap && RP_IN_RANGE(J.hit_off + jl, w.hits.cap, w.status)) {
                     const unsigned long long j = J.hit_off + jl;
                     const float4 phi = make_float4((float)p.x, (float)p.y, (float)p.z, (float)L);
                     w.hits.p[j] = phi;
@@ -701,7 +705,8 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                 if (b < B) atomicAdd(&acc.absb[b], (double)absorbed[b * PATH_THREADS]);
             if (HASH && w.ray_hash && rid >= J.first_ray && rid - J.first_ray < J.num_rays)
                 w.ray_hash[rid - J.first_ray] = hash;
-            if (plan) w.plan_seg[rid - J.first_ray] = (uint32_t)h;  // the path's segments
+            if (plan && RP_IN_RANGE(rid - J.first_ray, J.num_rays * (unsigned long long)M, w.status))
+                w.plan_seg[rid - J.first_ray] = (uint32_t)h;  // the path's segments
             have = false;
         }
     }
@@ -722,6 +727,7 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
 {
     const TraceConsts &k = w.k;
     const int B = k.B, T = k.T;
+    if (!RP_IN_RANGE(j, w.shits.cap, w.status) || !RP_IN_RANGE(w.horder.perm[j], w.hits.cap, w.status)) return;
     const float4 P = w.shits.p[j];
     float e[MAXB];
 #pragma unroll
@@ -768,7 +774,8 @@ __device__ __forceinline__ bool item_slot(const TraceWork &w, bool batch, int jo
     const unsigned r = (unsigned)(local & 31u);
     j = js.hit_prefix + tile * 32ull + r;
     gs = J.src_off + (int)(run - tile * (unsigned long long)J.S);
-    return tile * 32ull + r < n;
+    const bool real = tile * 32ull + r < n;
+    return real && RP_IN_RANGE(j, w.shits.cap, w.status);
 }
 
 // (job, reflection, global source) of shadow item q; false for a hole
@@ -858,7 +865,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
                         ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
                         st = {0, 0, INFINITY, false, false};
                         steps = 0;
-                        iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
+                        iter_cap = sc.iter_cap;
                         f = cth * inv_pi / dist2;
                         busy = true;
                     }
@@ -998,7 +1005,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 if (((grp >> lane) & 1u) && sc.num_tris > 0) leaf(0);
                 continue;
             }
-            const int iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
+            const int iter_cap = sc.iter_cap;
             int node = 0, sp = 0, iters = 0;
             unsigned mask = grp;  // lanes of the group that reach `node` and have no answer yet
             while (mask) {

@@ -28,7 +28,6 @@ namespace rp {
 constexpr int SMEM_STACK = 24;
 constexpr int LOCAL_STACK = 40;
 constexpr int STACK_DEPTH = SMEM_STACK + LOCAL_STACK;
-constexpr int ITER_CAP_MULT = 4;  // node visits per query are capped at 4 x nodes + 64
 constexpr float AMBIG_BARY = 2e-4f;
 constexpr float AMBIG_T = 2e-4f;
 
@@ -140,7 +139,7 @@ __device__ __forceinline__ void traverse_core(const SceneView &sc, float3 o, flo
         }
         return;
     }
-    const int iter_cap = ITER_CAP_MULT * sc.num_nodes + 64;
+    const int iter_cap = sc.iter_cap;
     int node = 0, sp = 0, iters = 0;
     while (true) {
         if (COUNT) ts.nodes++;

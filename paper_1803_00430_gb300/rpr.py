@@ -29,7 +29,7 @@ RP_OK = 0
 STATUS = {
     0: "RP_OK", -1: "RP_ERR_INVALID_ARG", -2: "RP_ERR_CUDA", -3: "RP_ERR_OOM", -4: "RP_ERR_CAPACITY",
     -5: "RP_ERR_STACK_OVERFLOW", -6: "RP_ERR_TIMEOUT", -7: "RP_ERR_NAN_INPUT", -8: "RP_ERR_EMPTY_SCENE",
-    -9: "RP_ERR_NO_DEVICE", -10: "RP_ERR_TOO_LARGE",
+    -9: "RP_ERR_NO_DEVICE", -10: "RP_ERR_TOO_LARGE", -11: "RP_ERR_BOUNDS",
 }
 RP_ERR = {v: k for k, v in STATUS.items()}
 RP_MEM_HOST, RP_MEM_DEVICE = 0, 1
@@ -107,6 +107,11 @@ class rp_mlp_config(C.Structure):
                 ("max_batch", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
 
 
+class rp_debug_limits(C.Structure):
+    _fields_ = [("iter_cap", C.c_int32), ("reserved", C.c_int32), ("hit_cap", C.c_uint64),
+                ("record_cap", C.c_uint64)]
+
+
 class rp_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
@@ -157,6 +162,8 @@ _SIGS = {
                            C.c_void_p], C.c_int),
     "rp_trace_noalloc": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                           C.c_void_p, C.c_void_p], C.c_int),
+    "rp_set_debug_limits": ([C.c_void_p, C.POINTER(rp_debug_limits)], C.c_int),
+    "rp_measure_pipe_peaks": ([C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "rp_sync_status": ([C.c_void_p], C.c_int),
     "rp_profile_enable": ([C.c_void_p, C.c_int], C.c_int),
     "rp_profile_reset": ([C.c_void_p], C.c_int),
@@ -184,8 +191,15 @@ def _close_all():
 atexit.register(_close_all)
 
 
+def checked_requested() -> bool:
+    """RPR_CHECKED=1 in the environment selects the bounds-checked build of the library
+    (compiled with RP_CHECKED: every node, triangle, reflection, record, key and
+    histogram index is tested before use; a violation is reported as RP_ERR_BOUNDS)."""
+    return os.environ.get("RPR_CHECKED", "0") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.lib_path(checked_requested())
 
 
 def load(build_if_missing: bool = False):
@@ -193,12 +207,14 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"CUDA library not built: {_build.LIB} is missing "
+    checked = checked_requested()
+    path = _build.lib_path(checked)
+    if build_if_missing and not _build.up_to_date(checked):
+        _build.build(checked=checked)
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
                            "(run python -m paper_1803_00430_gb300.build)")
-    lib = C.CDLL(_build.LIB)
+    lib = C.CDLL(path)
     for name, (args, res) in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = args
@@ -282,6 +298,17 @@ class Context:
 
     def set_stream(self, stream):
         check(self.lib.rp_set_stream(self.h, _stream_handle(stream)), "rp_set_stream")
+
+    def set_debug_limits(self, iter_cap: int = 0, hit_cap: int = 0, record_cap: int = 0):
+        """Lower limits that exercise the error paths (all zero: the normal limits)."""
+        lim = rp_debug_limits(iter_cap, 0, hit_cap, record_cap)
+        check(self.lib.rp_set_debug_limits(self.h, C.byref(lim)), "rp_set_debug_limits")
+
+    def pipe_peaks(self) -> tuple:
+        """(FP32 FMA instructions/s, FP32 min/max instructions/s) measured on the device."""
+        f, m = C.c_double(), C.c_double()
+        check(self.lib.rp_measure_pipe_peaks(self.h, C.byref(f), C.byref(m)), "rp_measure_pipe_peaks")
+        return f.value, m.value
 
     def sync_status(self) -> int:
         return self.lib.rp_sync_status(self.h)

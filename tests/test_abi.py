@@ -42,7 +42,8 @@ def test_status_strings(lib):
 
 def test_struct_layout_matches_c(lib):
     structs = ["rp_mesh_desc", "rp_scene_info", "rp_trace_params", "rp_direct", "rp_trace_stats",
-               "rp_estimate_params", "rp_reverb_params", "rp_kernel_time"]
+               "rp_estimate_params", "rp_reverb_params", "rp_kernel_time", "rp_debug_limits", "rp_batch_item",
+               "rp_batch_tuning", "rp_batch_info", "rp_mlp_config"]
     fields = {s: [f[0] for f in getattr(rpr, s)._fields_] for s in structs}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for s, fs in fields.items():
@@ -77,3 +78,13 @@ def test_create_without_device_fails_cleanly(lib):
     assert lib.rp_create(C.byref(h), 0, None) == rpr.RP_ERR["RP_ERR_NO_DEVICE"]
     assert lib.rp_sync_status(None) == rpr.RP_ERR["RP_ERR_INVALID_ARG"]
     assert lib.rp_trace(None, None, None, None, 0, None, None, None, None) == rpr.RP_ERR["RP_ERR_INVALID_ARG"]
+    assert lib.rp_set_debug_limits(None, None) == rpr.RP_ERR["RP_ERR_INVALID_ARG"]
+
+
+def test_bounds_checked_build_compiles_and_exports_the_same_entry_points():
+    import ctypes as C
+    path = cuda_build.build(checked=True)
+    assert path.endswith(os.path.join("checked", "librpr.so"))
+    lib2 = C.CDLL(path)
+    missing = [n for n in _declared_functions() if not hasattr(lib2, n)]
+    assert not missing, missing

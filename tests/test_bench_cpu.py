@@ -21,18 +21,26 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"].startswith("medium")
+    assert d["config"]["workload"].startswith("large")
+    assert "refill" in d["cpu_baseline"]["sample"] and d["cpu_baseline"]["cpu_model"]
 
 
 def test_cpu_baseline_scales_the_sample_to_the_target():
     sys.path.insert(0, ROOT)
     import bench
-    out = bench.cpu_baseline(target_s=2.0)
+    # the medium workload keeps this test short (the default large one has its own
+    # reference-arm test above)
+    wl, bench.WORKLOAD_NAME, bench.SCENE = bench.WORKLOADS["medium"]
+    bench.WORKLOAD.clear()
+    bench.WORKLOAD.update(wl)
+    out = bench.cpu_baseline(target_s=2.0, single_s=1.0)
     assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] == (os.cpu_count() or 1)
-    rays = int(out["sample"].split(" ")[0])
-    wall = float(out["sample"].rsplit(", ", 1)[1].split(" ")[0])
-    # grown past the 400-ray probe until the sample takes about the target (or the workload)
-    assert rays > 400 and (wall >= 1.0 or rays == bench.WORKLOAD["num_rays"])
+    assert out["cpu_model"] and out["single_thread"]["cores"] == 1 and out["single_thread"]["value"] > 0
+    for o, target in ((out, 2.0), (out["single_thread"], 1.0)):
+        rays = int(o["sample"].split(" ")[0])
+        wall = float(o["sample"].rsplit(", ", 1)[1].split(" ")[0])
+        # grown past the 20-ray probe until the sample takes about the target (or the workload)
+        assert rays > 20 and (wall >= 0.5 * target or rays == bench.WORKLOAD["num_rays"])
 
 
 def test_reference_arm_at_the_papers_operating_point():
@@ -42,3 +50,11 @@ def test_reference_arm_at_the_papers_operating_point():
     d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["config"]["workload"].startswith("paper operating point") and d["config"]["sample_rays_per_step"] == 50
+
+
+def test_reference_arm_on_the_medium_workload():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "medium", "--steps", "2",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert d["config"]["workload"].startswith("medium") and d["steps"] == 2 and d["value"] > 0

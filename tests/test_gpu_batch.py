@@ -87,6 +87,40 @@ def test_batch_item_matches_oracle(ctx):
         assert l1.max() <= pu.L1_BAR, l1
 
 
+def test_batch_at_the_batched_workload_sizes_matches_oracle(ctx):
+    """Items with the batched workload's own parameters -- 8 bands, SH order 2, 64
+    reflections, IR 2 s at 1 kHz, at least 10k rays, 1 to 64 sources, one scene of
+    about 40k triangles -- against the oracle: the histogram per (source, band) and
+    every reverb parameter."""
+    P8 = dict(max_order=64, sh_order=2, num_bins=2000, min_order=1, ir_rate_hz=1000.0)
+    spec = [(40000, 8, 10000, "room"), (12, 64, 10000, "room"), (3000, 16, 12000, "corridor"),
+            (600, 1, 20000, "corridor")]
+    its = []
+    for i, (tris, S, rays, kind) in enumerate(spec):
+        sc = scenes.room_or_corridor(scenes.SEED_BATCHED * 1000 + 600 + i, tris, bands=8, num_sources=S, kind=kind)
+        its.append((sc, rpr.Scene.from_scene(ctx, sc), rays, 300 + i))
+    assert its[0][0].num_tris >= 35000
+    p = rpr.TraceParams(**P8)
+    b = rpr.Batch(ctx, [(scene, sc.listener, sc.sources, rays, sid) for sc, scene, rays, sid in its], p)
+    b.run(seed=41)
+    assert b.stats_dict()["error"] == 0
+    Hb = b.H.double().cpu().numpy()
+    pb = b.params_dict()
+    for (sc, scene, rays, sid), off in zip(its, b.offsets):
+        S = sc.num_sources
+        q = rpr.TraceParams(num_rays=rays, scene_id=sid, seed=41, **P8)
+        o = pu.run_oracle(sc, q, want_hash=False)
+        l1_0, l1_k = pu.band_l1(Hb[off:off + S], o["H"])
+        g = {"params": {k: v[off:off + S] for k, v in pb.items()}}
+        errs = pu.param_errors(g["params"], o["params"])
+        print(f"batched item {sc.num_tris} tris, {S} sources, {rays} rays: L1 {l1_0.max():.2e} "
+              f"(k>0 {l1_k.max():.2e}), {errs}")
+        assert l1_0.max() <= pu.L1_BAR and l1_k.max() <= 2 * pu.L1_BAR
+        assert errs["range_kind_equal"] and errs["drr_inf_equal"], errs
+        assert errs["rt60"] <= pu.PARAM_BAR and errs["g_reverb"] <= pu.PARAM_BAR, errs
+        assert errs["drr_db"] <= pu.DRR_BAR_DB, errs
+
+
 def test_graph_replay_takes_new_keys(ctx):
     its = _items(ctx, n=4, seed=scenes.SEED_BATCHED + 9)
     p = rpr.TraceParams(**P)

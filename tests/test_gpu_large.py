@@ -70,20 +70,8 @@ def test_city_parity_50k_primaries(ctx, city, city_scene):
     # parameters are ill-posed (the estimator itself is pinned on identical H).  The
     # 0.5 % bar holds on the well-posed fits: the same window on both sides, at least
     # 20 bins, R^2 >= 0.9.
-    pg, po = g["params"], o["params"]
-    kinds_equal = pg["range_kind"] == po["range_kind"]
-    well = kinds_equal & (po["range_kind"] > 0) & (po["n_fit"] >= 20) & (po["fit_r2"] >= 0.9)
-    fin = well & np.isfinite(po["drr_db"]) & np.isfinite(pg["drr_db"])
-    with np.errstate(invalid="ignore", divide="ignore"):  # entries outside the masks may be NaN/inf
-        rt = np.abs(pg["rt60_raw"] - po["rt60_raw"])[well] / po["rt60_raw"][well]
-        gr = np.abs(pg["g_reverb"] - po["g_reverb"])[well] / po["g_reverb"][well]
-        drr = np.abs(pg["drr_db"] - po["drr_db"])[fin]
-    rep.update(well_posed=int(well.sum()), kinds_equal=float(kinds_equal.mean()),
-               rt60=float(rt.max()), g_reverb=float(gr.max()), drr_db=float(drr.max()) if fin.any() else 0.0)
+    rep.update(pu.assert_well_posed_params(g, o, min_well=50, min_kinds_equal=0.95))
     print("city, 50k primaries:", rep, "segments", g["stats"]["segments"], "shadow rays", g["stats"]["shadow_rays"])
-    assert well.sum() >= 50, rep
-    assert rep["kinds_equal"] >= 0.95, rep
-    assert rep["rt60"] <= pu.PARAM_BAR and rep["g_reverb"] <= pu.PARAM_BAR and rep["drr_db"] <= pu.DRR_BAR_DB, rep
 
 
 def test_city_full_size_direct_and_invariants(ctx, city, city_scene):

@@ -102,8 +102,9 @@ def test_medium_hall_parity_reduced_rays(ctx, mode):
     rep = pu.assert_parity(g, o, p.num_rays, check_params=False)
     assert g["stats"]["error"] == 0
     assert g["stats"]["segments"] == o["stats"]["segments"]
-    # parameters only where both fits exist; rays here are too few for a stable fit
-    # of every (source, band), the full-size test checks the 0.5 % bar
+    # at 20k primaries some of the 128 (source, band) fits are ill-posed (the
+    # full-size test checks every one); the bar holds on the well-posed ones
+    rep.update(pu.assert_well_posed_params(g, o, min_well=64, min_kinds_equal=0.97))
     print(rep)
 
 
@@ -120,14 +121,16 @@ def test_random_triangle_soup_bvh_matches_brute_force(ctx):
     s = rng.uniform(0.2, 0.8, size=(4, 2)).astype(np.float32)
     sc = scenes.Scene("soup", verts, tris, mats, a, s, np.array([5.0, 5.0, 0.3], np.float32),
                       np.array([[5.0, 0.4, 9.5], [9.6, 9.6, 9.6]], np.float32))
-    p = rpr.TraceParams(num_rays=5000, max_order=8, sh_order=1, num_bins=300, seed=77)
+    p = rpr.TraceParams(num_rays=20000, max_order=8, sh_order=1, num_bins=300, seed=77)
     g = pu.run_gpu(ctx, sc, p)
     osc = oracle.OracleScene.from_scene(sc, use_bvh=False)  # brute force
     op = pu.oracle_params(p)
     Ho, sto, hh = oracle.trace(osc, op, sc.listener, sc.sources, hash_cap=p.num_rays)
-    assert pu.divergence(g["hash"], hh) <= 2e-3  # grazing hits on a random soup
+    div = pu.divergence(g["hash"], hh)
     l1_0, _ = pu.band_l1(g["H"], Ho)
-    assert l1_0.max() <= 5e-3
+    print(f"soup vs brute force: divergence {div:.2e} ({int(round(div * p.num_rays))} rays), L1 {l1_0.max():.2e}")
+    assert div <= pu.DIVERGENCE_BAR
+    assert l1_0.max() <= pu.L1_BAR
 
 
 def test_degenerate_geometry_matches_brute_force(ctx):
@@ -169,15 +172,18 @@ def test_degenerate_geometry_matches_brute_force(ctx):
     s = rng.uniform(0.2, 0.8, size=(4, 3)).astype(np.float32)
     sc = scenes.Scene("degenerate", verts, tris, mat, a, s, np.array([1.0, 1.0, 1.0], np.float32),
                       np.array([[7.5, 5.5, 3.5], [0.5, 5.5, 3.5]], np.float32))
-    p = rpr.TraceParams(num_rays=4000, max_order=10, sh_order=1, num_bins=300, seed=91)
+    p = rpr.TraceParams(num_rays=20000, max_order=10, sh_order=1, num_bins=300, seed=91)
     g = pu.run_gpu(ctx, sc, p)
     assert g["stats"]["error"] == 0
     osc = oracle.OracleScene.from_scene(sc, use_bvh=False)  # brute force
     Ho, sto, hh = oracle.trace(osc, pu.oracle_params(p), sc.listener, sc.sources, hash_cap=p.num_rays)
-    assert abs(g["stats"]["segments"] - sto["segments"]) <= 2e-3 * sto["segments"]
-    assert pu.divergence(g["hash"], hh) <= 2e-3  # grazing hits on coincident and strip geometry
+    div = pu.divergence(g["hash"], hh)
     l1_0, _ = pu.band_l1(g["H"], Ho)
-    assert l1_0.max() <= 5e-3
+    print(f"degenerate geometry vs brute force: divergence {div:.2e} ({int(round(div * p.num_rays))} rays), "
+          f"L1 {l1_0.max():.2e}, segments {g['stats']['segments']} vs {sto['segments']}")
+    assert div <= pu.DIVERGENCE_BAR
+    assert abs(g["stats"]["segments"] - sto["segments"]) <= pu.DIVERGENCE_BAR * p.num_rays * p.max_order
+    assert l1_0.max() <= pu.L1_BAR
 
 
 @pytest.mark.parametrize("sh_order,bands", [(0, 1), (3, 8), (2, 3)])

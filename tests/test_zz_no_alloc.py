@@ -1,12 +1,15 @@
 """rp_trace_noalloc: the trace step for callers that must not allocate device memory
-during an update (real-time audio/game threads, code running under CUDA graph
-capture, applications owning all device memory).  It takes its temporaries from a
-fixed static device array instead of library-allocated workspace.
+during an update -- a real-time audio or game thread that cannot block on the
+allocator mid-frame, or an application that owns all device memory through its own
+pool.  It takes its temporaries from a fixed static device array instead of
+library-allocated workspace.
 
 Checked through the C ABI against rp_trace on the same inputs, on two calls in a
 row (the array keeps the previous call's contents, so the second call also checks
-that what must start at zero is cleared), plus the size limit.  This file is
-collected last on purpose."""
+that what must start at zero is cleared), with budget refill (rp_trace plans the
+refill waves with a counting pass, rp_trace_noalloc traces them wave by wave: the
+rays and results must be the same), plus the size limit.  This file is collected
+last on purpose."""
 import numpy as np
 import pytest
 
@@ -51,6 +54,24 @@ def test_noalloc_matches_rp_trace_on_two_calls_in_a_row(ctx):
         assert got.stats_dict()["error"] == 0
         assert np.abs(got.H.cpu().numpy()).sum() > 0
         _compare(got, ref)
+
+
+def test_noalloc_matches_rp_trace_with_budget_refill(ctx):
+    # an open box (one wall missing) so that rays escape early and the refill waves
+    # have unused budget to spend
+    sc = scenes.shoebox(num_sources=2)
+    keep = np.ones(len(sc.tris), dtype=bool)
+    keep[:2] = False
+    sc.tris, sc.tri_material = sc.tris[keep], sc.tri_material[keep]
+    scene = rpr.Scene.from_scene(ctx, sc)
+    p = rpr.TraceParams(num_rays=3000, max_order=20, sh_order=1, num_bins=800, budget_refill=1,
+                        seed=scenes.PHILOX_KEY_BASE + 3)
+    ref = rpr.trace(scene, p, sc.listener, sc.sources)
+    got = rpr.trace_noalloc(scene, p, sc.listener, sc.sources)
+    assert got.stats_dict()["error"] == 0
+    assert ref.stats_dict()["waves"] > 1
+    assert got.stats_dict()["waves"] == ref.stats_dict()["waves"]
+    _compare(got, ref)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(ctx):
