@@ -362,13 +362,19 @@ int rp_batch_autotune(rp_batch *batch, uint64_t seed, const char *cache_path,
  * --------------------------------------------------------------------------- */
 typedef struct rp_mlp rp_mlp;
 
+enum { RP_MLP_FLAG_LEGACY_GEMM = 1 /* every GEMM on the mma.sync kernels (for comparison) */ };
+
 typedef struct {
     int32_t in_dim;     /* input features, >= 522 and a multiple of 8 (features below) */
     int32_t hidden;     /* width of each hidden layer, multiple of 8 */
     int32_t layers;     /* hidden layers (GELU), 1..8 */
     int32_t out_dim;    /* outputs (16: log RT60 [s] and DRR [dB] per band) */
     int32_t max_batch;  /* largest n of one call */
-    int32_t reserved;
+    int32_t flags;      /* RP_MLP_FLAG_*; 0: the forward pass runs as one fused tcgen05
+                           tensor-core launch (TMA-staged operands, TMEM accumulators)
+                           when hidden is a multiple of 64 up to 256, out_dim a multiple of
+                           16 up to 256 and layers <= 8, else on mma.sync GEMMs; the
+                           backward pass runs on mma.sync GEMMs */
     uint64_t seed;      /* weight initialisation: uniform +-sqrt(6/(in+out)) from Philox */
 } rp_mlp_config;
 

@@ -306,49 +306,54 @@ def trace_rays(scene: OracleScene, p: TraceParams, listener, sources, begin: int
 def trace_parallel(scene: OracleScene, p: TraceParams, listener, sources, threads: int = 0,
                    chunk: int = 0, hash_cap: int = 0):
     """The same step as `trace`, with each wave's primaries split into contiguous
-    chunks traced by threads (ctypes releases the GIL).  Partial sums are added in
-    chunk order, so the result differs from `trace` only by FP64 rounding order."""
+    chunks traced by threads (ctypes releases the GIL).  Thread i traces chunks i,
+    i + threads, ... of every wave into partial sums of its own, kept across the
+    refill waves, and the partial sums are added in thread order at the end, so the
+    result is deterministic and differs from `trace` only by FP64 rounding order."""
     threads = threads or os.cpu_count() or 1
     lis, src = _src_arrays(listener, sources)
     S, B, K, T = src.shape[0], scene.B, (p.sh_order + 1) ** 2, p.num_bins
-    H = np.zeros((S, B, K, T))
-    st = np.zeros(ST_COUNT)
     hashes = np.zeros(max(hash_cap, 1), dtype=np.uint64)
     begin, count, waves = int(p.first_ray), int(p.num_rays), 0
     lib = _load()
+    cp = p.c()
+    parts_H: list = [None] * threads
+    parts_st = [np.zeros(ST_COUNT) for _ in range(threads)]
     while count > 0:
         csz = chunk or max(1, -(-count // (threads * 4)))
         ranges = [(a, min(a + csz, begin + count)) for a in range(begin, begin + count, csz)]
-        results: list = [None] * len(ranges)
-        nxt = [0]
-        lk = threading.Lock()
+        used = min(threads, len(ranges))
 
-        def worker():
-            while True:
-                with lk:
-                    i = nxt[0]
-                    nxt[0] += 1
-                if i >= len(ranges):
-                    return
-                a, b = ranges[i]
-                results[i] = trace_rays(scene, p, lis, src, a, b, want_hash=hash_cap > a - int(p.first_ray))
+        def worker(i):
+            if parts_H[i] is None:
+                parts_H[i] = np.zeros((S, B, K, T))
+            for a, b in ranges[i::used]:
+                a0 = a - int(p.first_ray)
+                hh = None
+                if hash_cap > a0 >= 0:
+                    hh = np.zeros(b - a, dtype=np.uint64)
+                lib.orc_trace_rays(scene._h, C.byref(cp), _d(lis), _d(src), S, int(a), int(b), _d(parts_H[i]),
+                                   _d(parts_st[i]), hh.ctypes.data_as(C.POINTER(C.c_uint64)) if hh is not None
+                                   else None)
+                if hh is not None:
+                    n = min(b - int(p.first_ray), hash_cap) - a0
+                    hashes[a0:a0 + n] = hh[:n]
 
-        ths = [threading.Thread(target=worker) for _ in range(min(threads, len(ranges)))]
+        ths = [threading.Thread(target=worker, args=(i,)) for i in range(used)]
         for t in ths:
             t.start()
         for t in ths:
             t.join()
-        for (a, b), (h, s, hh) in zip(ranges, results):
-            H += h
-            st += s
-            a0 = a - int(p.first_ray)
-            if hash_cap > a0 >= 0:
-                n = min(b - int(p.first_ray), hash_cap) - a0
-                hashes[a0:a0 + n] = hh[:n]
         begin += count
         waves += 1
-        count = (int(lib.orc_next_wave(int(p.num_rays), int(p.max_order), float(st[36])))
-                 if p.budget_refill else 0)
+        segs = sum(float(x[36]) for x in parts_st)
+        count = int(lib.orc_next_wave(int(p.num_rays), int(p.max_order), segs)) if p.budget_refill else 0
+    H = np.zeros((S, B, K, T))
+    st = np.zeros(ST_COUNT)
+    for h, x in zip(parts_H, parts_st):
+        if h is not None:
+            H += h
+        st += x
     st[41] = waves
     kp = st[38]
     if kp > 0:

@@ -9,9 +9,11 @@
 // from Philox), and every cell is summed in FP32: each group of 32 staged records
 // with plain fused multiply-adds (relative error at most 32 * 2^-24), the groups with
 // Kahan compensation.  Each cell is written by exactly one warp, so no atomics touch
-// H.  Chunks of records
-// (when the record buffer is smaller than one step's records) are merged into a
-// running (sum, error) pair with an error-free two-sum.
+// H.  Chunks of records (when the record buffer is smaller than one step's records)
+// are merged into a running (sum, error) pair with an error-free two-sum.  The running
+// pair is kept key-major, [source][bin][band][coefficient], so that a warp's B*K cells
+// of one key are contiguous (coalesced loads and stores); the finalize kernel
+// transposes it through shared memory into H[s][b][k][t].
 #include "internal.cuh"
 
 namespace rp {
@@ -232,13 +234,12 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, u
             for (int i = 0; i < ACC_SLOTS; ++i) kahan_add(sum[i], err[i], part[i]);
             __syncwarp();
         }
-        const int s = (int)(key / T), bin = (int)(key - (long long)s * T);
 #pragma unroll
         for (int i = 0; i < ACC_SLOTS; ++i) {
             const int c = lane + 32 * i;
             if (c < BK) {
-                const int b = c / K, kk = c - b * K;
-                const unsigned long long idx = (((unsigned long long)s * B + b) * K + kk) * T + bin;
+                // running pair, key-major: [s][bin][b][kk]
+                const unsigned long long idx = (unsigned long long)key * BK + c;
                 if (!RP_IN_RANGE(idx, (unsigned long long)S * B * K * T, w.status)) continue;
                 if (first) {
                     w.Hs[idx] = sum[i];
@@ -257,20 +258,42 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, u
     }
 }
 
-// H = (sum + error) / K_primaries of the source's job; late energy likewise (one
-// job); then direct sound binned into H when min_order == 0
-__global__ void k_finalize(TraceWork w)
+// H[s][b][k][t] = (sum + error)[s][t][b][k] / K_primaries of the source's job: a 32 x 32
+// tile of (bin, cell) per block, read along cells and written along bins through shared
+// memory.  Block (0, 0, 0) also normalises the late energy (one job).
+constexpr int FIN_TILE = 32;
+
+__global__ void __launch_bounds__(FIN_TILE * 8) k_finalize(TraceWork w)
 {
-    const unsigned long long per_src = (unsigned long long)w.k.B * w.k.K * w.k.T;
-    const unsigned long long n = (unsigned long long)w.k.S * per_src;
-    float *Hg = w.H + (unsigned long long)w.src_base * per_src;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const int gs = w.src_base + (int)(i / per_src);
+    __shared__ float tile[FIN_TILE][FIN_TILE + 1];
+    const int BK = w.k.B * w.k.K, T = w.k.T;
+    const int t0 = blockIdx.x * FIN_TILE, c0 = blockIdx.y * FIN_TILE;
+    const int tx = threadIdx.x & (FIN_TILE - 1), ty = threadIdx.x / FIN_TILE;
+    const unsigned long long src_cells = (unsigned long long)BK * T;
+    for (int s = blockIdx.z; s < w.k.S; s += gridDim.z) {
+        const int gs = w.src_base + s;
         const unsigned long long kp = w.njobs > 1 ? w.js[w.src_job[gs]].primaries : w.js[0].primaries;
-        Hg[i] = kp > 0 ? (w.Hs[i] + w.He[i]) / (float)kp : 0.f;
+        const float *hs = w.Hs + (unsigned long long)s * src_cells;
+        const float *he = w.He + (unsigned long long)s * src_cells;
+        __syncthreads();  // the previous source's tile has been written out
+        for (int r = ty; r < FIN_TILE; r += 8) {  // r: bin within the tile, tx: cell
+            const int t = t0 + r, c = c0 + tx;
+            float v = 0.f;
+            if (t < T && c < BK && kp > 0) {
+                const unsigned long long i = (unsigned long long)t * BK + c;
+                v = (hs[i] + he[i]) / (float)kp;
+            }
+            tile[r][tx] = v;
+        }
+        __syncthreads();
+        float *Hg = w.H + ((unsigned long long)gs * BK) * T;
+        for (int r = ty; r < FIN_TILE; r += 8) {  // r: cell within the tile, tx: bin
+            const int c = c0 + r, t = t0 + tx;
+            if (t < T && c < BK) Hg[(unsigned long long)c * T + t] = tile[tx][r];
+        }
     }
-    if (w.njobs == 1 && blockIdx.x == 0 && threadIdx.x < w.k.B && w.js[0].primaries > 0)
+    if (w.njobs == 1 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < w.k.B &&
+        w.js[0].primaries > 0)
         w.stats->late[threadIdx.x] /= (double)w.js[0].primaries;
 }
 
@@ -332,10 +355,9 @@ void launch_accum(const TraceWork &w, int first_chunk, unsigned long long chunk,
 
 void launch_finalize(const TraceWork &w, cudaStream_t st)
 {
-    const unsigned long long n = (unsigned long long)w.k.S * w.k.B * w.k.K * w.k.T;
-    const unsigned long long nb = (n + 255) / 256;
-    const int blocks = (int)(nb < 4096ull ? nb : 4096ull);
-    k_finalize<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(w);
+    const int BK = w.k.B * w.k.K;
+    const dim3 grid((w.k.T + FIN_TILE - 1) / FIN_TILE, (BK + FIN_TILE - 1) / FIN_TILE, std::min(w.k.S, 65535));
+    if (w.k.S > 0) k_finalize<<<grid, FIN_TILE * 8, 0, st>>>(w);
     if (w.k.min_order == 0 && w.direct) {
         const int m = w.k.S * w.k.B * w.k.K;
         k_direct_add<<<(m + 255) / 256, 256, 0, st>>>(w);

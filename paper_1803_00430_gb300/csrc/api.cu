@@ -53,39 +53,6 @@ void free_buf(Buf &b)
     b.bytes = 0;
 }
 
-cudaEvent_t get_event(rp_ctx *c)
-{
-    if (!c->free_events.empty()) {
-        cudaEvent_t e = c->free_events.back();
-        c->free_events.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-}
-
-struct ProfScope {
-    rp_ctx *c;
-    const char *name;
-    cudaEvent_t a = nullptr;
-    ProfScope(rp_ctx *c_, const char *n) : c(c_), name(n)
-    {
-        if (c->prof) {
-            a = get_event(c);
-            cudaEventRecord(a, c->stream);
-        }
-    }
-    ~ProfScope()
-    {
-        if (c->prof && a) {
-            cudaEvent_t b = get_event(c);
-            cudaEventRecord(b, c->stream);
-            c->pending.push_back({name, a, b});
-        }
-    }
-};
-
 void prof_collect(rp_ctx *c)
 {
     if (c->pending.empty()) return;

@@ -11,6 +11,10 @@
 //   network    in -> [GELU(W x + b)] x layers -> W x + b; weights W[in][out]
 //   loss       masked mean squared error on standardised targets
 //
+// Forward pass: one fused launch on the tcgen05 tensor cores (mlp_tc.cu: TMA-staged
+// operands, TMEM accumulators, bias / GELU epilogue, all layers per 128-sample tile)
+// where the shape allows it (hidden width a multiple of 64 up to 256, output width a
+// multiple of 16); otherwise, and for the backward pass, the GEMM below.
 // GEMM: 64x64 block tile, 4 warps of 32x32, K-steps of 32 staged in shared memory
 // (row stride 40 bf16: the fragment loads are bank-conflict free), mma.sync
 // m16n8k16 BF16 -> FP32, epilogues fused: +bias, +bias then GELU (keeping the
@@ -23,6 +27,7 @@
 #include <vector>
 
 #include "handles.cuh"
+#include "mlp_tc.cuh"
 
 using namespace rp;
 
@@ -302,6 +307,22 @@ __global__ void k_to_bf16_weights(long long count, const float *__restrict__ p, 
     }
 }
 
+// BF16 weights transposed for the tensor-core forward pass: wt[o][i] = w[i][o] of one layer
+__global__ void k_transpose_w(int in, int out, const bf16 *__restrict__ w, bf16 *__restrict__ wt)
+{
+    __shared__ bf16 tile[32][33];
+    const int i0 = blockIdx.x * 32, o0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = i0 + r, o = o0 + threadIdx.x;
+        if (i < in && o < out) tile[r][threadIdx.x] = w[(size_t)i * out + o];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int o = o0 + r, i = i0 + threadIdx.x;
+        if (i < in && o < out) wt[(size_t)o * in + i] = tile[threadIdx.x][r];
+    }
+}
+
 // uniform(-a, a) initialisation of weights (a = sqrt(6 / (in + out))), zero biases
 __global__ void k_init(long long count, float *__restrict__ p, const float *__restrict__ scale, unsigned long long seed)
 {
@@ -425,6 +446,11 @@ struct rp_mlp {
     std::vector<int> in_of, out_of;
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 masters, gradients, moments
     bf16 *pb = nullptr;                                           // BF16 weights
+    bf16 *wt = nullptr;                                           // BF16 weights transposed, [out][in] per layer
+    bool use_tc = false;                                          // forward pass on the tcgen05 tensor cores
+    TcForwardParams tc;                                           // its weight tensor maps and layer shapes
+    const void *tc_x = nullptr;                                   // input whose map tc.xmap holds
+    int tc_n = 0;
     long long *wmap = nullptr;                                    // master index -> bf16 index or -1
     float *in_mean = nullptr, *in_istd = nullptr, *out_mean = nullptr, *out_std = nullptr;
     float *Z = nullptr, *Y = nullptr, *scratch = nullptr;         // workspace for max_batch
@@ -448,13 +474,47 @@ int mrc(cudaError_t e)
         if (e_ != cudaSuccess) return mrc(e_);   \
     } while (0)
 
-// forward pass; keeps pre-activations Z[l] (f32) and activations Act[l] (bf16)
-void forward(rp_mlp *mp, const bf16 *X, int n, cudaStream_t st)
+// the transposed BF16 weights of every layer, from the BF16 weights
+void refresh_transposed(rp_mlp *mp, cudaStream_t st)
+{
+    if (!mp->use_tc) return;
+    for (size_t l = 0; l < mp->in_of.size(); ++l) {
+        const int in = mp->in_of[l], out = mp->out_of[l];
+        k_transpose_w<<<dim3((in + 31) / 32, (out + 31) / 32), dim3(32, 8), 0, st>>>(in, out, mp->pb + mp->wb_off[l],
+                                                                                    mp->wt + mp->wb_off[l]);
+    }
+}
+
+// forward pass; with `keep` (training) it keeps the pre-activations Z[l] (f32) and the
+// activations Act[l] (bf16) for the backward pass
+void forward(rp_mlp *mp, const bf16 *X, int n, cudaStream_t st, bool keep = true)
 {
     const rp_mlp_config &c = mp->cfg;
     const int L = c.layers, H = c.hidden;
+    if (mp->use_tc) {
+        TcForwardParams p = mp->tc;
+        p.n = n;
+        p.Y = mp->Y;
+        p.Z = keep ? mp->Z : nullptr;
+        p.Act = keep ? mp->Act : nullptr;
+        p.act_stride = (long long)c.max_batch * H;
+        p.status = mp->ctx->d_status;
+        bool ok = true;
+        if (X != mp->tc_x || n != mp->tc_n) {  // the input's tensor map, re-made when it changes
+            ok = tc_encode_map(&mp->tc.xmap, X, n, c.in_dim, TC_TILE_ROWS);
+            mp->tc_x = ok ? X : nullptr;
+            mp->tc_n = ok ? n : 0;
+            p.xmap = mp->tc.xmap;
+        }
+        if (ok) {
+            ProfScope ps(mp->ctx, "mlp_forward_tc");
+            if (mlp_forward_tc(p, st) == cudaSuccess) return;
+        }
+        mp->use_tc = false;  // the maps could not be made for this input: the GEMM path from now on
+    }
     const bf16 *in = X;
     int width = c.in_dim;
+    ProfScope ps(mp->ctx, "mlp_forward_gemm");
     for (int l = 0; l < L; ++l) {
         float *Zl = mp->Z + (size_t)l * c.max_batch * H;
         bf16 *Al = mp->Act + (size_t)l * c.max_batch * H;
@@ -577,8 +637,24 @@ int rp_mlp_create(rp_ctx *ctx, const rp_mlp_config *cfg, rp_mlp **out)
         rc = mrc(e);
         goto fail;
     }
+    if (!(cfg->flags & RP_MLP_FLAG_LEGACY_GEMM) && mlp_tc_supported(cfg->in_dim, cfg->hidden, L, cfg->out_dim)) {
+        if ((e = cudaMalloc(&mp->wt, sizeof(bf16) * boff))) {
+            rc = mrc(e);
+            goto fail;
+        }
+        mp->use_tc = true;
+        mp->tc.nlayers = L + 1;
+        for (int l = 0; l <= L && mp->use_tc; ++l) {
+            mp->tc.kdim[l] = mp->in_of[l];
+            mp->tc.ndim[l] = mp->out_of[l];
+            mp->tc.bias[l] = mp->p + mp->b_off[l];
+            mp->use_tc = tc_encode_map(&mp->tc.wmap[l], mp->wt + mp->wb_off[l], mp->out_of[l], mp->in_of[l],
+                                       mp->out_of[l]);
+        }
+    }
     k_init<<<(int)blocks_for(off), 256>>>(off, mp->p, d_scale, cfg->seed);
     k_to_bf16_weights<<<(int)blocks_for(off), 256>>>(off, mp->p, mp->wmap, mp->pb);
+    refresh_transposed(mp, 0);
     if ((e = cudaDeviceSynchronize())) {
         rc = mrc(e);
         goto fail;
@@ -598,7 +674,7 @@ int rp_mlp_destroy(rp_mlp *mp)
     cudaSetDevice(mp->ctx->device);
     cudaStreamSynchronize(mp->ctx->stream);
     for (void *q : {(void *)mp->p, (void *)mp->g, (void *)mp->m, (void *)mp->v, (void *)mp->pb, (void *)mp->wmap,
-                    (void *)mp->in_mean, (void *)mp->in_istd, (void *)mp->out_mean, (void *)mp->out_std,
+                    (void *)mp->in_mean, (void *)mp->in_istd, (void *)mp->out_mean, (void *)mp->out_std, (void *)mp->wt,
                     (void *)mp->Z, (void *)mp->Act, (void *)mp->dA, (void *)mp->dB, (void *)mp->Y, (void *)mp->dY,
                     (void *)mp->part, (void *)mp->cpart, (void *)mp->scratch})
         cudaFree(q);
@@ -626,6 +702,7 @@ int rp_mlp_set_params(rp_mlp *mp, const float *params)
     cudaStream_t st = mp->ctx->stream;
     CKM(cudaMemcpyAsync(mp->p, params, sizeof(float) * mp->nparams, cudaMemcpyDeviceToDevice, st));
     k_to_bf16_weights<<<(int)blocks_for(mp->nparams), 256, 0, st>>>(mp->nparams, mp->p, mp->wmap, mp->pb);
+    refresh_transposed(mp, st);
     return mrc(cudaGetLastError());
 }
 
@@ -712,7 +789,7 @@ int rp_mlp_forward(rp_mlp *mp, const void *Xb, int32_t n, float *Y, int32_t dest
 {
     if (!mp || !Xb || !Y || n < 1 || n > mp->cfg.max_batch) return RP_ERR_INVALID_ARG;
     cudaStream_t st = mp->ctx->stream;
-    forward(mp, (const bf16 *)Xb, n, st);
+    forward(mp, (const bf16 *)Xb, n, st, false);
     const long long cnt = (long long)n * mp->cfg.out_dim;
     CKM(cudaMemcpyAsync(Y, mp->Y, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, st));
     if (destandardize)
@@ -744,6 +821,7 @@ int rp_mlp_train_step(rp_mlp *mp, const void *Xb, const float *Tg, const float *
     const float c1 = 1.0f - std::pow(b1, (float)mp->step), c2 = 1.0f - std::pow(b2, (float)mp->step);
     k_adamw<<<(int)blocks_for(mp->nparams), 256, 0, st>>>(mp->nparams, mp->p, mp->g, mp->m, mp->v, lr, b1, b2, eps,
                                                            weight_decay, c1, c2, mp->wmap, mp->pb);
+    refresh_transposed(mp, st);
     return mrc(cudaGetLastError());
 }
 

@@ -286,12 +286,14 @@ def mlp_flops_per_sample(in_dim: int = IN_DIM, hidden: int = 256, layers: int = 
 def mlp_throughput(ctx: rpr.Context, batches=(512, 4096, 16384, 65536), reps: int = 20, seed: int = 3) -> dict:
     """Achieved TFLOP/s of the network's forward pass and of a training step (forward,
     backward and AdamW; counted as 3 x the forward flops) at each batch size, from
-    CUDA events on the context's stream around `reps` back-to-back calls."""
+    CUDA events on the context's stream around `reps` back-to-back calls; plus the
+    forward pass on the mma.sync GEMMs (forward_legacy) for comparison."""
     import torch
     out = {}
     rng = np.random.default_rng(seed)
     for n in batches:
         mlp = rpr.MLP(ctx, in_dim=IN_DIM, out_dim=OUT_DIM, max_batch=n, seed=seed)
+        legacy = rpr.MLP(ctx, in_dim=IN_DIM, out_dim=OUT_DIM, max_batch=n, seed=seed, legacy_gemm=True)
         X = torch.tensor(rng.normal(size=(n, IN_DIM)), dtype=torch.float32, device="cuda")
         Xb = mlp.prepare(X)
         T = torch.tensor(rng.normal(size=(n, OUT_DIM)), dtype=torch.float32, device="cuda")
@@ -300,6 +302,7 @@ def mlp_throughput(ctx: rpr.Context, batches=(512, 4096, 16384, 65536), reps: in
         st = torch.cuda.current_stream()
         res = {}
         for name, fn in (("forward", lambda: mlp.forward(Xb, destandardize=False)),
+                         ("forward_legacy", lambda: legacy.forward(Xb, destandardize=False)),
                          ("train_step", lambda: mlp.train_step(Xb, T, M, 1e-4, 0.0, loss))):
             for _ in range(3):
                 fn()
@@ -313,8 +316,21 @@ def mlp_throughput(ctx: rpr.Context, batches=(512, 4096, 16384, 65536), reps: in
             ms = a.elapsed_time(b) / reps
             flops = mlp_flops_per_sample() * n * (3.0 if name == "train_step" else 1.0)
             res[name] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+            if name.startswith("forward"):
+                # the forward kernel(s) alone: events on the stream right around the launch
+                ctx.profile(True)
+                ctx.profile_reset()
+                for _ in range(reps):
+                    fn()
+                kt = ctx.profile_read()
+                ctx.profile(False)
+                key = "mlp_forward_gemm" if name == "forward_legacy" else "mlp_forward_tc"
+                if key in kt:
+                    kms = kt[key][1] / kt[key][0]
+                    res[name].update(kernel_ms=kms, kernel_tflops=mlp_flops_per_sample() * n / (kms * 1e-3) / 1e12)
         out[int(n)] = res
         mlp.close()
+        legacy.close()
     return out
 
 

@@ -35,6 +35,7 @@ RP_ERR = {v: k for k, v in STATUS.items()}
 RP_MEM_HOST, RP_MEM_DEVICE = 0, 1
 RP_FLAG_RAY_HASH, RP_FLAG_COUNT_VISITS, RP_FLAG_DEVICE_POSITIONS, RP_FLAG_FP32_PATHS = 1, 2, 4, 8
 RP_FLAG_SHADOW_PACKETS, RP_FLAG_SHADOW_LANES = 16, 32
+RP_MLP_FLAG_LEGACY_GEMM = 1
 
 
 class rp_mesh_desc(C.Structure):
@@ -104,7 +105,7 @@ class rp_batch_info(C.Structure):
 
 class rp_mlp_config(C.Structure):
     _fields_ = [("in_dim", C.c_int32), ("hidden", C.c_int32), ("layers", C.c_int32), ("out_dim", C.c_int32),
-                ("max_batch", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+                ("max_batch", C.c_int32), ("flags", C.c_int32), ("seed", C.c_uint64)]
 
 
 class rp_debug_limits(C.Structure):
@@ -599,10 +600,12 @@ def mlp_features(ctx: Context, H, scene_feats, ir_rate_hz: float, in_dim: int = 
 class MLP:
     """rp_mlp: the learned estimator (BF16 tensor-core GEMMs, FP32 masters, AdamW)."""
 
-    def __init__(self, ctx: Context, in_dim=528, hidden=256, layers=3, out_dim=16, max_batch=4096, seed=1):
+    def __init__(self, ctx: Context, in_dim=528, hidden=256, layers=3, out_dim=16, max_batch=4096, seed=1,
+                 legacy_gemm: bool = False):
         self.ctx = ctx
         self.lib = ctx.lib
-        self.cfg = rp_mlp_config(in_dim, hidden, layers, out_dim, max_batch, 0, seed)
+        self.cfg = rp_mlp_config(in_dim, hidden, layers, out_dim, max_batch,
+                                 RP_MLP_FLAG_LEGACY_GEMM if legacy_gemm else 0, seed)
         h = C.c_void_p()
         check(self.lib.rp_mlp_create(ctx.h, C.byref(self.cfg), C.byref(h)), "rp_mlp_create")
         self.h = h

@@ -194,3 +194,49 @@ def test_learned_estimator_gains_over_plain(ctx):
     assert hist[-1][1] < 0.5 * hist[0][1]
     assert ev["rt_err_mean_net"] < ev["rt_err_mean_plain"]
     assert ev["rt_err_p95_net"] < ev["rt_err_p95_plain"]
+
+
+@pytest.mark.parametrize("n", [1, 100, 128, 300, 4097])
+def test_tensor_core_forward_matches_gemm_forward_and_oracle(ctx, n):
+    """The fused tcgen05 forward pass (TMA-staged operands, TMEM accumulators, one
+    launch for all layers) against the mma.sync GEMM path on the same weights and
+    inputs, and against the FP64 oracle; ragged batches (1, a partial 128-sample tile,
+    a tile and a tail) and the 528-wide input's partial last K-chunk."""
+    rng = np.random.default_rng(100 + n)
+    tc = rpr.MLP(ctx, max_batch=max(n, 256), seed=21)
+    ref = rpr.MLP(ctx, max_batch=max(n, 256), seed=22, legacy_gemm=True)
+    ref.set_params(tc.params())
+    X = torch.tensor(rng.normal(size=(n, DIN)), dtype=torch.float32, device="cuda")
+    Xb = tc.prepare(X)
+    Yt = tc.forward(Xb, destandardize=False).double().cpu().numpy()
+    Yr = ref.forward(Xb, destandardize=False).double().cpu().numpy()
+    assert np.isfinite(Yt).all()
+    rel = np.linalg.norm(Yt - Yr) / np.linalg.norm(Yr)
+    # same BF16 activations up to FP32 accumulation order (a rounding flip of a BF16
+    # activation moves the output by about 2^-9 of one term)
+    assert rel < 2e-3, rel
+    Po = _oracle_params(tc, tc.params())
+    Yo = oracle.mlp_forward(Po, Xb.double().cpu().numpy(), DIN, DH, NH, DOUT)
+    assert np.linalg.norm(Yt - Yo) / np.linalg.norm(Yo) < 1e-2
+    assert ctx.sync_status() == 0
+
+
+def test_tensor_core_forward_keeps_training_state(ctx):
+    """Training runs the tcgen05 forward pass with the pre-activations and BF16
+    activations kept for the backward pass: gradients equal the GEMM path's."""
+    n = 700
+    rng = np.random.default_rng(7)
+    tc = rpr.MLP(ctx, max_batch=n, seed=31)
+    ref = rpr.MLP(ctx, max_batch=n, seed=32, legacy_gemm=True)
+    ref.set_params(tc.params())
+    X = torch.tensor(rng.normal(size=(n, DIN)), dtype=torch.float32, device="cuda")
+    Xb = tc.prepare(X)
+    T = torch.tensor(rng.normal(size=(n, DOUT)), dtype=torch.float32, device="cuda")
+    M = torch.ones((n, DOUT), dtype=torch.float32, device="cuda")
+    lt, gt = tc.loss_grad(Xb, T, M)
+    lr, gr = ref.loss_grad(Xb, T, M)
+    gt, gr = gt.double().cpu().numpy(), gr.double().cpu().numpy()
+    assert float(lt.item()) == pytest.approx(float(lr.item()), rel=1e-3)
+    cos = float(gt @ gr / (np.linalg.norm(gt) * np.linalg.norm(gr)))
+    assert cos >= 0.9999, cos
+    assert np.linalg.norm(gt - gr) / np.linalg.norm(gr) < 1e-2
