@@ -120,6 +120,7 @@ typedef struct {
     float bounds_hi[3];
     float ray_epsilon;     /* t_min used by every ray */
     float build_ms;        /* device time of the BVH build */
+    float refit_ms;        /* device time of the last rp_scene_refit's refit launch (0: none) */
 } rp_scene_info;
 
 /* One trace step (Section 5): num_rays primaries from the listener, each followed to
@@ -241,6 +242,20 @@ int rp_set_stream(rp_ctx *ctx, void *cuda_stream);
  * of range RP_ERR_INVALID_ARG.  Synchronises the stream before returning. */
 int rp_scene_create(rp_ctx *ctx, const rp_mesh_desc *mesh, rp_scene **out);
 int rp_scene_destroy(rp_scene *scene);
+
+/* Dynamic scenes (Section 6: the benchmark scenes have moving objects; the method is
+ * built for interactive propagation in dynamic scenes): new positions for the
+ * vertices of an existing scene -- same triangles, materials and vertex count.
+ * verts [num_verts][3] metres in the memory named by `memory`, copied.  The BVH keeps
+ * its tree and every box is recomputed bottom-up on the device (one launch); the
+ * scene bounds, the box padding and the self-intersection guard t_min (when the mesh
+ * gave ray_epsilon = 0) are derived from the new positions as a build derives them,
+ * so every query answers as it would on a scene built from the moved mesh (the tree
+ * decides only the speed).  Large motions make sibling boxes overlap and traversal
+ * slower: rebuild with rp_scene_create then.  Non-finite vertices give
+ * RP_ERR_NAN_INPUT and leave the scene unchanged; a wrong vertex count gives
+ * RP_ERR_INVALID_ARG.  Synchronises the context stream. */
+int rp_scene_refit(rp_scene *scene, const float *verts, int32_t num_verts, int32_t memory);
 int rp_scene_info_get(const rp_scene *scene, rp_scene_info *out);
 
 /* Reserve the workspace one rp_trace of these sizes needs, so that later calls
@@ -277,6 +292,76 @@ int rp_update(rp_scene *scene, const rp_trace_params *params,
               const rp_estimate_params *est, const float *listener, const float *sources,
               int32_t num_sources, float *H_host, rp_reverb_params *params_host,
               rp_direct *direct_host, rp_trace_stats *stats_host, double *state_host);
+
+/* ---------------------------------------------------------------------------
+ * Temporal coherence (Section 5, "Sound Propagation"): the early reflections (the
+ * first orders; the paper uses 2) go to a diffuse path cache with spherical-harmonic
+ * directivity per path, smoothed over updates (tau_ER = 1 s in the paper); the N_ER
+ * most intense early paths (100 among all sources) are rendered and the others are
+ * added to the late IR before it is analysed; the late IR itself is smoothed by an
+ * impulse response cache (tau_LR = 3 s).
+ * --------------------------------------------------------------------------- */
+typedef struct rp_er_cache rp_er_cache;
+
+/* One early path: the diffuse-rain contributions of this cache's source through the
+ * same reflections, summed (reading of the paper's diffuse path cache):
+ * energy[b] = sum of e_b / K, sh[b][k] = sum of e_b Y_k(d0) / K (d0: each
+ * contribution's arrival direction, its path's first segment), delay = the
+ * energy-weighted mean arrival time; K = primaries of the update. */
+typedef struct {
+    int32_t source;
+    int32_t order;                          /* 1 or 2 */
+    int32_t tri[2];                         /* input triangle of reflections 1 and 2 (-1: none) */
+    double delay_s;
+    double energy[RP_MAX_BANDS];            /* per unit source power, b < B */
+    double sh[RP_MAX_BANDS][RP_MAX_SH];     /* b < B, k < K */
+} rp_er_path;
+
+typedef struct {
+    double dt_update;          /* seconds since the previous update */
+    double tau_er;             /* smoothing time constant of the path cache (paper: 1 s); 0: none */
+    double prune;              /* cached paths whose total energy falls to this or below are dropped */
+    double hearing_threshold;  /* paths whose total energy is at or below this are not rendered
+                                  (the listener's threshold of hearing, per unit source power) */
+    int32_t n_er;              /* paths rendered per update among all sources (paper: 100) */
+    int32_t reserved;
+} rp_er_params;
+
+/* A path cache for num_bands bands and SH order sh_order (owned by the caller until
+ * rp_er_cache_destroy; its device arrays grow as the cache does). */
+int rp_er_cache_create(rp_ctx *ctx, int32_t num_bands, int32_t sh_order, rp_er_cache **out);
+int rp_er_cache_destroy(rp_er_cache *cache);
+/* Forget every path: the next update starts the cache (alpha = 1). */
+int rp_er_cache_reset(rp_er_cache *cache);
+/* The cached paths in key order (source, triangle of reflection 1, of reflection 2,
+ * an order-1 path after the order-2 paths of its triangle) into device out[max_paths];
+ * *count (host) = paths in the cache. */
+int rp_er_cache_read(rp_er_cache *cache, rp_er_path *out, int64_t max_paths, int64_t *count);
+
+/* rp_trace with the early reflections kept apart (2 <= min_order <= 3: orders below
+ * min_order are early; at most 2):
+ *   1. the trace step as rp_trace: H holds orders >= min_order;
+ *   2. every early reflection's diffuse-rain shadow ray to every source; each visible
+ *      one is a contribution of the path (source, its reflections' triangles);
+ *   3. this update's paths, updated into the cache: energy and SH as
+ *      (1 - alpha) cached + alpha new, alpha = 1 - exp(-dt_update / tau_er) (1 on the
+ *      cache's first update), delay weighted by energy; paths pruned as ep->prune says;
+ *   4. the cached paths above the hearing threshold sorted by decreasing total energy
+ *      (ties in key order): the first n_er are written to `rendered` (device
+ *      rp_er_path[n_er]), their number to *num_rendered (device int32); the others are
+ *      added to H at bin floor(delay x ir_rate_hz) (dropped past the last bin).
+ * The cache's band count and SH order must match the scene and params; the scene
+ * must have fewer than 2^21 - 1 triangles and S < 4096.  Synchronises the stream
+ * (sizes are read back between the steps). */
+int rp_trace_er(rp_scene *scene, const rp_trace_params *params, const float *listener, const float *sources,
+                int32_t num_sources, float *H, rp_direct *direct, rp_trace_stats *stats, rp_er_cache *cache,
+                const rp_er_params *er, rp_er_path *rendered, int32_t *num_rendered);
+
+/* The impulse response cache of the late IR: C = (1 - alpha) C + alpha H over `count`
+ * cells (device float arrays), alpha = 1 - exp(-dt_update / tau) (paper: tau_LR =
+ * 3 s), or C = H when `first` is nonzero or tau = 0.  rp_estimate then runs on C. */
+int rp_ir_cache_update(rp_ctx *ctx, const float *H, float *C, int64_t count, double dt_update, double tau,
+                       int32_t first);
 
 /* ---------------------------------------------------------------------------
  * Batched updates: many independent scenes, each with its own sources, listener and

@@ -102,6 +102,9 @@ def _load():
         lib.orc_trace_ray_log.argtypes = [C.c_void_p, P(_TraceParams), dp, dp, C.c_int, C.c_uint64, dp, dp,
                                           ip, dp, dp, dp]
         lib.orc_trace_ray_log.restype = C.c_int
+        lib.orc_er_rays.argtypes = [C.c_void_p, P(_TraceParams), dp, dp, C.c_int, C.c_int64, C.c_int64, dp,
+                                    C.c_int64]
+        lib.orc_er_rays.restype = C.c_int64
         lib.orc_next_wave.argtypes = [C.c_int64, C.c_int, C.c_double]
         lib.orc_next_wave.restype = C.c_int64
         lib.orc_estimate.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
@@ -365,6 +368,168 @@ def trace_parallel(scene: OracleScene, p: TraceParams, listener, sources, thread
             if dd["visible"][s] and dd["bin"][s] < T:
                 H[s, :, :, int(dd["bin"][s])] += dd["sh"][s][None, :K]
     return H, stats_dict(st, B), hashes[:hash_cap]
+
+
+# ----------------------------------------------------------------------------
+# Temporal coherence (Section 5): the early-reflection diffuse path cache with SH
+# directivity per path, the prioritisation of early paths (the N_ER most intense are
+# rendered, the rest join the late IR), and the impulse-response cache of the late IR.
+# ----------------------------------------------------------------------------
+ER_REC = 30
+ER_NONE = -1  # triangle of reflection 2 of an order-1 path
+
+
+def er_records(scene: OracleScene, p: TraceParams, listener, sources, num_primaries: int) -> np.ndarray:
+    """Early-reflection contribution records [n, 30] of primaries first_ray ..
+    first_ray + num_primaries - 1 (the primaries of a trace step, refill waves
+    included): source, order, triangles of reflections 1 and 2, path length, ray id,
+    energy per band (not divided by the primaries), SH basis of the arrival direction.
+    Paths are followed with the trace step's random numbers to order min_order - 1."""
+    lib = _load()
+    lis, src = _src_arrays(listener, sources)
+    S = src.shape[0]
+    cp = p.c()
+    b0, b1 = int(p.first_ray), int(p.first_ray) + int(num_primaries)
+    cap = max(1, (b1 - b0) * 2 * max(S, 1))
+    rec = np.zeros((cap, ER_REC))
+    n = int(lib.orc_er_rays(scene._h, C.byref(cp), _d(lis), _d(src), S, b0, b1, _d(rec), cap))
+    assert n <= cap
+    return rec[:n]
+
+
+def er_paths(scene: OracleScene, p: TraceParams, listener, sources, num_primaries: int) -> dict:
+    """This update's early-reflection paths [reading of Section 5's diffuse path
+    cache]: the records with the same key (source, triangle of reflection 1, triangle
+    of reflection 2 or none) are one path.  Per path, over its records r, with K the
+    step's primaries:
+        energy[b] = sum_r e_r[b] / K
+        sh[b][k]  = sum_r e_r[b] Y_k(d0_r) / K     (directivity of the path)
+        delay     = sum_r E_r t_r / sum_r E_r,  E_r = sum_b e_r[b],  t_r = length_r / c
+    Paths sorted by key."""
+    rec = er_records(scene, p, listener, sources, num_primaries)
+    B = scene.B
+    K = (p.sh_order + 1) ** 2
+    kp = float(num_primaries)
+    out = {"source": np.zeros(0, np.int64), "tri1": np.zeros(0, np.int64), "tri2": np.zeros(0, np.int64),
+           "order": np.zeros(0, np.int64), "energy": np.zeros((0, B)), "sh": np.zeros((0, B, K)),
+           "delay": np.zeros(0)}
+    if len(rec) == 0:
+        return out
+    keys = rec[:, [0, 2, 3]].astype(np.int64)
+    uniq, inv = np.unique(keys, axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+    n = len(uniq)
+    e = rec[:, 6:6 + B]
+    Y = rec[:, 14:14 + K]
+    E = np.zeros((n, B))
+    X = np.zeros((n, B, K))
+    np.add.at(E, inv, e)
+    np.add.at(X, inv, e[:, :, None] * Y[:, None, :])
+    etot = e.sum(axis=1)
+    t = rec[:, 4] / p.speed_of_sound
+    num = np.zeros(n)
+    den = np.zeros(n)
+    np.add.at(num, inv, etot * t)
+    np.add.at(den, inv, etot)
+    order = np.where(uniq[:, 2] == ER_NONE, 1, 2)
+    return {"source": uniq[:, 0], "tri1": uniq[:, 1], "tri2": uniq[:, 2], "order": order, "energy": E / kp,
+            "sh": X / kp, "delay": np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)}
+
+
+def smoothing_alpha(dt_update: float, tau: float, first: bool) -> float:
+    """alpha = 1 - exp(-dt / tau) of the exponential smoothing (Section 4.2's RT60
+    smoothing; Section 5 gives tau_ER = 1 s, tau_LR = 3 s); 1 on the first update or
+    without smoothing (tau = 0)."""
+    if first or tau <= 0.0:
+        return 1.0
+    return 1.0 - np.exp(-dt_update / tau)
+
+
+def er_cache_update(cache: dict | None, frame: dict, alpha: float, prune: float = 0.0) -> dict:
+    """The diffuse path cache [reading]: every key of the cache or of this update's
+    paths is kept with
+        energy = (1 - alpha) energy_cached + alpha energy_frame   (absent: zero)
+        sh     = (1 - alpha) sh_cached     + alpha sh_frame
+        delay  = energy-weighted mean of the two delays, weights (1 - alpha) E_cached
+                 and alpha E_frame (E = sum over bands)
+    and paths whose total energy falls to `prune` or below are dropped."""
+    if cache is None or len(cache["source"]) == 0:
+        keys = [("frame", i) for i in range(len(frame["source"]))]
+        src = {"frame": frame}
+        w = {"frame": alpha}
+    else:
+        src = {"cache": cache, "frame": frame}
+        w = {"cache": 1.0 - alpha, "frame": alpha}
+    table: dict = {}
+    for name, d in src.items():
+        for i in range(len(d["source"])):
+            k = (int(d["source"][i]), int(d["tri1"][i]), int(d["tri2"][i]))
+            ent = table.setdefault(k, [None, None])
+            ent[0 if name == "cache" else 1] = i
+    B = frame["energy"].shape[1] if len(frame["source"]) else cache["energy"].shape[1]
+    K = frame["sh"].shape[2] if len(frame["source"]) else cache["sh"].shape[2]
+    rows = []
+    for k in sorted(table):
+        ic, jf = table[k]
+        E = np.zeros(B)
+        X = np.zeros((B, K))
+        num = den = 0.0
+        for idx, name in ((ic, "cache"), (jf, "frame")):
+            if idx is None or name not in src:
+                continue
+            d, a = src[name], w[name]
+            E += a * d["energy"][idx]
+            X += a * d["sh"][idx]
+            et = a * d["energy"][idx].sum()
+            num += et * d["delay"][idx]
+            den += et
+        if E.sum() <= prune:
+            continue
+        rows.append((k, E, X, num / den if den > 0 else 0.0))
+    return {"source": np.array([r[0][0] for r in rows], np.int64), "tri1": np.array([r[0][1] for r in rows], np.int64),
+            "tri2": np.array([r[0][2] for r in rows], np.int64),
+            "order": np.array([1 if r[0][2] == ER_NONE else 2 for r in rows], np.int64),
+            "energy": np.array([r[1] for r in rows]).reshape(-1, B), "sh": np.array([r[2] for r in rows]).reshape(-1, B, K),
+            "delay": np.array([r[3] for r in rows])}
+
+
+def er_prioritize(cache: dict, n_er: int = 100, hearing_threshold: float = 0.0):
+    """Section 5's prioritisation: paths at or below the threshold of hearing (total
+    energy over bands, per unit source power) are discarded; the rest are sorted by
+    decreasing intensity (total energy; equal intensities by key) and the first
+    n_er among all sources are rendered.  Returns (rendered indices in that order,
+    indices of the other kept paths)."""
+    n = len(cache["source"])
+    if n == 0:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    inten = cache["energy"].sum(axis=1)
+    keep = np.nonzero(inten > hearing_threshold)[0]
+    order = sorted(keep.tolist(), key=lambda i: (-inten[i], int(cache["source"][i]), int(cache["tri1"][i]),
+                                                int(cache["tri2"][i])))
+    return np.array(order[:n_er], np.int64), np.array(sorted(order[n_er:]), np.int64)
+
+
+def er_spill(H, cache: dict, idx, ir_rate_hz: float) -> np.ndarray:
+    """Section 5: the early paths that are not rendered are added to the late IR
+    before it is analysed -- path i's SH energy sh[i] into bin floor(delay_i f_ir) of
+    its source (dropped past the last bin).  Returns the new H (a copy)."""
+    H = np.array(H, dtype=np.float64, copy=True)
+    T = H.shape[3]
+    for i in idx:
+        b = int(np.floor(cache["delay"][i] * ir_rate_hz))
+        if b < T:
+            H[int(cache["source"][i]), :, :, b] += cache["sh"][i]
+    return H
+
+
+def ir_cache_update(C_prev, L, alpha: float) -> np.ndarray:
+    """The impulse response cache of the late IR [reading of Section 5]: every cell of
+    the SH energy histogram smoothed exponentially, C = (1 - alpha) C_prev + alpha L
+    (C_prev ignored when alpha = 1)."""
+    L = np.asarray(L, dtype=np.float64)
+    if C_prev is None or alpha >= 1.0:
+        return L.copy()
+    return (1.0 - alpha) * np.asarray(C_prev, dtype=np.float64) + alpha * L
 
 
 def trace_ray_log(scene: OracleScene, p: TraceParams, listener, sources, rid: int) -> dict:

@@ -319,11 +319,23 @@ static int tri_hit(const orc_scene *sc, int t, const double o[3], const double d
     return orc_intersect_tri(o, d, sc->v + 3 * ix[0], sc->v + 3 * ix[1], sc->v + 3 * ix[2], th);
 }
 
-/* closest-hit candidate update: nearer t wins, equal t goes to the smaller triangle id [reading] */
+/* closest-hit candidate update: the nearer t wins; a t within ORC_TIE (relative) of the
+ * best is equal and goes to the smaller triangle id [reading].  Coplanar overlapping
+ * surfaces meet a ray at one mathematical distance, and the FP64 values computed from
+ * their different vertices differ only by rounding, so "equal" means equal up to it. */
+#define ORC_TIE 1e-9
 static void consider(int t, double th, double tmin, int exclude, int *best, double *best_t)
 {
     if (t == exclude || !(th > tmin)) return;
-    if (th < *best_t || (th == *best_t && *best >= 0 && t < *best)) {
+    if (*best < 0) {
+        if (th < *best_t) {
+            *best_t = th;
+            *best = t;
+        }
+        return;
+    }
+    const double tol = ORC_TIE * fabs(*best_t);
+    if (th < *best_t - tol || (th <= *best_t + tol && t < *best)) {
         *best_t = th;
         *best = t;
     }
@@ -480,11 +492,28 @@ typedef struct {
     int n;
 } orc_ray_log;
 
+/* Early-reflection paths (Section 5: the first orders go to the diffuse path cache,
+ * with spherical-harmonic directivity per path).  One record per visible diffuse-rain
+ * contribution of a reflection of order 1 .. min_order - 1:
+ *   [0] source, [1] order, [2] triangle of reflection 1, [3] triangle of reflection 2
+ *   (-1 for order 1), [4] path length to the listener through the source, [5] primary
+ *   ray id, [6 .. 14) energy per band (the contribution of the histogram's diffuse
+ *   rain, not divided by the number of primaries; zero past B), [14 .. 30) the SH
+ *   basis of the path's arrival direction (its first segment), zero past K */
+#define ORC_ER_REC 30
+typedef struct {
+    double *rec;
+    int64_t cap, n;
+} orc_er_sink;
+
 static void trace_ray(const orc_scene *sc, const orc_trace_params *p, const double lis[3],
                       const double *src, int S, uint64_t rid, double *H, double *st, uint64_t *hash_out,
-                      orc_ray_log *log)
+                      orc_ray_log *log, orc_er_sink *er)
 {
-    const int B = sc->B, K = (p->sh_order + 1) * (p->sh_order + 1), M = p->max_order;
+    const int B = sc->B, K = (p->sh_order + 1) * (p->sh_order + 1);
+    /* with an early-reflection sink only the early orders are followed */
+    const int M = er ? (p->max_order < p->min_order - 1 ? p->max_order : p->min_order - 1) : p->max_order;
+    int seq[2] = { -1, -1 };
     uint32_t r[4];
     /* primary direction uniform on the sphere from bounce-0 draws [reading] */
     draw(rid, p->scene_id, 0u, p->seed, r);
@@ -539,6 +568,7 @@ static void trace_ray(const orc_scene *sc, const orc_trace_params *p, const doub
             break;
         }
         Lpath += t;
+        if (h <= 2) seq[h - 1] = tri;
         double hp[3] = { o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2] };
         st[ST_MFP_SUM] += t;
         st[ST_MFP_CNT] += 1.0;
@@ -576,6 +606,30 @@ static void trace_ray(const orc_scene *sc, const orc_trace_params *p, const doub
                 double e[ORC_MAXB];
                 for (int b = 0; b < B; ++b) e[b] = w[b] * sc_b[b] * cs / (ORC_PI * dist * dist);
                 add_contrib(p, B, K, s, e, Lpath + dist, Y, H, st);
+            }
+        } else if (er && h <= 2) {
+            /* an early reflection: the same diffuse rain, kept as a path record keyed
+             * by the source and the reflections' triangles */
+            for (int s = 0; s < S; ++s) {
+                double v[3];
+                sub3(src + 3 * s, hp, v);
+                double dist = sqrt(dot3(v, v));
+                double cs = dot3(n, v) / dist;
+                if (!(cs > 0.0)) continue;
+                double dir[3] = { v[0] / dist, v[1] / dist, v[2] / dist };
+                if (orc_any_hit(sc, hp, dir, sc->tmin, dist, tri)) continue;
+                if (er->n < er->cap) {
+                    double *q = er->rec + (size_t)er->n * ORC_ER_REC;
+                    q[0] = s;
+                    q[1] = h;
+                    q[2] = seq[0];
+                    q[3] = h >= 2 ? seq[1] : -1.0;
+                    q[4] = Lpath + dist;
+                    q[5] = (double)rid;
+                    for (int b = 0; b < ORC_MAXB; ++b) q[6 + b] = b < B ? w[b] * sc_b[b] * cs / (ORC_PI * dist * dist) : 0.0;
+                    for (int k = 0; k < ORC_MAXK; ++k) q[14 + k] = k < K ? Y[k] : 0.0;
+                }
+                er->n++;
             }
         }
         if (h == M) {
@@ -620,7 +674,24 @@ void orc_trace_rays(const orc_scene *sc, const orc_trace_params *p, const double
                     double *st, uint64_t *ray_hash)
 {
     for (int64_t r = ray_begin; r < ray_end; ++r)
-        trace_ray(sc, p, lis, src, S, (uint64_t)r, H_raw, st, ray_hash ? &ray_hash[r - ray_begin] : NULL, NULL);
+        trace_ray(sc, p, lis, src, S, (uint64_t)r, H_raw, st, ray_hash ? &ray_hash[r - ray_begin] : NULL, NULL, NULL);
+}
+
+/* Early-reflection path records (ORC_ER_REC doubles each) of primaries
+ * [ray_begin, ray_end): each path followed to order min_order - 1 (at most 2) with the
+ * random numbers of the full trace.  Writes at most cap records; returns how many
+ * there are. */
+int64_t orc_er_rays(const orc_scene *sc, const orc_trace_params *p, const double lis[3], const double *src, int S,
+                    int64_t ray_begin, int64_t ray_end, double *rec, int64_t cap)
+{
+    const int B = sc->B, K = (p->sh_order + 1) * (p->sh_order + 1);
+    double st[ST_COUNT];
+    double Hd[ORC_MAXB * ORC_MAXK];  /* never written: no order reaches min_order */
+    orc_er_sink er = { rec, cap, 0 };
+    (void)B;
+    (void)K;
+    for (int64_t r = ray_begin; r < ray_end; ++r) trace_ray(sc, p, lis, src, S, (uint64_t)r, Hd, st, NULL, NULL, &er);
+    return er.n;
 }
 
 /* Debug: the segments of primary ray `rid` (at most max_order entries); returns
@@ -629,7 +700,7 @@ int orc_trace_ray_log(const orc_scene *sc, const orc_trace_params *p, const doub
                       int S, uint64_t rid, double *H_raw, double *st, int *tri, double *t, double *o, double *d)
 {
     orc_ray_log log = { tri, t, o, d, 0 };
-    trace_ray(sc, p, lis, src, S, rid, H_raw, st, NULL, &log);
+    trace_ray(sc, p, lis, src, S, rid, H_raw, st, NULL, &log, NULL);
     return log.n;
 }
 
@@ -686,7 +757,7 @@ int orc_trace(const orc_scene *sc, const orc_trace_params *p, const double lis[3
         for (int64_t r = begin; r < begin + count; ++r) {
             const int64_t hi = r - p->first_ray;
             uint64_t *hp = (ray_hash && hi >= 0 && hi < hash_cap) ? &ray_hash[hi] : NULL;
-            trace_ray(sc, p, lis, src, S, (uint64_t)r, H, st, hp, NULL);
+            trace_ray(sc, p, lis, src, S, (uint64_t)r, H, st, hp, NULL, NULL);
         }
         begin += count;
         waves++;

@@ -340,6 +340,8 @@ int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
     sc->num_nodes = nt - 1;
     sc->num_mats = nm;
     sc->B = B;
+    sc->num_verts = nv;
+    sc->ray_eps = m->ray_epsilon;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     BvhBuildArgs a;
     BvhOut o;
@@ -367,7 +369,12 @@ int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
         (err = cudaMalloc(&sc->scat, sizeof(float) * nm * B)) != cudaSuccess ||
         (err = cudaMalloc(&sc->wdiff, sizeof(float) * nm * B)) != cudaSuccess ||
         (err = cudaMalloc(&sc->wspec, sizeof(float) * nm * B)) != cudaSuccess ||
-        (err = cudaMalloc(&sc->thr, sizeof(uint32_t) * nm)) != cudaSuccess) {
+        (err = cudaMalloc(&sc->thr, sizeof(uint32_t) * nm)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->vidx, sizeof(int32_t) * 3 * (size_t)nt)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->pleaf, sizeof(int) * (size_t)nt)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->pint, sizeof(int) * (size_t)std::max(nt - 1, 1))) != cudaSuccess ||
+        (err = cudaMemcpyAsync(sc->vidx, dt, sizeof(int32_t) * 3 * (size_t)nt, cudaMemcpyDeviceToDevice,
+                               c->stream)) != cudaSuccess) {
         rc = cuda_status(err);
         goto fail;
     }
@@ -379,6 +386,8 @@ int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
     o.wdiff = sc->wdiff;
     o.wspec = sc->wspec;
     o.thr = sc->thr;
+    o.pleaf = sc->pleaf;
+    o.pint = sc->pint;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
@@ -424,6 +433,9 @@ int rp_scene_destroy(rp_scene *sc)
     cudaFree(sc->wdiff);
     cudaFree(sc->wspec);
     cudaFree(sc->thr);
+    cudaFree(sc->vidx);
+    cudaFree(sc->pleaf);
+    cudaFree(sc->pint);
     delete sc;
     return RP_OK;
 }
@@ -441,6 +453,7 @@ int rp_scene_info_get(const rp_scene *sc, rp_scene_info *out)
     }
     out->ray_epsilon = sc->tmin;
     out->build_ms = sc->build_ms;
+    out->refit_ms = sc->refit_ms;
     return RP_OK;
 }
 
@@ -452,8 +465,13 @@ int rp_trace_reserve(rp_scene *sc, const rp_trace_params *p, int32_t S)
     return reserve(sc->ctx, trace_sizes(sc, p, S), sc->B, 1, S, 1);
 }
 
-int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, const float *sources, int32_t S,
-             float *H, rp_direct *direct, rp_trace_stats *stats, uint64_t *ray_hash)
+}  // extern "C"
+
+// The trace step of rp_trace, optionally keeping early reflections (rp_trace_er);
+// *work_out receives the step's bindings (device counters, positions, job state).
+int rp::trace_enqueue(rp_scene *sc, const rp_trace_params *p, const float *listener, const float *sources, int32_t S,
+                      float *H, rp_direct *direct, rp_trace_stats *stats, uint64_t *ray_hash, const EarlyHits *early,
+                      TraceWork *work_out)
 {
     int rc = check_params(sc, p, S);
     if (rc) return rc;
@@ -528,9 +546,22 @@ int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, cons
     L.exact_blocks = c->num_sms * 2;
     L.flat_blocks = c->num_sms * 8;
     L.acc_blocks = (int)std::max(1ll, std::min<long long>(((long long)z.keys + 7) / 8, (long long)c->num_sms * 8));
+    if (early) {
+        L.w.er = *early;
+        w.er = *early;
+    }
     CK(enqueue_step(L, st, prof_hook, c));
     if (stats) CK(cudaMemcpyAsync(stats, w.stats, sizeof(rp_trace_stats), cudaMemcpyDeviceToDevice, st));
+    if (work_out) *work_out = w;
     return RP_OK;
+}
+
+extern "C" {
+
+int rp_trace(rp_scene *sc, const rp_trace_params *p, const float *listener, const float *sources, int32_t S,
+             float *H, rp_direct *direct, rp_trace_stats *stats, uint64_t *ray_hash)
+{
+    return trace_enqueue(sc, p, listener, sources, S, H, direct, stats, ray_hash, nullptr, nullptr);
 }
 
 int rp_estimate(rp_ctx *c, const float *H, const rp_direct *direct, int32_t S, int32_t B, int32_t K, int32_t T,

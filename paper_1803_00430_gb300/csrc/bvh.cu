@@ -543,6 +543,9 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
             k_pack_nodes<<<(nt - 1 + 255) / 256, 256, 0, st>>>(nt, v0, blo, bhi, child, nlo, nhi, pad,
                                                               out.nodes);
         k_pack_tris<<<nblk_tri, 256, 0, st>>>(nt, v0, a.verts, a.tris, a.tri_mat, out.tris);
+        if (out.pleaf) RP_TRY(cudaMemcpyAsync(out.pleaf, pleaf, sizeof(int) * nt, cudaMemcpyDeviceToDevice, st));
+        if (out.pint && nt > 1)
+            RP_TRY(cudaMemcpyAsync(out.pint, pint, sizeof(int) * (nt - 1), cudaMemcpyDeviceToDevice, st));
         k_materials<<<(a.nmat + 127) / 128, 128, 0, st>>>(a.alpha, a.scat, a.nmat, a.B, out.alpha, out.scat,
                                                           out.wdiff, out.wspec, out.thr, d_status);
         RP_TRY(cudaGetLastError());

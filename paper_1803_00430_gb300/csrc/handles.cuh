@@ -62,13 +62,24 @@ struct rp_ctx {
 
 struct rp_scene {
     rp_ctx *ctx = nullptr;
-    int num_tris = 0, num_nodes = 0, num_mats = 0, B = 0, max_depth = 0;
-    float tmin = 0.f, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, build_ms = 0.f;
+    int num_tris = 0, num_nodes = 0, num_mats = 0, B = 0, max_depth = 0, num_verts = 0;
+    float tmin = 0.f, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, build_ms = 0.f, refit_ms = 0.f;
+    float ray_eps = 0.f;             // the mesh's ray_epsilon (0: t_min follows the bounds)
+    int32_t *vidx = nullptr;         // [num_tris][3] vertex indices (input order), for refits
+    int *pleaf = nullptr, *pint = nullptr;  // parents of leaves and internal nodes (refits)
     double tmin_d = 0.0;
     float4 *nodes = nullptr, *tris = nullptr;
     float *alpha = nullptr, *scat = nullptr, *wdiff = nullptr, *wspec = nullptr;
     uint32_t *thr = nullptr;
 };
+
+namespace rp {
+// The trace step of rp_trace (api.cu), optionally keeping the early reflections for
+// rp_trace_er; *work_out (if given) receives the step's bindings.
+int trace_enqueue(rp_scene *sc, const rp_trace_params *p, const float *listener, const float *sources, int32_t S,
+                  float *H, rp_direct *direct, rp_trace_stats *stats, uint64_t *ray_hash, const EarlyHits *early,
+                  TraceWork *work_out);
+}  // namespace rp
 
 // the device view of a scene that a trace step uses
 inline rp::SceneView make_view(const rp_scene *sc)

@@ -91,7 +91,8 @@ struct TraceCounters {
     unsigned long long total_hits;  // stored reflections of the step (sum over jobs)
     // planned refill: candidate rays still needed (0 = planned), primaries and waves
     unsigned long long plan_need, plan_rays, plan_waves;
-    unsigned long long pad[3];
+    unsigned long long n_er;  // early reflections stored (rp_trace_er)
+    unsigned long long pad[2];
 };
 
 // Contribution records: key = (global source - first source of the group) * T + bin,
@@ -111,6 +112,15 @@ struct Hits {
     float *ws;      // [j * B + b] path weight after absorption times s_b
     uint32_t *rid;  // primary ray id
     unsigned long long cap;
+};
+
+// Early reflections (orders 1 .. min_order - 1, at most 2) kept for the early-path
+// cache of rp_trace_er: the reflection as in Hits, and the leaf triangle of the path's
+// previous reflection (-1 for order 1).  cap = 0: not kept (every other step).
+struct EarlyHits {
+    Hits hits = {nullptr, nullptr, nullptr, nullptr, nullptr, 0ull};
+    int *prev = nullptr;
+    unsigned long long cap = 0ull;
 };
 
 struct TraceConsts {
@@ -142,6 +152,8 @@ struct BvhOut {
     double tmin_d;
     float lo[3], hi[3];
     int max_depth;
+    int *pleaf = nullptr;  // if set: [nt] parent node of each leaf (Morton order), kept for refits
+    int *pint = nullptr;   // if set: [nt - 1] parent node of each internal node (-1: the root)
 };
 
 // Builds the BVH; all temporaries are allocated and freed inside.  Returns a
@@ -226,6 +238,7 @@ struct TraceWork {
     int shadow_packets;  // 1: shadow rays as warp packets, 0: one ray per lane
     Hits shits;        // point, normal, weights and ray id of the reflections in that order (shadow
                        // rays read these; the FP64 residuals stay in `hits`, found through horder.perm)
+    EarlyHits er;      // early reflections (single-job steps of rp_trace_er only)
 };
 
 void launch_setup(const TraceWork &w, int wave, cudaStream_t st);

@@ -5,7 +5,7 @@
 //
 // CTA of 18 warps, one 128-sample tile:
 //   warp 16 (one lane)  producer: TMA of the weight K-chunks of every layer (and of the
-//                       input tile's K-chunks for layer 0) into a two-stage ring;
+//                       input tile's K-chunks for layer 0) into a three-stage ring;
 //   warp 17 (one lane)  MMA issuer: per 64-wide K-chunk four tcgen05.mma of K = 16
 //                       (M = 128, N = layer width), accumulating in TMEM; commits free
 //                       the ring stages and, after a layer's last chunk, signal the
@@ -37,7 +37,7 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TC_M = 128;           // samples per CTA (TMEM lanes)
 constexpr int TC_KC = 64;           // K elements per chunk: 128 bytes of BF16, one swizzle row
-constexpr int TC_NST = 2;           // ring stages
+constexpr int TC_NST = 3;           // ring stages
 constexpr int TC_EPI_WARPS = 16;   // four per TMEM lane quarter, a quarter of the columns each
 constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
 constexpr uint32_t TC_A_BYTES = TC_M * 128;         // one K-chunk of the 128-sample tile

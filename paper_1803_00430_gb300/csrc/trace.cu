@@ -641,21 +641,28 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     wgt[b * PATH_THREADS] *= (1.0f - a);
                 }
             }
-            if (!plan && h >= k.min_order && J.S > 0) {
+            // an early reflection (below min_order, order <= 2) is kept apart for the
+            // early-path cache when the step asks for it (rp_trace_er)
+            const bool early = !BATCH && w.er.cap > 0 && h < k.min_order && h <= 2;
+            if (!plan && (h >= k.min_order || early) && J.S > 0) {
+                const Hits &dst = early ? w.er.hits : w.hits;
+                const unsigned long long cap = early ? w.er.cap : J.hit_cap, off = early ? 0ull : J.hit_off;
                 const unsigned long long jl =
-                    BATCH ? warp_append_job(&w.js[job].n_hits, job) : warp_append(&w.js[0].n_hits);
-                if (jl < J.hit_cap && RP_IN_RANGE(J.hit_off + jl, w.hits.cap, w.status)) {
-                    const unsigned long long j = J.hit_off + jl;
+                    early ? warp_append(&w.ctr->n_er)
+                          : (BATCH ? warp_append_job(&w.js[job].n_hits, job) : warp_append(&w.js[0].n_hits));
+                if (jl < cap && RP_IN_RANGE(off + jl, dst.cap, w.status)) {
+                    const unsigned long long j = off + jl;
                     const float4 phi = make_float4((float)p.x, (float)p.y, (float)p.z, (float)L);
-                    w.hits.p[j] = phi;
-                    w.hits.plo[j] = make_float4((float)(p.x - (R)phi.x), (float)(p.y - (R)phi.y),
-                                                (float)(p.z - (R)phi.z), (float)(L - (R)phi.w));
-                    w.hits.n[j] = make_float4((float)n.x, (float)n.y, (float)n.z, __int_as_float(tri));
+                    dst.p[j] = phi;
+                    dst.plo[j] = make_float4((float)(p.x - (R)phi.x), (float)(p.y - (R)phi.y),
+                                             (float)(p.z - (R)phi.z), (float)(L - (R)phi.w));
+                    dst.n[j] = make_float4((float)n.x, (float)n.y, (float)n.z, __int_as_float(tri));
                     const float *sb = sc.scat + mat * B;
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b)
-                        if (b < B) w.hits.ws[j * B + b] = wgt[b * PATH_THREADS] * __ldg(sb + b);
-                    w.hits.rid[j] = rid;
+                        if (b < B) dst.ws[j * B + b] = wgt[b * PATH_THREADS] * __ldg(sb + b);
+                    dst.rid[j] = rid;
+                    if (early) w.er.prev[j] = prev;
                 } else {
                     raise_error(w.status, RP_ERR_CAPACITY);
                 }

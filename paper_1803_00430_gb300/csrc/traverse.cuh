@@ -9,7 +9,9 @@
 // (one column per thread, conflict-free) and the rest in a small per-thread array.
 //
 // Closest hit: the nearest t in (tmin, tmax); equal t goes to the smaller original
-// triangle index.  Any hit: some triangle with tmin < t < tmax.  The triangle
+// triangle index.  In the FP64 decision (traverse_exact) "equal" means within TIE_REL
+// (relative): coplanar overlapping surfaces meet a ray at one distance whose computed
+// values differ only by rounding.  Any hit: some triangle with tmin < t < tmax.  The triangle
 // `exclude` (leaf order) is skipped, which keeps a ray from re-hitting the surface
 // it leaves.  Triangle test: Moller-Trumbore, two-sided.
 //
@@ -30,6 +32,7 @@ constexpr int LOCAL_STACK = 40;
 constexpr int STACK_DEPTH = SMEM_STACK + LOCAL_STACK;
 constexpr float AMBIG_BARY = 2e-4f;
 constexpr float AMBIG_T = 2e-4f;
+constexpr double TIE_REL = 1e-9;  // FP64 closest-hit distances this close (relative) are equal
 
 struct TravStats {
     uint32_t nodes;
@@ -290,11 +293,12 @@ __device__ __noinline__ int traverse_exact(const SceneView &sc, D3 o, D3 d, doub
             }
             return false;
         }
-        if (t < best_t || (t == best_t && best >= 0 && orig < best_orig)) {
+        const double tol = best >= 0 ? TIE_REL * fabs(best_t) : 0.0;
+        if (best < 0 ? t < best_t : (t < best_t - tol || (t <= best_t + tol && orig < best_orig))) {
             best = tri;
             best_t = t;
             best_orig = orig;
-            bound = __double2float_ru(t);
+            bound = __double2float_ru(t * (1.0 + TIE_REL));  // a tied candidate just beyond t stays in reach
         }
         return false;
     });

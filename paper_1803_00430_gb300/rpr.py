@@ -48,7 +48,7 @@ class rp_mesh_desc(C.Structure):
 class rp_scene_info(C.Structure):
     _fields_ = [("num_tris", C.c_int32), ("num_nodes", C.c_int32), ("max_depth", C.c_int32),
                 ("num_bands", C.c_int32), ("bounds_lo", C.c_float * 3), ("bounds_hi", C.c_float * 3),
-                ("ray_epsilon", C.c_float), ("build_ms", C.c_float)]
+                ("ray_epsilon", C.c_float), ("build_ms", C.c_float), ("refit_ms", C.c_float)]
 
 
 class rp_trace_params(C.Structure):
@@ -108,6 +108,16 @@ class rp_mlp_config(C.Structure):
                 ("max_batch", C.c_int32), ("flags", C.c_int32), ("seed", C.c_uint64)]
 
 
+class rp_er_path(C.Structure):
+    _fields_ = [("source", C.c_int32), ("order", C.c_int32), ("tri", C.c_int32 * 2), ("delay_s", C.c_double),
+                ("energy", C.c_double * MAX_BANDS), ("sh", (C.c_double * MAX_SH) * MAX_BANDS)]
+
+
+class rp_er_params(C.Structure):
+    _fields_ = [("dt_update", C.c_double), ("tau_er", C.c_double), ("prune", C.c_double),
+                ("hearing_threshold", C.c_double), ("n_er", C.c_int32), ("reserved", C.c_int32)]
+
+
 class rp_debug_limits(C.Structure):
     _fields_ = [("iter_cap", C.c_int32), ("reserved", C.c_int32), ("hit_cap", C.c_uint64),
                 ("record_cap", C.c_uint64)]
@@ -126,6 +136,7 @@ _SIGS = {
     "rp_scene_create": ([C.c_void_p, C.POINTER(rp_mesh_desc), C.POINTER(C.c_void_p)], C.c_int),
     "rp_scene_destroy": ([C.c_void_p], C.c_int),
     "rp_scene_info_get": ([C.c_void_p, C.POINTER(rp_scene_info)], C.c_int),
+    "rp_scene_refit": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "rp_trace_reserve": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_int32], C.c_int),
     "rp_trace": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
                   C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -134,6 +145,14 @@ _SIGS = {
     "rp_update": ([C.c_void_p, C.POINTER(rp_trace_params), C.POINTER(rp_estimate_params), C.c_void_p,
                    C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                   C.c_int),
+    "rp_er_cache_create": ([C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
+    "rp_er_cache_destroy": ([C.c_void_p], C.c_int),
+    "rp_er_cache_reset": ([C.c_void_p], C.c_int),
+    "rp_er_cache_read": ([C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+    "rp_trace_er": ([C.c_void_p, C.POINTER(rp_trace_params), C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                     C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(rp_er_params), C.c_void_p, C.c_void_p], C.c_int),
+    "rp_ir_cache_update": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_int32],
+                           C.c_int),
     "rp_batch_create": ([C.c_void_p, C.POINTER(rp_batch_item), C.c_int32, C.POINTER(rp_trace_params),
                          C.POINTER(rp_estimate_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                          C.POINTER(C.c_void_p)], C.c_int),
@@ -180,7 +199,7 @@ def _close_all():
     """Release library objects while the CUDA runtime is still alive (interpreter
     exit runs Python's atexit handlers before the C runtime's)."""
     global _closed
-    for obj in sorted(list(_live), key=lambda o: 0 if isinstance(o, (Batch, MLP)) else 1 if isinstance(o, Scene)
+    for obj in sorted(list(_live), key=lambda o: 0 if isinstance(o, (Batch, MLP, ERCache)) else 1 if isinstance(o, Scene)
                       else 2):
         try:
             obj.close()
@@ -383,6 +402,15 @@ class Scene:
         check(self.lib.rp_scene_info_get(self.h, C.byref(out)), "rp_scene_info_get")
         return out
 
+    def refit(self, verts):
+        """rp_scene_refit: new vertex positions (same triangles), BVH refitted on the device."""
+        if hasattr(verts, "is_cuda") and verts.is_cuda:
+            v = verts.float().contiguous()
+            check(self.lib.rp_scene_refit(self.h, _ptr(v), v.shape[0], RP_MEM_DEVICE), "rp_scene_refit")
+        else:
+            v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+            check(self.lib.rp_scene_refit(self.h, _ptr(v), v.shape[0], RP_MEM_HOST), "rp_scene_refit")
+
     def close(self):
         if getattr(self, "h", None) and not _closed and getattr(self.ctx, "h", None):
             self.lib.rp_scene_destroy(self.h)
@@ -486,6 +514,78 @@ def trace_noalloc(scene: Scene, p: TraceParams, listener, sources, out: DeviceTr
     if sync:
         check(scene.ctx.sync_status(), "rp_trace_noalloc (device)")
     return out
+
+
+def _er_paths_to_dict(raw: bytes, n: int, B: int, K: int) -> dict:
+    arr = (rp_er_path * max(n, 1)).from_buffer_copy(raw) if n else []
+    return {"source": np.array([arr[i].source for i in range(n)], np.int64),
+            "order": np.array([arr[i].order for i in range(n)], np.int64),
+            "tri1": np.array([arr[i].tri[0] for i in range(n)], np.int64),
+            "tri2": np.array([arr[i].tri[1] for i in range(n)], np.int64),
+            "delay": np.array([arr[i].delay_s for i in range(n)]),
+            "energy": np.array([list(arr[i].energy)[:B] for i in range(n)]).reshape(n, B),
+            "sh": np.array([[list(arr[i].sh[b])[:K] for b in range(B)] for i in range(n)]).reshape(n, B, K)}
+
+
+class ERCache:
+    """rp_er_cache: the early-reflection path cache of the temporal coherence (Section 5)."""
+
+    def __init__(self, ctx: Context, num_bands: int, sh_order: int):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.B, self.K = num_bands, (sh_order + 1) ** 2
+        h = C.c_void_p()
+        check(self.lib.rp_er_cache_create(ctx.h, num_bands, sh_order, C.byref(h)), "rp_er_cache_create")
+        self.h = h
+        ctx.deps.add(self)
+        _live.add(self)
+
+    def reset(self):
+        check(self.lib.rp_er_cache_reset(self.h), "rp_er_cache_reset")
+
+    def read(self) -> dict:
+        import torch
+        n = C.c_int64()
+        check(self.lib.rp_er_cache_read(self.h, None, 0, C.byref(n)), "rp_er_cache_read")
+        buf = torch.empty(max(n.value, 1) * C.sizeof(rp_er_path), dtype=torch.uint8, device="cuda")
+        check(self.lib.rp_er_cache_read(self.h, _ptr(buf), n.value, C.byref(n)), "rp_er_cache_read")
+        torch.cuda.synchronize()
+        return _er_paths_to_dict(buf.cpu().numpy().tobytes(), n.value, self.B, self.K)
+
+    def trace(self, scene: "Scene", p: TraceParams, listener, sources, dt_update=0.0, tau_er=1.0, prune=0.0,
+              hearing_threshold=0.0, n_er=100):
+        """rp_trace_er with host positions: (DeviceTrace, rendered paths dict)."""
+        import torch
+        lis = np.ascontiguousarray(listener, np.float32).reshape(3)
+        src = np.ascontiguousarray(sources, np.float32).reshape(-1, 3)
+        S = src.shape[0]
+        out = DeviceTrace(S, scene.B, p.K, p.num_bins)
+        ep = rp_er_params(dt_update, tau_er, prune, hearing_threshold, n_er, 0)
+        ren = torch.empty(max(n_er, 1) * C.sizeof(rp_er_path), dtype=torch.uint8, device="cuda")
+        nr = torch.zeros(1, dtype=torch.int32, device="cuda")
+        check(self.lib.rp_trace_er(scene.h, C.byref(p.c()), _ptr(lis), _ptr(src), S, _ptr(out.H), _ptr(out.direct),
+                                   _ptr(out.stats), self.h, C.byref(ep), _ptr(ren), _ptr(nr)), "rp_trace_er")
+        check(self.ctx.sync_status(), "rp_trace_er (device)")
+        n = int(nr.item())
+        return out, _er_paths_to_dict(ren.cpu().numpy().tobytes()[: max(n, 1) * C.sizeof(rp_er_path)], n, self.B,
+                                      self.K)
+
+    def close(self):
+        if getattr(self, "h", None) and not _closed:
+            self.lib.rp_er_cache_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ir_cache_update(ctx: Context, H, C_, dt_update: float, tau: float, first: bool):
+    """rp_ir_cache_update: C_ = (1 - alpha) C_ + alpha H in place (device tensors)."""
+    check(ctx.lib.rp_ir_cache_update(ctx.h, _ptr(H), _ptr(C_), H.numel(), dt_update, tau, int(first)),
+          "rp_ir_cache_update")
 
 
 class Batch:

@@ -114,3 +114,32 @@ def test_any_hit_occlusion(oracle_lib):
     assert not osc.any_hit(p, d2, tmax=np.linalg.norm(q2 - p))
     # tmax before the box: not blocked
     assert not osc.any_hit(p, d, tmax=2.0)
+
+
+def test_coplanar_overlapping_triangles_tie_to_the_smaller_index(oracle_lib):
+    """Two triangles with different vertices in one plane, overlapping: a ray meets both
+    at one mathematical distance, so the smaller triangle index must win whatever the
+    FP64 rounding of the two computed distances and whatever order the triangles are
+    visited in (BVH and brute force, and both index assignments).  Lifted by 1e-5 m
+    towards the rays, the second one is simply nearer."""
+    rng = np.random.default_rng(12)
+    a = np.array([[0.3, 0.1, 0.2], [7.9, 0.7, 0.2], [1.1, 6.3, 0.2]])
+    b = np.array([[0.05, 0.4, 0.2], [6.7, -0.3, 0.2], [2.2, 7.1, 0.2]])
+    for first, second, lift, want in ((a, b, 0.0, 0), (b, a, 0.0, 0), (a, b, 1e-5, 1), (b, a, 1e-5, 1)):
+        s = second.copy()
+        s[:, 2] += lift  # the second triangle above the first: nearer for rays from above
+        verts = np.concatenate([first, s]).astype(np.float32)
+        tris = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+        mats = np.zeros(2, np.int32)
+        al = np.full((1, 1), 0.1, np.float32)
+        for use_bvh in (True, False):
+            osc = oracle_lib.OracleScene(verts, tris, mats, al, al, use_bvh=use_bvh)
+            hits = 0
+            for _ in range(400):
+                p = np.array([rng.uniform(1.5, 3.5), rng.uniform(1.0, 3.0), 0.2])  # inside both
+                o = p + rng.uniform(0.5, 3.0) * np.array([rng.normal(0.3, 0.2), rng.normal(0.3, 0.2), 1.0])
+                d = (p - o) / np.linalg.norm(p - o)
+                tri, t = osc.closest_hit(o, d)
+                assert tri == want, (tri, want, lift, use_bvh)
+                hits += 1
+            assert hits == 400
