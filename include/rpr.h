@@ -294,6 +294,51 @@ int rp_update(rp_scene *scene, const rp_trace_params *params,
               rp_direct *direct_host, rp_trace_stats *stats_host, double *state_host);
 
 /* ---------------------------------------------------------------------------
+ * Reverberator parameters (Section 4.1 "Sound Rendering", Section 4.2 "Reflection
+ * Density"): the SH-domain Schroeder reverberator of each source has RP_N_COMB comb
+ * filters in parallel (then all-pass filters in series).
+ * --------------------------------------------------------------------------- */
+#define RP_N_COMB 8
+
+typedef struct {
+    double mean_delay_s;      /* r_free / c the comb delays were drawn for (state) */
+    uint32_t generation;      /* draws so far (state; 0 before the first: zero the struct) */
+    int32_t resampled;        /* 1 when this update drew new delays */
+    double t_comb[RP_N_COMB];                     /* feedback delays, s */
+    double g_comb[RP_N_COMB][RP_MAX_BANDS];       /* feedback gains 10^(-3 t_comb / RT60_b) (0: no RT60) */
+    double dir[RP_N_COMB][3];                     /* dominant direction of each comb's input */
+    float comb_in[RP_N_COMB][RP_MAX_SH];          /* input SH gains Y_lm(dir) / RP_N_COMB */
+    float rot[RP_N_COMB][3][3];                   /* the comb's rotation Rz(g) Ry(b) Rx(a) */
+    float J[RP_N_COMB][RP_MAX_SH][RP_MAX_SH];     /* its SH rotation: Y(rot d) = J Y(d) */
+    float D[RP_MAX_BANDS][RP_MAX_SH][RP_MAX_SH];  /* directional loudness per band */
+} rp_reverberator;
+
+/* The reverberator parameters of S sources from their IR H [S][B][K][T] and
+ * rp_estimate's parameters [S][B] (smoothed RT60, average directivity xbar), device
+ * memory; rev: device rp_reverberator[S], zeroed before the first update, updated in
+ * place (the comb delays persist between updates):
+ *   comb delays: N(r_free / c, sigma = (r_free / c) / 3) per comb (Section 4.2), at
+ *     least a tenth of the mean, drawn from Philox (key seed, counter (source, comb,
+ *     generation, 3)) by Box-Muller, and drawn again only when r_free / c moved by
+ *     more than 2 sigma from the mean of the last draw;
+ *   comb gains: 10^(-3 t_comb / RT60_b) (comb feedback gain equation);
+ *   comb input: the dominant direction normalize(-X_11, -X_1-1, X_10) of the
+ *     band-summed first-order IR at t_comb past its first non-zero bin (linear
+ *     interpolation; +z when it vanishes), and Y_lm(dir) / N_comb (Section 4.1);
+ *   rotations: per comb a random rotation, angles uniform in [90, 270] degrees about
+ *     x, y and z (Philox counter (source, comb, 0, 2)), and its SH rotation matrix by
+ *     the recurrence of Ivanic and Ruedenberg (Section 4.1 "SH Rotations");
+ *   directional loudness: D_b = sum_j w_j a(x_j) Y(x_j) Y(x_j)^T over a product Gauss
+ *     rule of the sphere (2n + 2 Gauss-Legendre nodes in cos(theta) x 4n + 4
+ *     azimuths, standing in for the paper's spherical t-design), a(x) the amplitude
+ *     gain sqrt(max(f(x), 0) / mean f) of the average directivity's density
+ *     f(x) = sum_k xbar_k Y_k(x); the identity for isotropic reverberation.
+ * mean_free_path: rp_trace_stats' mfp_sum / mfp_count (m). */
+int rp_reverb_configure(rp_ctx *ctx, const float *H, const rp_reverb_params *params, int32_t num_sources,
+                        int32_t num_bands, int32_t num_sh, int32_t num_bins, double ir_rate_hz,
+                        double mean_free_path, double speed_of_sound, uint64_t seed, rp_reverberator *rev);
+
+/* ---------------------------------------------------------------------------
  * Temporal coherence (Section 5, "Sound Propagation"): the early reflections (the
  * first orders; the paper uses 2) go to a diffuse path cache with spherical-harmonic
  * directivity per path, smoothed over updates (tau_ER = 1 s in the paper); the N_ER

@@ -646,3 +646,6 @@ def mlp_split(P, din: int, dh: int, nh: int, dout: int):
         o += w
         out.append((W, b))
     return out
+
+
+from . import reverb  # noqa: E402,F401  (reverberator parameters, Sections 4.1-4.2)

@@ -118,6 +118,17 @@ class rp_er_params(C.Structure):
                 ("hearing_threshold", C.c_double), ("n_er", C.c_int32), ("reserved", C.c_int32)]
 
 
+N_COMB = 8
+
+
+class rp_reverberator(C.Structure):
+    _fields_ = [("mean_delay_s", C.c_double), ("generation", C.c_uint32), ("resampled", C.c_int32),
+                ("t_comb", C.c_double * N_COMB), ("g_comb", (C.c_double * MAX_BANDS) * N_COMB),
+                ("dir", (C.c_double * 3) * N_COMB), ("comb_in", (C.c_float * MAX_SH) * N_COMB),
+                ("rot", ((C.c_float * 3) * 3) * N_COMB), ("J", ((C.c_float * MAX_SH) * MAX_SH) * N_COMB),
+                ("D", ((C.c_float * MAX_SH) * MAX_SH) * MAX_BANDS)]
+
+
 class rp_debug_limits(C.Structure):
     _fields_ = [("iter_cap", C.c_int32), ("reserved", C.c_int32), ("hit_cap", C.c_uint64),
                 ("record_cap", C.c_uint64)]
@@ -145,6 +156,8 @@ _SIGS = {
     "rp_update": ([C.c_void_p, C.POINTER(rp_trace_params), C.POINTER(rp_estimate_params), C.c_void_p,
                    C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                   C.c_int),
+    "rp_reverb_configure": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                             C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_void_p], C.c_int),
     "rp_er_cache_create": ([C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
     "rp_er_cache_destroy": ([C.c_void_p], C.c_int),
     "rp_er_cache_reset": ([C.c_void_p], C.c_int),
@@ -514,6 +527,31 @@ def trace_noalloc(scene: Scene, p: TraceParams, listener, sources, out: DeviceTr
     if sync:
         check(scene.ctx.sync_status(), "rp_trace_noalloc (device)")
     return out
+
+
+def reverb_configure(ctx: Context, H, params, S: int, B: int, K: int, ir_rate_hz: float, mean_free_path: float,
+                     seed: int, rev=None, speed_of_sound: float = 343.0):
+    """rp_reverb_configure; params: the device buffer rp_estimate filled; rev: the
+    device state (a zeroed buffer is made when None).  Returns (rev, list of dicts)."""
+    import torch
+    T = H.shape[-1]
+    if rev is None:
+        rev = torch.zeros(S * C.sizeof(rp_reverberator), dtype=torch.uint8, device="cuda")
+    check(ctx.lib.rp_reverb_configure(ctx.h, _ptr(H), _ptr(params), S, B, K, T, ir_rate_hz, mean_free_path,
+                                      speed_of_sound, seed, _ptr(rev)), "rp_reverb_configure")
+    check(ctx.sync_status(), "rp_reverb_configure (device)")
+    arr = (rp_reverberator * S).from_buffer_copy(rev.cpu().numpy().tobytes())
+    out = []
+    for s in range(S):
+        r = arr[s]
+        out.append({"mean_delay": r.mean_delay_s, "generation": r.generation, "resampled": bool(r.resampled),
+                    "t_comb": np.array(r.t_comb[:]), "g_comb": np.array([r.g_comb[i][:B] for i in range(N_COMB)]),
+                    "dir": np.array([r.dir[i][:] for i in range(N_COMB)]),
+                    "comb_in": np.array([r.comb_in[i][:K] for i in range(N_COMB)]),
+                    "rot": np.array([[r.rot[i][p][:] for p in range(3)] for i in range(N_COMB)]),
+                    "J": np.array([[r.J[i][k][:K] for k in range(K)] for i in range(N_COMB)]),
+                    "D": np.array([[r.D[b][k][:K] for k in range(K)] for b in range(B)])})
+    return rev, out
 
 
 def _er_paths_to_dict(raw: bytes, n: int, B: int, K: int) -> dict:
