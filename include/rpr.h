@@ -338,6 +338,40 @@ int rp_reverb_configure(rp_ctx *ctx, const float *H, const rp_reverb_params *par
                         int32_t num_bands, int32_t num_sh, int32_t num_bins, double ir_rate_hz,
                         double mean_free_path, double speed_of_sound, uint64_t seed, rp_reverberator *rev);
 
+/* The reverberator itself (Section 4.1 "Sound Rendering"; Section 5 "Auralization"),
+ * rendered for many sources at once, block by block:
+ *   bands     a serial Linkwitz-Riley 4th-order crossover (2nd-order Butterworth
+ *             biquads applied twice, bilinear transform, FP64 state): band 0 is the
+ *             low part at crossover_hz[0], the high part is split again at the next
+ *             frequency, band B-1 is the last high part;
+ *   predelay  each band read round(predelay_s x fs) samples late (rp_reverb_params);
+ *   combs     RP_N_COMB in parallel in the SH domain: y[n] = comb_in x[n - p] +
+ *             g_comb J y[n - d], d = max(1, round(t_comb fs)) -- every pass through
+ *             the feedback rotates the delayed K-vector by the comb's J and scales it;
+ *   all-pass  4 in series per (band, SH channel): v[n] = -0.7 u[n] + u[n - d] +
+ *             0.7 v[n - d], d = 5, 1.7, 0.6, 0.2 ms (the paper gives only the count);
+ *   output    q[n] = sum_b g_reverb_b D_b v_b[n]: K SH channels per source.
+ * Comb delays above max_delay_samples or a predelay above max_predelay_samples are
+ * clamped and RP_ERR_CAPACITY is recorded. */
+typedef struct {
+    double sample_rate;                        /* fs, Hz */
+    double crossover_hz[RP_MAX_BANDS - 1];     /* B - 1 increasing frequencies below fs / 2
+                                                  (the paper's 4 bands: 176, 775, 3408 Hz) */
+    int32_t max_delay_samples;                 /* comb ring length */
+    int32_t max_predelay_samples;
+} rp_reverb_render_config;
+
+/* Bytes of the render state of S sources (device memory the caller owns; zero it
+ * before the first block -- the rings, crossover states and sample counters). */
+int rp_reverb_state_bytes(int32_t num_sources, int32_t num_bands, int32_t num_sh, const rp_reverb_render_config *cfg,
+                          int64_t *bytes);
+/* One block of N samples: in [S][N] (device, mono source signals), out [S][K][N]
+ * (device); rev [S] (rp_reverb_configure) and params [S][B] (rp_estimate) device
+ * memory; state as rp_reverb_state_bytes says, carried from block to block. */
+int rp_reverb_render(rp_ctx *ctx, const rp_reverberator *rev, const rp_reverb_params *params, int32_t num_sources,
+                     int32_t num_bands, int32_t num_sh, const rp_reverb_render_config *cfg, const float *in,
+                     int32_t num_samples, float *out, void *state);
+
 /* ---------------------------------------------------------------------------
  * Temporal coherence (Section 5, "Sound Propagation"): the early reflections (the
  * first orders; the paper uses 2) go to a diffuse path cache with spherical-harmonic

@@ -649,3 +649,4 @@ def mlp_split(P, din: int, dh: int, nh: int, dout: int):
 
 
 from . import reverb  # noqa: E402,F401  (reverberator parameters, Sections 4.1-4.2)
+from . import reverberator  # noqa: E402,F401  (the SH-domain Schroeder reverberator, Section 4.1)

@@ -275,7 +275,8 @@ int rp_destroy(rp_ctx *c)
                    &c->rec_e, &c->perm, &c->rerun,
                    &c->cnt, &c->off, &c->cur, &c->scan_part, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H,
                    &c->direct,
-                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->plan_seg})
+                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->plan_seg, &c->rv_raw,
+                   &c->rv_bands, &c->rv_comb, &c->rv_ap, &c->rv_phi})
         free_buf(*b);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);

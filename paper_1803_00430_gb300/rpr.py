@@ -129,6 +129,11 @@ class rp_reverberator(C.Structure):
                 ("D", ((C.c_float * MAX_SH) * MAX_SH) * MAX_BANDS)]
 
 
+class rp_reverb_render_config(C.Structure):
+    _fields_ = [("sample_rate", C.c_double), ("crossover_hz", C.c_double * (MAX_BANDS - 1)),
+                ("max_delay_samples", C.c_int32), ("max_predelay_samples", C.c_int32)]
+
+
 class rp_debug_limits(C.Structure):
     _fields_ = [("iter_cap", C.c_int32), ("reserved", C.c_int32), ("hit_cap", C.c_uint64),
                 ("record_cap", C.c_uint64)]
@@ -158,6 +163,11 @@ _SIGS = {
                   C.c_int),
     "rp_reverb_configure": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                              C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_void_p], C.c_int),
+    "rp_reverb_state_bytes": ([C.c_int32, C.c_int32, C.c_int32, C.POINTER(rp_reverb_render_config),
+                               C.POINTER(C.c_int64)], C.c_int),
+    "rp_reverb_render": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                          C.POINTER(rp_reverb_render_config), C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p],
+                         C.c_int),
     "rp_er_cache_create": ([C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
     "rp_er_cache_destroy": ([C.c_void_p], C.c_int),
     "rp_er_cache_reset": ([C.c_void_p], C.c_int),
@@ -552,6 +562,33 @@ def reverb_configure(ctx: Context, H, params, S: int, B: int, K: int, ir_rate_hz
                     "J": np.array([[r.J[i][k][:K] for k in range(K)] for i in range(N_COMB)]),
                     "D": np.array([[r.D[b][k][:K] for k in range(K)] for b in range(B)])})
     return rev, out
+
+
+class Reverberator:
+    """rp_reverb_render: the SH-domain Schroeder reverberators of S sources with their
+    render state (device), rendering blocks of mono input."""
+
+    def __init__(self, ctx: Context, S: int, B: int, K: int, crossover_hz, sample_rate: float = 48000.0,
+                 max_delay_samples: int = 1 << 14, max_predelay_samples: int = 1 << 14):
+        import torch
+        self.ctx, self.S, self.B, self.K = ctx, S, B, K
+        xo = list(crossover_hz) + [0.0] * (MAX_BANDS - 1 - len(crossover_hz))
+        self.cfg = rp_reverb_render_config(sample_rate, (C.c_double * (MAX_BANDS - 1))(*xo), max_delay_samples,
+                                           max_predelay_samples)
+        n = C.c_int64()
+        check(ctx.lib.rp_reverb_state_bytes(S, B, K, C.byref(self.cfg), C.byref(n)), "rp_reverb_state_bytes")
+        self.state = torch.zeros(max(n.value, 1), dtype=torch.uint8, device="cuda")
+
+    def render(self, rev, params, x):
+        """x: device float32 [S][N] -> device float32 [S][K][N]."""
+        import torch
+        x = x.float().contiguous()
+        N = x.shape[1]
+        out = torch.empty((self.S, self.K, N), dtype=torch.float32, device="cuda")
+        check(self.ctx.lib.rp_reverb_render(self.ctx.h, _ptr(rev), _ptr(params), self.S, self.B, self.K,
+                                            C.byref(self.cfg), _ptr(x), N, _ptr(out), _ptr(self.state)),
+              "rp_reverb_render")
+        return out
 
 
 def _er_paths_to_dict(raw: bytes, n: int, B: int, K: int) -> dict:
