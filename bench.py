@@ -434,7 +434,11 @@ def main():
                 "node_visits_per_segment": stc["node_visits"][0] / max(1, stc["segments"]),
                 "node_visits_per_shadow_ray": stc["node_visits"][1] / max(1, stc["shadow_rays"]),
                 "tri_tests_per_segment": stc["tri_tests"][0] / max(1, stc["segments"]),
-                "tri_tests_per_shadow_ray": stc["tri_tests"][1] / max(1, stc["shadow_rays"])},
+                "tri_tests_per_shadow_ray": stc["tri_tests"][1] / max(1, stc["shadow_rays"]),
+                "shadow_items": stc["hits_stored"] * S,
+                "packet_walks": stc["packet_walks"],
+                "rays_per_packet_walk": stc["shadow_rays"] / max(1, stc["packet_walks"]),
+                "node_fetches_per_packet_walk": stc["packet_steps"] / max(1, stc["packet_walks"])},
         "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "traffic_note": ("DRAM bytes per update of the shadow-ray kernel, from an ncu capture at "

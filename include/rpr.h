@@ -187,6 +187,9 @@ typedef struct {
     uint64_t hits_stored;            /* reflections kept for next-event estimation */
     uint64_t fp64_reruns;            /* queries whose FP32 answer was rounding-sensitive and
                                         were decided again in FP64 */
+    uint64_t packet_walks;           /* with RP_FLAG_COUNT_VISITS: BVH walks of shadow-ray
+                                        warp packets (one per packet and job) */
+    uint64_t packet_steps;           /* with RP_FLAG_COUNT_VISITS: nodes those walks fetched */
     int32_t error;                   /* first RP_ERR_* raised by a kernel, or 0 */
     int32_t reserved;
 } rp_trace_stats;

@@ -89,8 +89,10 @@ struct TraceCounters {
     unsigned long long n_rerun;      // shadow items queued for an FP64 decision (current chunk)
     unsigned long long total_items; // shadow items of the step (sum over jobs of shadow_items(hits, S))
     unsigned long long total_hits;  // stored reflections of the step (sum over jobs)
-    // planned refill: candidate rays still needed (0 = planned), primaries and waves
+    // planned refill: candidate rays still needed (0 = planned), primaries and waves;
+    // where the wave walk stopped (segments used, next wave's size, walk started)
     unsigned long long plan_need, plan_rays, plan_waves;
+    unsigned long long plan_used, plan_count, plan_started;
     unsigned long long n_er;  // early reflections stored (rp_trace_er)
     unsigned long long pad[2];
 };

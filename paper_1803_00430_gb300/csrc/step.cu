@@ -45,9 +45,10 @@ constexpr int REFILL_BATCH = 16;  // refill waves enqueued between host checks
         if (e_ != cudaSuccess) return e_;         \
     } while (0)
 
-// Planned refill: counting passes over candidate ray ids (4 N or 4096 at first, then
-// twice as many while the waves reach past them), then the waves' sizes.  The host
-// reads whether more candidates are needed after each pass.
+// Planned refill: counting passes over candidate ray ids (4 N or 4096 at first), then
+// the waves' sizes.  The host reads after each pass whether more candidates are
+// needed; the next pass reaches to where the segments per ray seen so far say the
+// budget runs out (3 % beyond), at least to the wave that did not fit.
 cudaError_t plan_refill(const TraceWork &w, int blocks, cudaStream_t st, ProfHook hook, void *hook_ctx)
 {
     const unsigned long long N = w.job0.num_rays, budget = N * (unsigned long long)w.k.M;
@@ -64,11 +65,17 @@ cudaError_t plan_refill(const TraceWork &w, int blocks, cudaStream_t st, ProfHoo
         }
         done = cand;
         launch_refill_plan(w, done, st);
-        unsigned long long need = 0;
-        CKS(cudaMemcpyAsync(&need, &w.ctr->plan_need, sizeof(need), cudaMemcpyDeviceToHost, st));
+        unsigned long long pl[4] = {0, 0, 0, 0};  // plan_need, plan_rays, plan_waves, plan_used
+        CKS(cudaMemcpyAsync(pl, &w.ctr->plan_need, sizeof(pl), cudaMemcpyDeviceToHost, st));
         CKS(cudaStreamSynchronize(st));
+        const unsigned long long need = pl[0], rays = pl[1], used = pl[3];
         if (need == 0) break;
-        cand = std::min(budget, std::max(2 * cand, need));
+        unsigned long long next = 2 * cand;
+        if (rays > 0 && used > 0 && used < budget) {
+            const double per_ray = (double)used / (double)rays;
+            next = (unsigned long long)(1.03 * ((double)rays + (double)(budget - used) / per_ray)) + 1024;
+        }
+        cand = std::min(budget, std::max(next, need));
         if (cand <= done) return cudaErrorUnknown;  // cannot happen: the waves hold at most N M rays
     }
     launch_plan_apply(w, st);

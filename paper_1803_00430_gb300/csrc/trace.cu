@@ -47,7 +47,7 @@ constexpr int SHADOW_WINDOW = 256;  // items a warp of k_shadow takes from the c
 struct BlockAcc {
     double esc[MAXB], absb[MAXB], rem[MAXB], late[MAXB];
     double mfp, mfp_np;
-    unsigned long long mfp_cnt, mfp_cnt_np, segs, shadow, contrib, sphere, nodes, tris;
+    unsigned long long mfp_cnt, mfp_cnt_np, segs, shadow, contrib, sphere, nodes, tris, walks, steps;
 };
 
 __device__ __forceinline__ void acc_init(BlockAcc &a)
@@ -62,6 +62,7 @@ __device__ __forceinline__ void acc_init(BlockAcc &a)
     if (t == 0) {
         a.mfp = a.mfp_np = 0.0;
         a.mfp_cnt = a.mfp_cnt_np = a.segs = a.shadow = a.contrib = a.sphere = a.nodes = a.tris = 0ull;
+        a.walks = a.steps = 0ull;
     }
 }
 
@@ -98,6 +99,8 @@ __device__ __forceinline__ void acc_flush(BlockAcc &a, rp_trace_stats *st, int B
         if (a.sphere) atomicAdd((unsigned long long *)&st->sphere_hits, a.sphere);
         if (a.nodes) atomicAdd((unsigned long long *)&st->node_visits[which], a.nodes);
         if (a.tris) atomicAdd((unsigned long long *)&st->tri_tests[which], a.tris);
+        if (a.walks) atomicAdd((unsigned long long *)&st->packet_walks, a.walks);
+        if (a.steps) atomicAdd((unsigned long long *)&st->packet_steps, a.steps);
     }
 }
 
@@ -116,6 +119,7 @@ __device__ __forceinline__ void acc_counters(BlockAcc &a, double mfp, double mfp
     contrib = warp_sum_u(contrib);
     sphere = warp_sum_u(sphere);
     const unsigned long long nodes = warp_sum_u(ts.nodes), tris = warp_sum_u(ts.tris);
+    const unsigned long long walks = warp_sum_u(ts.walks), steps = warp_sum_u(ts.steps);
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&a.mfp, mfp);
         atomicAdd(&a.mfp_np, mfp_np);
@@ -127,6 +131,8 @@ __device__ __forceinline__ void acc_counters(BlockAcc &a, double mfp, double mfp
         atomicAdd(&a.sphere, sphere);
         atomicAdd(&a.nodes, nodes);
         atomicAdd(&a.tris, tris);
+        if (walks) atomicAdd(&a.walks, walks);
+        if (steps) atomicAdd(&a.steps, steps);
     }
 }
 
@@ -199,32 +205,56 @@ __global__ void k_plan_block(TraceWork w, unsigned long long begin, unsigned lon
 
 // The waves from the candidates' segment counts: wave 1 is the N primaries; each later
 // wave takes floor(unused / M) further ray ids, unused being the budget N M less the
-// segments of all rays so far (as k_setup's later waves).  One warp sums each wave.
+// segments of all rays so far (as k_setup's later waves).  One block of REFILL_THREADS
+// sums each wave's range; the walk resumes where the previous pass stopped.
 // plan_need > 0: the waves reach past the candidates traced so far.
-__global__ void k_refill_plan(TraceWork w, unsigned long long cand)
+constexpr int REFILL_THREADS = 1024;
+__global__ void __launch_bounds__(REFILL_THREADS) k_refill_plan(TraceWork w, unsigned long long cand)
 {
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    __shared__ unsigned long long part[REFILL_THREADS / 32];
+    if (blockIdx.x != 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    TraceCounters *C = w.ctr;
     const unsigned long long N = w.jobs[0].num_rays, M = (unsigned long long)w.k.M, budget = N * M;
     unsigned long long r = 0, used = 0, waves = 0, count = N, need = 0;
+    if (C->plan_started) {
+        r = C->plan_rays;
+        used = C->plan_used;
+        waves = C->plan_waves;
+        count = C->plan_count;
+    }
+    __syncthreads();  // every thread has read the counters before thread 0 rewrites them
     while (count > 0) {  // r grows by count >= 1 each time and stays <= cand
         if (r + count > cand) {
             need = r + count;
             break;
         }
         unsigned long long seg = 0;
-        for (unsigned long long i = r + lane; i < r + count; i += 32) seg += w.plan_seg[i];
+        const uint32_t *ps = w.plan_seg;
+        unsigned long long i = r + tid;
+        for (; i + 3 * REFILL_THREADS < r + count; i += 4 * REFILL_THREADS)
+            seg += (unsigned long long)ps[i] + ps[i + REFILL_THREADS] + ps[i + 2 * REFILL_THREADS] +
+                   ps[i + 3 * REFILL_THREADS];
+        for (; i < r + count; i += REFILL_THREADS) seg += ps[i];
         for (int o = 16; o > 0; o >>= 1) seg += __shfl_xor_sync(FULL, seg, o);
+        if (lane == 0) part[wid] = seg;
+        __syncthreads();
+        seg = 0;
+        for (int q = 0; q < REFILL_THREADS / 32; ++q) seg += part[q];  // the same order in every thread
+        __syncthreads();  // part is rewritten by the next wave
         used += seg;
         r += count;
         ++waves;
         const unsigned long long unused = budget > used ? budget - used : 0ull;
         count = (M > 0 && unused >= M) ? unused / M : 0ull;
     }
-    if (lane == 0) {
-        w.ctr->plan_need = need;
-        w.ctr->plan_rays = r;
-        w.ctr->plan_waves = waves;
+    if (tid == 0) {
+        C->plan_need = need;
+        C->plan_rays = r;
+        C->plan_waves = waves;
+        C->plan_used = used;
+        C->plan_count = count;
+        C->plan_started = 1;
     }
 }
 
@@ -1015,6 +1045,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
             const int iter_cap = sc.iter_cap;
             int node = 0, sp = 0, iters = 0;
             unsigned mask = grp;  // lanes of the group that reach `node` and have no answer yet
+            if (COUNT && lane == 0) ts.walks++;
             while (mask) {
                 if (++iters > iter_cap) {
                     if (lane == 0) raise_error(w.status, RP_ERR_TIMEOUT);
@@ -1026,6 +1057,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 }
                 const bool need = (mask >> lane) & 1u;
                 if (COUNT && need) ts.nodes++;
+                if (COUNT && lane == 0) ts.steps++;
                 const float4 *np = sc.nodes + 4 * node;
                 const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
                 const float a0 = n0.x * ray.idir.x - ray.ood.x, b0 = n0.y * ray.idir.x - ray.ood.x;
@@ -1195,7 +1227,7 @@ void launch_plan_block(const TraceWork &w, unsigned long long begin, unsigned lo
 
 void launch_refill_plan(const TraceWork &w, unsigned long long candidates, cudaStream_t st)
 {
-    k_refill_plan<<<1, 32, 0, st>>>(w, candidates);
+    k_refill_plan<<<1, REFILL_THREADS, 0, st>>>(w, candidates);
 }
 
 void launch_plan_apply(const TraceWork &w, cudaStream_t st) { k_plan_apply<<<1, 32, 0, st>>>(w); }

@@ -37,6 +37,7 @@ constexpr double TIE_REL = 1e-9;  // FP64 closest-hit distances this close (rela
 struct TravStats {
     uint32_t nodes;
     uint32_t tris;
+    uint32_t walks = 0, steps = 0;  // shadow-ray packets: BVH walks and their node fetches (lane 0)
 };
 
 struct D3 {

@@ -70,7 +70,8 @@ class rp_trace_stats(C.Structure):
                 ("mfp_count_np", C.c_uint64), ("segments", C.c_uint64), ("shadow_rays", C.c_uint64),
                 ("primaries", C.c_uint64), ("contributions", C.c_uint64), ("sphere_hits", C.c_uint64),
                 ("waves", C.c_uint64), ("node_visits", C.c_uint64 * 2), ("tri_tests", C.c_uint64 * 2),
-                ("hits_stored", C.c_uint64), ("fp64_reruns", C.c_uint64), ("error", C.c_int32),
+                ("hits_stored", C.c_uint64), ("fp64_reruns", C.c_uint64), ("packet_walks", C.c_uint64),
+                ("packet_steps", C.c_uint64), ("error", C.c_int32),
                 ("reserved", C.c_int32)]
 
 
@@ -454,7 +455,8 @@ def _struct_array(raw: bytes, ctype, n: int):
 def stats_to_dict(st: rp_trace_stats, B: int) -> dict:
     out = {k: np.array(getattr(st, k)[:B]) for k in ("escaped", "absorbed", "remaining", "late")}
     for k in ("mfp_sum", "mfp_sum_np", "mfp_count", "mfp_count_np", "segments", "shadow_rays", "primaries",
-              "contributions", "sphere_hits", "waves", "hits_stored", "fp64_reruns", "error"):
+              "contributions", "sphere_hits", "waves", "hits_stored", "fp64_reruns", "packet_walks", "packet_steps",
+              "error"):
         out[k] = getattr(st, k)
     out["node_visits"] = list(st.node_visits)
     out["tri_tests"] = list(st.tri_tests)
