@@ -608,11 +608,13 @@ int rp_mlp_train_step(rp_mlp *mlp, const void *Xb, const float *T, const float *
  *   (96 + 8 B) bytes per reflection (stored reflections, their spatial order and the
  *   cell-ordered copy the shadow rays read), 1 MiB of cell counts, 12 B per (source,
  *   bin) (counting sort), 8 B per histogram cell S x B x K x T (compensated sums),
- *   and room for at least R / 2 + 4096 + S contribution records of (29 + 4 B) bytes
- *   each (key, ray id, energies, sort index and the share of the FP64 re-decision
- *   queue).  Larger problems return RP_ERR_TOO_LARGE before any work is enqueued.
- * The first call on a device looks up the array's device address with that device
- * current: make it before any stream capture.  Every call shares the array and
+ *   and room for at least R / 2 + 4096 + S contribution records of
+ *   (29 + 4 B + ceil((8 + 16 B K) / 1024)) bytes each (key, ray id, energies, sort
+ *   index and the shares of the FP64 re-decision queue and of the segment sums of
+ *   heavy (source, bin) keys).  Larger problems return RP_ERR_TOO_LARGE before any
+ *   work is enqueued.
+ * The first call on a device looks up the array's device address (a host-side query,
+ * with that device current).  Every call shares the array and
  * overwrites the previous call's temporaries, so calls that may overlap on the GPU
  * (several streams or host threads) race and must be serialised by the caller.
  * Host positions are copied with cudaMemcpyAsync, and budget_refill reads the waves'

@@ -8,8 +8,12 @@
 // staged in shared memory (energies, and SH of the primary direction recomputed
 // from Philox), and every cell is summed in FP32: each group of 32 staged records
 // with plain fused multiply-adds (relative error at most 32 * 2^-24), the groups with
-// Kahan compensation.  Each cell is written by exactly one warp, so no atomics touch
-// H.  Chunks of records (when the record buffer is smaller than one step's records)
+// Kahan compensation.  A key with more than ACC_SEG records in a chunk is split into
+// segments of ACC_SEG records, each summed so by its own warp, and its warp then
+// combines the segments' pairs in segment order with an error-free two-sum: a few
+// keys can hold a large share of the records (one warp each left most of the GPU idle
+// while they finished), and the fixed segmentation keeps the sums deterministic.
+// Each cell is written by exactly one warp, so no atomics touch H.  Chunks of records (when the record buffer is smaller than one step's records)
 // are merged into a running (sum, error) pair with an error-free two-sum.  The running
 // pair is kept key-major, [source][bin][band][coefficient], so that a warp's B*K cells
 // of one key are contiguous (coalesced loads and stores); the finalize kernel
@@ -181,6 +185,127 @@ __device__ __forceinline__ void kahan_add(float &sum, float &err, float x)
     sum = t;
 }
 
+// The compensated sums of records perm[begin .. end) of one key, by one warp: lane l
+// owns cells l + 32 i; groups of 32 records are staged in shared memory (energies and
+// the SH of the primary direction), summed in plain FP32, and the groups Kahan-added.
+__device__ __forceinline__ void accum_range(const TraceWork &w, long long key, uint32_t begin, uint32_t end,
+                                            float (*se)[MAXB], float (*sy)[MAXK], float *sum, float *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int B = w.k.B, K = w.k.K, T = w.k.T, BK = B * K;
+    const unsigned long long seed = w.seed ? w.seed[0] : w.seed_val;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    const int gs = w.src_base + (int)(key / T);
+    const uint32_t scene_id = w.njobs > 1 ? w.jobs[w.src_job[gs]].scene_id : w.job0.scene_id;
+#pragma unroll
+    for (int i = 0; i < ACC_SLOTS; ++i) sum[i] = err[i] = 0.f;
+    for (uint32_t base = begin; base < end; base += 32) {
+        const int n = (int)min(32u, end - base);
+        if (lane < n) {
+            uint32_t r = w.perm[base + lane];
+            if (!RP_IN_RANGE(r, w.rec.cap, w.status)) r = 0;  // (checked build) keep going on record 0
+            const uint32_t rid = w.rec.rid[r];
+            const float *e = w.rec.e + (unsigned long long)r * B;
+#pragma unroll
+            for (int b = 0; b < MAXB; ++b)
+                if (b < B) se[lane][b] = e[b];
+            const float3 d0 = primary_direction(rid, scene_id, key0, key1);
+            float Y[MAXK];
+            sh_eval(w.k.sh_order, d0.x, d0.y, d0.z, Y);
+#pragma unroll
+            for (int kk = 0; kk < MAXK; ++kk)
+                if (kk < K) sy[lane][kk] = Y[kk];
+        }
+        __syncwarp();
+        // the staged records in plain FP32, then one compensated add per group of 32
+        float part[ACC_SLOTS];
+#pragma unroll
+        for (int i = 0; i < ACC_SLOTS; ++i) part[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < ACC_SLOTS; ++i) {
+            const int c = lane + 32 * i;
+            if (c < BK) {
+                const int b = c / K, kk = c - b * K;
+                for (int j = 0; j < n; ++j) part[i] = fmaf(se[j][b], sy[j][kk], part[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ACC_SLOTS; ++i) kahan_add(sum[i], err[i], part[i]);
+        __syncwarp();
+    }
+}
+
+// two-sum merge of the pair (b, be) into the running pair (a, ae)
+__device__ __forceinline__ void pair_merge(float &a, float &ae, float b, float be)
+{
+    const float s2 = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s2, a);
+    const float e2 = __fadd_rn(__fsub_rn(a, __fsub_rn(s2, bp)), __fsub_rn(b, bp));
+    a = s2;
+    ae = ae + be + e2;
+}
+
+// Heavy keys: cur[key] = its number of segments of ACC_SEG records when it has more
+// than ACC_SEG records in this chunk, else 0 (its warp in k_accum sums it directly).
+__global__ void k_seg_count(TraceWork w, unsigned long long chunk)
+{
+    if (!chunk_active(w, chunk)) return;
+    const long long n = (long long)w.k.S * w.k.T;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c = w.off[i + 1] - w.off[i];
+        w.cur[i] = c > ACC_SEG ? (c + ACC_SEG - 1) / ACC_SEG : 0u;
+    }
+}
+
+// after the scan of cur into cnt: the key of every segment
+__global__ void k_seg_map(TraceWork w, unsigned long long chunk)
+{
+    if (!chunk_active(w, chunk)) return;
+    const long long n = (long long)w.k.S * w.k.T;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t m = w.cur[i], g0 = w.cnt[i];
+        for (uint32_t j = 0; j < m; ++j) {
+            if ((unsigned long long)g0 + j >= w.seg_cap) {  // cannot happen: seg_cap holds 2 rec_cap / ACC_SEG
+                raise_error(w.status, RP_ERR_CAPACITY);
+                break;
+            }
+            w.segkey[g0 + j] = (uint32_t)i;
+        }
+    }
+}
+
+// one warp per segment of a heavy key: its compensated sums into Ss / Se
+__global__ void __launch_bounds__(ACC_THREADS) k_accum_seg(TraceWork w, unsigned long long chunk)
+{
+    if (!chunk_active(w, chunk)) return;
+    __shared__ float se[ACC_WARPS][32][MAXB];
+    __shared__ float sy[ACC_WARPS][32][MAXK];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const long long nkeys = (long long)w.k.S * w.k.T;
+    const int BK = w.k.B * w.k.K;
+    const unsigned long long nseg = min((unsigned long long)w.cnt[nkeys], w.seg_cap);
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * ACC_WARPS;
+    for (unsigned long long g = (unsigned long long)blockIdx.x * ACC_WARPS + wp; g < nseg; g += nwarps) {
+        const uint32_t key = w.segkey[g];
+        if (key >= (unsigned long long)nkeys) continue;
+        const uint32_t begin = w.off[key] + (uint32_t)(g - w.cnt[key]) * ACC_SEG;
+        const uint32_t end = min(begin + ACC_SEG, w.off[key + 1]);
+        float sum[ACC_SLOTS], err[ACC_SLOTS];
+        accum_range(w, key, begin, end, se[wp], sy[wp], sum, err);
+#pragma unroll
+        for (int i = 0; i < ACC_SLOTS; ++i) {
+            const int c = lane + 32 * i;
+            if (c < BK) {
+                w.Ss[g * BK + c] = sum[i];
+                w.Se[g * BK + c] = err[i];
+            }
+        }
+    }
+}
+
+// One warp per (source, bin): this chunk's sums of the key -- its records directly,
+// or its segments' sums (k_accum_seg) combined in segment order -- merged into the
+// running pair (written on the first chunk).
 __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, unsigned long long chunk)
 {
     if (!chunk_active(w, chunk)) return;
@@ -190,49 +315,33 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, u
     const int S = w.k.S, B = w.k.B, K = w.k.K, T = w.k.T, BK = B * K;
     const long long nkeys = (long long)S * T;
     const long long nwarps = (long long)gridDim.x * ACC_WARPS;
-    const unsigned long long seed = w.seed ? w.seed[0] : w.seed_val;
-    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
     for (long long key = (long long)blockIdx.x * ACC_WARPS + wp; key < nkeys; key += nwarps) {
         const uint32_t begin = w.off[key], end = w.off[key + 1];
         if (!first && begin == end) continue;  // nothing to merge: the running pair stands
-        const int gs = w.src_base + (int)(key / T);
-        const uint32_t scene_id = w.njobs > 1 ? w.jobs[w.src_job[gs]].scene_id : w.job0.scene_id;
         float sum[ACC_SLOTS], err[ACC_SLOTS];
+        const uint32_t m = w.cur[key];
+        if (m == 0) {
+            accum_range(w, key, begin, end, se[wp], sy[wp], sum, err);
+        } else {
+            const unsigned long long g0 = w.cnt[key];
 #pragma unroll
-        for (int i = 0; i < ACC_SLOTS; ++i) sum[i] = err[i] = 0.f;
-        for (uint32_t base = begin; base < end; base += 32) {
-            const int n = (int)min(32u, end - base);
-            if (lane < n) {
-                uint32_t r = w.perm[base + lane];
-                if (!RP_IN_RANGE(r, w.rec.cap, w.status)) r = 0;  // (checked build) keep going on record 0
-                const uint32_t rid = w.rec.rid[r];
-                const float *e = w.rec.e + (unsigned long long)r * B;
+            for (int i = 0; i < ACC_SLOTS; ++i) sum[i] = err[i] = 0.f;
+            for (uint32_t j = 0; j < m; ++j) {
+                const unsigned long long g = g0 + j;
+                if (g >= w.seg_cap) break;  // (k_seg_map has raised the error)
 #pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < B) se[wp][lane][b] = e[b];
-                const float3 d0 = primary_direction(rid, scene_id, key0, key1);
-                float Y[MAXK];
-                sh_eval(w.k.sh_order, d0.x, d0.y, d0.z, Y);
-#pragma unroll
-                for (int kk = 0; kk < MAXK; ++kk)
-                    if (kk < K) sy[wp][lane][kk] = Y[kk];
-            }
-            __syncwarp();
-            // the staged records in plain FP32, then one compensated add per group of 32
-            float part[ACC_SLOTS];
-#pragma unroll
-            for (int i = 0; i < ACC_SLOTS; ++i) part[i] = 0.f;
-#pragma unroll
-            for (int i = 0; i < ACC_SLOTS; ++i) {
-                const int c = lane + 32 * i;
-                if (c < BK) {
-                    const int b = c / K, kk = c - b * K;
-                    for (int j = 0; j < n; ++j) part[i] = fmaf(se[wp][j][b], sy[wp][j][kk], part[i]);
+                for (int i = 0; i < ACC_SLOTS; ++i) {
+                    const int c = lane + 32 * i;
+                    if (c < BK) {
+                        if (j == 0) {
+                            sum[i] = w.Ss[g * BK + c];
+                            err[i] = w.Se[g * BK + c];
+                        } else {
+                            pair_merge(sum[i], err[i], w.Ss[g * BK + c], w.Se[g * BK + c]);
+                        }
+                    }
                 }
             }
-#pragma unroll
-            for (int i = 0; i < ACC_SLOTS; ++i) kahan_add(sum[i], err[i], part[i]);
-            __syncwarp();
         }
 #pragma unroll
         for (int i = 0; i < ACC_SLOTS; ++i) {
@@ -245,13 +354,10 @@ __global__ void __launch_bounds__(ACC_THREADS) k_accum(TraceWork w, int first, u
                     w.Hs[idx] = sum[i];
                     w.He[idx] = err[i];
                 } else {
-                    // two-sum merge of the running pair with this chunk's pair
-                    const float a = w.Hs[idx], bsum = sum[i];
-                    const float s2 = __fadd_rn(a, bsum);
-                    const float bp = __fsub_rn(s2, a);
-                    const float e2 = __fadd_rn(__fsub_rn(a, __fsub_rn(s2, bp)), __fsub_rn(bsum, bp));
-                    w.Hs[idx] = s2;
-                    w.He[idx] = w.He[idx] + err[i] + e2;
+                    float a = w.Hs[idx], ae = w.He[idx];
+                    pair_merge(a, ae, sum[i], err[i]);
+                    w.Hs[idx] = a;
+                    w.He[idx] = ae;
                 }
             }
         }
@@ -350,6 +456,13 @@ void launch_scatter(const TraceWork &w, unsigned long long chunk, int blocks, cu
 
 void launch_accum(const TraceWork &w, int first_chunk, unsigned long long chunk, int blocks, cudaStream_t st)
 {
+    // heavy keys: their segments, the segments' keys, then a warp per segment
+    const int n = w.k.S * w.k.T;
+    const int kb = std::min((n + 255) / 256, 4 * std::max(w.num_sms, 1) * 8);
+    k_seg_count<<<kb, 256, 0, st>>>(w, chunk);
+    scan_u32(w.cur, w.cnt, n, w.scan_part, &w.ctr->total_items, chunk * w.items_per_chunk, st);
+    k_seg_map<<<kb, 256, 0, st>>>(w, chunk);
+    k_accum_seg<<<blocks, ACC_THREADS, 0, st>>>(w, chunk);
     k_accum<<<blocks, ACC_THREADS, 0, st>>>(w, first_chunk, chunk);
 }
 

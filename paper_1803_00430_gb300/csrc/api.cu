@@ -98,8 +98,11 @@ int reserve(rp_ctx *c, const StepSizes &z, int B, int njobs, int total_sources, 
     if ((r = ensure(c, c->rec_e, z.rec_cap * B * sizeof(float)))) return r;
     if ((r = ensure(c, c->perm, z.rec_cap * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->rerun, z.rerun_cap * sizeof(unsigned long long)))) return r;
-    if ((r = ensure(c, c->cnt, z.keys * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->cnt, (z.keys + 1) * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->cur, z.keys * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->segkey, z.seg_cap * sizeof(uint32_t)))) return r;
+    if ((r = ensure(c, c->seg_s, z.seg_cells * sizeof(float)))) return r;
+    if ((r = ensure(c, c->seg_e, z.seg_cells * sizeof(float)))) return r;
     if ((r = ensure(c, c->off, (z.keys + 1) * sizeof(uint32_t)))) return r;
     if ((r = ensure(c, c->scan_part,
                     scan_parts(std::max<unsigned long long>(z.keys, hit_order_cells(njobs))) * sizeof(uint32_t))))
@@ -132,6 +135,10 @@ void bind_workspace(rp_ctx *c, const StepSizes &z, TraceWork &w)
     w.perm = (uint32_t *)c->perm.p;
     w.Hs = (float *)c->Hs.p;
     w.He = (float *)c->He.p;
+    w.segkey = (uint32_t *)c->segkey.p;
+    w.Ss = (float *)c->seg_s.p;
+    w.Se = (float *)c->seg_e.p;
+    w.seg_cap = z.seg_cap;
     w.items_per_chunk = z.items_per_chunk;
     w.rerun = (unsigned long long *)c->rerun.p;
     w.rerun_cap = z.rerun_cap;
@@ -275,7 +282,7 @@ int rp_destroy(rp_ctx *c)
                    &c->rec_e, &c->perm, &c->rerun,
                    &c->cnt, &c->off, &c->cur, &c->scan_part, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H,
                    &c->direct,
-                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->plan_seg, &c->rv_raw,
+                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->plan_seg, &c->segkey, &c->seg_s, &c->seg_e, &c->rv_raw,
                    &c->rv_bands, &c->rv_comb, &c->rv_ap, &c->rv_phi})
         free_buf(*b);
     for (auto &p : c->pending) {

@@ -161,8 +161,11 @@ int reserve_batch(rp_batch *b)
     if ((r = grow(c, c->rec_e, z.rec_cap * B * sizeof(float)))) return r;
     if ((r = grow(c, c->perm, z.rec_cap * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->rerun, z.rerun_cap * sizeof(unsigned long long)))) return r;
-    if ((r = grow(c, c->cnt, z.keys * sizeof(uint32_t)))) return r;
+    if ((r = grow(c, c->cnt, (z.keys + 1) * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->cur, z.keys * sizeof(uint32_t)))) return r;
+    if ((r = grow(c, c->segkey, z.seg_cap * sizeof(uint32_t)))) return r;
+    if ((r = grow(c, c->seg_s, z.seg_cells * sizeof(float)))) return r;
+    if ((r = grow(c, c->seg_e, z.seg_cells * sizeof(float)))) return r;
     if ((r = grow(c, c->off, (z.keys + 1) * sizeof(uint32_t)))) return r;
     if ((r = grow(c, c->scan_part, scan_parts(std::max<unsigned long long>(z.keys, cells)) * sizeof(uint32_t))))
         return r;
@@ -192,6 +195,10 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
     w.perm = (uint32_t *)c->perm.p;
     w.Hs = (float *)c->Hs.p;
     w.He = (float *)c->He.p;
+    w.segkey = (uint32_t *)c->segkey.p;
+    w.Ss = (float *)c->seg_s.p;
+    w.Se = (float *)c->seg_e.p;
+    w.seg_cap = g.z.seg_cap;
     w.items_per_chunk = g.z.items_per_chunk;
     w.rerun = (unsigned long long *)c->rerun.p;
     w.rerun_cap = g.z.rerun_cap;
@@ -471,6 +478,8 @@ int rp_batch_create(rp_ctx *c, const rp_batch_item *items, int32_t n, const rp_t
         zm.rerun_cap = std::max(zm.rerun_cap, g.z.rerun_cap);
         zm.keys = std::max(zm.keys, g.z.keys);
         zm.cells = std::max(zm.cells, g.z.cells);
+        zm.seg_cap = std::max(zm.seg_cap, g.z.seg_cap);
+        zm.seg_cells = std::max(zm.seg_cells, g.z.seg_cells);
         b->max_jobs = std::max(b->max_jobs, g.job_end - g.job_begin);
         b->groups.push_back(g);
     }

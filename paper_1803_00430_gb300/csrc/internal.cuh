@@ -226,9 +226,12 @@ struct TraceWork {
     uint64_t *ray_hash;     // one job: hash of primary first_ray + i at [i]
     int *status;
     // accumulation
-    uint32_t *cnt, *off, *cur, *perm;
+    uint32_t *cnt, *off, *cur, *perm;  // cnt holds S T + 1 entries (it takes the segment scan)
     uint32_t *scan_part;  // tile sums of the multi-block scans (scan_parts of the longest scan)
     float *Hs, *He;  // running compensated sums [S][B][K][T] of the group
+    uint32_t *segkey;     // [seg_cap] key of each segment of a heavy key (this chunk)
+    float *Ss, *Se;       // [seg_cap][B K] compensated sums of those segments
+    unsigned long long seg_cap;
     float *H;        // output, [global source][B][K][T]
     rp_direct *direct;  // [global sources]
     unsigned long long items_per_chunk;
@@ -278,8 +281,12 @@ cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, vo
 
 struct StepSizes {
     unsigned long long hit_cap, items, sph_cap, items_per_chunk, n_chunks, rec_cap, rerun_cap, keys, cells;
+    unsigned long long seg_cap, seg_cells;  // segments of heavy keys a chunk can hold, and their cells
     int S;
 };
+// A (source, bin) with more than ACC_SEG records in a chunk is summed in segments of
+// ACC_SEG records by separate warps, then the segments are combined in order.
+constexpr unsigned ACC_SEG = 1024;
 StepSizes step_sizes(const unsigned long long *rays, const int *sources, int njobs, int M, int B, int K, int T,
                      unsigned long long rec_budget);
 

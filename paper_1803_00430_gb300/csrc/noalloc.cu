@@ -118,21 +118,28 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     const unsigned long long o_sp = cv.take<float4>(z.hit_cap), o_sq = cv.take<uint32_t>(z.hit_cap),
                              o_sn = cv.take<float4>(z.hit_cap), o_sw = cv.take<float>(z.hit_cap * B),
                              o_sr = cv.take<uint32_t>(z.hit_cap);
-    const unsigned long long o_cnt = cv.take<uint32_t>(z.keys), o_off = cv.take<uint32_t>(z.keys + 1),
+    const unsigned long long o_cnt = cv.take<uint32_t>(z.keys + 1), o_off = cv.take<uint32_t>(z.keys + 1),
                              o_cur = cv.take<uint32_t>(z.keys);
     const unsigned long long o_part = cv.take<uint32_t>(
         scan_parts(std::max<unsigned long long>(z.keys, hit_order_cells(1, NOALLOC_CELLS_LOG2))));
     const unsigned long long o_hs = cv.take<float>(z.cells), o_he = cv.take<float>(z.cells);
     if (cv.off >= RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
-    // the rest holds contribution records (key, ray, energies, sort index) and the
-    // FP64 re-decision queue (one entry per 8 records)
-    const unsigned long long per_rec = 4ull + 4ull + 4ull * B + 4ull + 1ull + 16ull;
-    const unsigned long long rec_room = (RP_NOALLOC_SCRATCH_BYTES - cv.off) / per_rec;
+    // the rest holds contribution records (key, ray, energies, sort index), the FP64
+    // re-decision queue (one entry per 8 records) and the segment sums of heavy keys
+    // (at most 2 segments of B K sum and error pairs and a key per ACC_SEG records)
+    const unsigned long long seg_bytes = 4ull + 8ull * B * K;
+    const unsigned long long per_rec =
+        4ull + 4ull + 4ull * B + 4ull + 1ull + 16ull + (2ull * seg_bytes + ACC_SEG - 1) / ACC_SEG;
+    const unsigned long long fixed = 2ull * seg_bytes + 8ull * 256ull;  // 2 more segments, the arrays' alignment
+    if (cv.off + fixed >= RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
+    const unsigned long long rec_room = (RP_NOALLOC_SCRATCH_BYTES - cv.off - fixed) / per_rec;
     if (rec_room < z.sph_cap + (unsigned long long)std::max(S, 1)) return RP_ERR_TOO_LARGE;
     z = step_sizes(&rays, &S, 1, M, B, K, T, rec_room);
     const unsigned long long o_rk = cv.take<uint32_t>(z.rec_cap), o_rr = cv.take<uint32_t>(z.rec_cap),
                              o_re = cv.take<float>(z.rec_cap * B), o_pm = cv.take<uint32_t>(z.rec_cap);
     const unsigned long long o_rq = cv.take<unsigned long long>(z.rerun_cap);
+    const unsigned long long o_sk = cv.take<uint32_t>(z.seg_cap), o_ss = cv.take<float>(z.seg_cells),
+                             o_se = cv.take<float>(z.seg_cells);
     if (cv.off > RP_NOALLOC_SCRATCH_BYTES) return RP_ERR_TOO_LARGE;
 
     CKN(cudaSetDevice(c->device));
@@ -209,6 +216,10 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
     w.perm = (uint32_t *)(base + o_pm);
     w.Hs = (float *)(base + o_hs);
     w.He = (float *)(base + o_he);
+    w.segkey = (uint32_t *)(base + o_sk);
+    w.Ss = (float *)(base + o_ss);
+    w.Se = (float *)(base + o_se);
+    w.seg_cap = z.seg_cap;
     w.H = H;
     w.direct = direct;
     w.items_per_chunk = z.items_per_chunk;

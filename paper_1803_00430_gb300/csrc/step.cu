@@ -197,6 +197,9 @@ StepSizes step_sizes(const unsigned long long *rays, const int *sources, int njo
     z.rerun_cap = z.rec_cap / 8 + 4096;
     z.keys = (unsigned long long)z.S * T;
     z.cells = z.keys * B * K;
+    // a heavy key (more than ACC_SEG records) has at most 2 c / ACC_SEG segments
+    z.seg_cap = 2 * z.rec_cap / ACC_SEG + 2;
+    z.seg_cells = z.seg_cap * B * K;
     return z;
 }
 
