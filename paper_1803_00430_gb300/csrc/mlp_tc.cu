@@ -142,22 +142,35 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// 16 consecutive FP32 columns of this thread's TMEM lane (tmem_wait_ld completes it)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu_tc(float z) { return 0.5f * z * (1.0f + erff(z * 0.7071067811865476f)); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// GELU (erf form) with erf from Abramowitz & Stegun, Handbook of Mathematical Functions,
+// formula 7.1.26 (after Hastings): erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2),
+// t = 1 / (1 + p x) for x >= 0, |error| <= 1.5e-7, odd in x -- far below the BF16
+// rounding of the activation it feeds; fast reciprocal and exponential.
+__device__ __forceinline__ float gelu_tc(float z)
+{
+    const float x = fabsf(z) * 0.7071067811865476f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float poly = fmaf(t, 1.061405429f, -1.453152027f);
+    poly = fmaf(t, poly, 1.421413741f);
+    poly = fmaf(t, poly, -0.284496736f);
+    poly = fmaf(t, poly, 0.254829592f);
+    const float erf_abs = fmaf(-poly * t, __expf(-x * x), 1.0f);
+    const float e = copysignf(erf_abs, z);
+    return 0.5f * z * (1.0f + e);
+}
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const __grid_constant__ TcForwardParams p)
 {
@@ -279,49 +292,61 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const __grid_c
             const bool last = l == nl - 1;
             const int cw = N / 4;  // columns per quarter (a multiple of 16 for hidden layers)
             const float *bias = sbias + l * TC_MAX_N;
-            for (int c0 = part * cw; c0 < (part + 1) * cw; c0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                const int cn = min(16, (part + 1) * cw - c0);
-                if (last) {
-                    if (row < p.n) {
-                        float *y = p.Y + (size_t)row * p.ndim[l] + c0;
+            // 32 columns per round: two TMEM loads, one wait
+            for (int c00 = part * cw; c00 < (part + 1) * cw; c00 += 32) {
+                uint32_t rr[2][16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c00, rr[0]);
+                if (c00 + 16 < (part + 1) * cw) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c00 + 16), rr[1]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c0 = c00 + 16 * h;
+                    if (c0 >= (part + 1) * cw) break;
+                    float v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(rr[h][i]);
+                    const int cn = min(16, (part + 1) * cw - c0);
+                    if (last) {
+                        if (row < p.n) {
+                            float *y = p.Y + (size_t)row * p.ndim[l] + c0;
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                if (i < cn) y[i] = v[i] + bias[c0 + i];
+                        }
+                        continue;
+                    }
+                    uint32_t packed[8];
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {
+                        const float z0 = v[i] + (i < cn ? bias[c0 + i] : 0.f);
+                        const float z1 = v[i + 1] + (i + 1 < cn ? bias[c0 + i + 1] : 0.f);
+                        v[i] = z0;
+                        v[i + 1] = z1;
+                        const __nv_bfloat162 a2 = __floats2bfloat162_rn(gelu_tc(z0), gelu_tc(z1));
+                        packed[i / 2] = *reinterpret_cast<const uint32_t *>(&a2);
+                    }
+                    // next layer's A operand: K-chunk c0 / 64, row r, 16-byte units j, j + 1
+                    // of the 128-byte row, swizzled (unit index XOR row mod 8)
+                    unsigned char *rowp = act + (c0 / TC_KC) * TC_A_BYTES + r * 128;
+                    const int j = (c0 % TC_KC) / 8;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (u * 8 < cn) {
+                            uint4 w4 =
+                                make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
+                            *reinterpret_cast<uint4 *>(rowp + (((j + u) ^ (r & 7)) * 16)) = w4;
+                        }
+                    }
+                    if (p.Z && row < p.n) {  // training keeps Z and the BF16 activations
+                        float *zrow = p.Z + (size_t)l * p.act_stride + (size_t)row * N + c0;
+                        bf16 *arow = p.Act + (size_t)l * p.act_stride + (size_t)row * N + c0;
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (i < cn) y[i] = v[i] + bias[c0 + i];
+                            if (i < cn) zrow[i] = v[i];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (2 * i < cn) reinterpret_cast<uint32_t *>(arow)[i] = packed[i];
                     }
-                    continue;
-                }
-                uint32_t packed[8];
-#pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                    const float z0 = v[i] + (i < cn ? bias[c0 + i] : 0.f);
-                    const float z1 = v[i + 1] + (i + 1 < cn ? bias[c0 + i + 1] : 0.f);
-                    v[i] = z0;
-                    v[i + 1] = z1;
-                    const __nv_bfloat162 a2 = __floats2bfloat162_rn(gelu_tc(z0), gelu_tc(z1));
-                    packed[i / 2] = *reinterpret_cast<const uint32_t *>(&a2);
-                }
-                // next layer's A operand: K-chunk c0 / 64, row r, 16-byte units j, j + 1 of
-                // the 128-byte row, swizzled (unit index XOR row mod 8)
-                unsigned char *rowp = act + (c0 / TC_KC) * TC_A_BYTES + r * 128;
-                const int j = (c0 % TC_KC) / 8;
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    if (u * 8 < cn) {
-                        uint4 w4 = make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
-                        *reinterpret_cast<uint4 *>(rowp + (((j + u) ^ (r & 7)) * 16)) = w4;
-                    }
-                }
-                if (p.Z && row < p.n) {  // training keeps Z and the BF16 activations
-                    float *zrow = p.Z + (size_t)l * p.act_stride + (size_t)row * N + c0;
-                    bf16 *arow = p.Act + (size_t)l * p.act_stride + (size_t)row * N + c0;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (i < cn) zrow[i] = v[i];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (2 * i < cn) reinterpret_cast<uint32_t *>(arow)[i] = packed[i];
                 }
             }
             if (last) break;
