@@ -613,8 +613,9 @@ int rp_mlp_train_step(rp_mlp *mlp, const void *Xb, const float *T, const float *
  *   index and the shares of the FP64 re-decision queue and of the segment sums of
  *   heavy (source, bin) keys).  Larger problems return RP_ERR_TOO_LARGE before any
  *   work is enqueued.
- * The first call on a device looks up the array's device address (a host-side query,
- * with that device current).  Every call shares the array and
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current): make that first call before any stream capture begins.
+ * Every call shares the array and
  * overwrites the previous call's temporaries, so calls that may overlap on the GPU
  * (several streams or host threads) race and must be serialised by the caller.
  * Host positions are copied with cudaMemcpyAsync, and budget_refill reads the waves'
