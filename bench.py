@@ -230,6 +230,37 @@ def cpu_baseline(target_s: float = 12.0, single_s: float = 6.0):
             "single_thread": {"value": w1 / d1, "unit": UNIT, "cores": 1, "sample": _sample_text(r1, d1)}}
 
 
+def learned_at_bar(ctx) -> dict:
+    """The metric's second half: IR + reverberation-parameter updates/s at <= 5 % mean
+    decay-time error, for the plain estimator and for the learned one (a network trained
+    here, on the method's own IRs), on held-out procedural rooms and corridors whose
+    references are the plain estimator at 500k rays; the learned workflow's training
+    protocol and ray counts (python -m paper_1803_00430_gb300.learned), so that the two give
+    the same numbers; about two minutes.  Near the bar the mean error moves by a few tenths
+    of a percent between independent trace sets, which can move a form's crossing by one
+    ray count."""
+    from paper_1803_00430_gb300 import learned as L
+    t0 = time.time()
+    rays = [1000, 2000, 4000, 8000, 16000, 32000]  # the workflow's list: the traces' keys follow it
+    train = L.make_dataset(ctx, 8192, seed=101, low_rays=[2000, 4000, 8000], high_rays=100000, copies=2)
+    test_scenes = L.learned_scenes(202, 512)
+    test = L.make_dataset(ctx, 512, seed=202, low_rays=rays, high_rays=500000)
+    mlp, _ = L.fit(ctx, train, steps=6000, batch=512, lr=1e-3, weight_decay=1e-2, log_every=6000)
+    res = L.sweep(ctx, mlp, test, rays, test_scenes)
+    mlp.close()
+    out = {"bar": res["bar"], "unit": "updates/s",
+           "workload": "512 held-out procedural rooms and corridors, 1 source, 8 bands, 64 reflections, "
+                       "SH order 0, IR 2 s at 1 kHz; references: the plain estimator at 500k rays",
+           "training": "8192 scenes x (2k, 4k, 8k) rays x 2 copies, labels at 100k rays, 6000 AdamW steps",
+           "seconds": round(time.time() - t0, 1)}
+    for form, key in (("plain", "plain"), ("learned", "net")):
+        n = res[f"rays_at_bar_{key}"]
+        e = res["per_rays"][n] if n else {}
+        out[form] = {"rays": n, "updates_per_s": res[f"updates_per_s_at_bar_{key}"],
+                     "rt_err_mean": e.get(f"rt_err_mean_{key}"), "rt_err_p95": e.get(f"rt_err_p95_{key}")}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -271,6 +302,8 @@ def main():
                     help="shadow rays as warp packets or one per lane (auto: the library default, packets)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-vs-plain updates/s at the 5 %% decay-time error bar (one GPU only)")
     ap.add_argument("--rays", type=int, default=0, help="primaries per update (default: the workload's; "
                     "smaller values make a small case for profilers)")
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
@@ -463,6 +496,8 @@ def main():
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if ws == 1 and not args.no_learned:
+        line["updates_per_s_at_5pct_decay_err"] = learned_at_bar(ctx)
     print(json.dumps(line), flush=True)
     return 0
 
