@@ -9,6 +9,15 @@
 // Everything is enqueued on one stream without host synchronisation, except the
 // refill waves of a single-job step (the next wave's size is read back), so a step
 // without refill can be captured into a CUDA graph.
+//
+// Every stage is enqueued inside an NVTX range named after it ("rp:paths",
+// "rp:shadow", ...), nested in one "rp:step" range, so that timeline and profiling
+// tools can select a step or a stage (ncu --nvtx --nvtx-include "rp:step/").  Without
+// a tool attached the ranges cost a few host instructions.
+#include <cstring>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 namespace rp {
@@ -23,18 +32,40 @@ __global__ void k_copy_status(TraceWork w)
     w.stats->hits_stored += h;
 }
 
+// NVTX range name of a stage: "rp:" + the profiling name
+inline const char *nvtx_name(const char *name)
+{
+    static const char *const names[][2] = {
+        {"setup", "rp:setup"},         {"paths", "rp:paths"},           {"item_prefix", "rp:item_prefix"},
+        {"hit_order", "rp:hit_order"}, {"direct", "rp:direct"},         {"shadow", "rp:shadow"},
+        {"shadow_exact", "rp:shadow_exact"}, {"count", "rp:count"},     {"scan", "rp:scan"},
+        {"scatter", "rp:scatter"},     {"accum", "rp:accum"},           {"finalize", "rp:finalize"},
+        {"copy_status", "rp:copy_status"}};
+    for (const auto &n : names)
+        if (std::strcmp(n[0], name) == 0) return n[1];
+    return "rp:stage";
+}
+
 struct Hook {
     ProfHook fn;
     void *ctx;
     const char *name;
     Hook(ProfHook f, void *c, const char *n) : fn(f), ctx(c), name(n)
     {
+        nvtxRangePushA(nvtx_name(name));
         if (fn) fn(ctx, name, 1);
     }
     ~Hook()
     {
         if (fn) fn(ctx, name, 0);
+        nvtxRangePop();
     }
+};
+
+// the whole step
+struct StepRange {
+    StepRange() { nvtxRangePushA("rp:step"); }
+    ~StepRange() { nvtxRangePop(); }
 };
 
 constexpr int REFILL_BATCH = 16;  // refill waves enqueued between host checks
@@ -86,6 +117,7 @@ cudaError_t plan_refill(const TraceWork &w, int blocks, cudaStream_t st, ProfHoo
 
 cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, void *hook_ctx)
 {
+    const StepRange step_range;
     const TraceWork &w = L.w;
     const int S = w.k.S;
     CKS(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
