@@ -172,6 +172,61 @@ __device__ __forceinline__ float gelu_tc(float z)
     return 0.5f * z * (1.0f + e);
 }
 
+// Packed FP32 pairs (sm_100 and later): one instruction for two lanes' worth of FP32
+// arithmetic, round to nearest, the same results as the scalar operations.
+__device__ __forceinline__ unsigned long long pk2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// GELU of two values at once: the same formula as gelu_tc (Abramowitz & Stegun 7.1.26
+// for erf), its multiplications and additions on packed pairs
+__device__ __forceinline__ void gelu_tc2(float z0, float z1, float &g0, float &g1)
+{
+    const float c = 0.7071067811865476f;
+    const unsigned long long Z = pk2(z0, z1);
+    const unsigned long long X = pk2(fabsf(z0) * c, fabsf(z1) * c);
+    float d0, d1;
+    upk2(fma2(X, pk2(0.3275911f, 0.3275911f), pk2(1.0f, 1.0f)), d0, d1);
+    const unsigned long long T = pk2(__fdividef(1.0f, d0), __fdividef(1.0f, d1));
+    unsigned long long poly = fma2(T, pk2(1.061405429f, 1.061405429f), pk2(-1.453152027f, -1.453152027f));
+    poly = fma2(T, poly, pk2(1.421413741f, 1.421413741f));
+    poly = fma2(T, poly, pk2(-0.284496736f, -0.284496736f));
+    poly = fma2(T, poly, pk2(0.254829592f, 0.254829592f));
+    const unsigned long long PT = mul2(poly, T);
+    float y0, y1;
+    upk2(mul2(X, X), y0, y1);
+    const unsigned long long E = pk2(__expf(-y0), __expf(-y1));
+    float m0, m1;  // 1 - erf(|x|) ... as poly t exp(-x^2), then erf with the sign of z
+    upk2(fma2(PT, E, pk2(-1.0f, -1.0f)), m0, m1);  // -(erf |x|)
+    const unsigned long long EZ = pk2(copysignf(-m0, z0), copysignf(-m1, z1));
+    upk2(mul2(mul2(Z, pk2(0.5f, 0.5f)), add2(EZ, pk2(1.0f, 1.0f))), g0, g1);
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const __grid_constant__ TcForwardParams p)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -316,14 +371,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_forward_tc(const __grid_c
                         continue;
                     }
                     uint32_t packed[8];
+                    if (cn == 16) {  // every column of the chunk (hidden layers: always)
+                        const float2 *b2 = reinterpret_cast<const float2 *>(bias + c0);
 #pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        const float z0 = v[i] + (i < cn ? bias[c0 + i] : 0.f);
-                        const float z1 = v[i + 1] + (i + 1 < cn ? bias[c0 + i + 1] : 0.f);
-                        v[i] = z0;
-                        v[i + 1] = z1;
-                        const __nv_bfloat162 a2 = __floats2bfloat162_rn(gelu_tc(z0), gelu_tc(z1));
-                        packed[i / 2] = *reinterpret_cast<const uint32_t *>(&a2);
+                        for (int i = 0; i < 16; i += 2) {
+                            const float2 bb = b2[i / 2];
+                            float z0, z1, g0, g1;
+                            upk2(add2(pk2(v[i], v[i + 1]), pk2(bb.x, bb.y)), z0, z1);
+                            v[i] = z0;
+                            v[i + 1] = z1;
+                            gelu_tc2(z0, z1, g0, g1);
+                            const __nv_bfloat162 a2 = __floats2bfloat162_rn(g0, g1);
+                            packed[i / 2] = *reinterpret_cast<const uint32_t *>(&a2);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2) {
+                            const float z0 = v[i] + (i < cn ? bias[c0 + i] : 0.f);
+                            const float z1 = v[i + 1] + (i + 1 < cn ? bias[c0 + i + 1] : 0.f);
+                            v[i] = z0;
+                            v[i + 1] = z1;
+                            const __nv_bfloat162 a2 = __floats2bfloat162_rn(gelu_tc(z0), gelu_tc(z1));
+                            packed[i / 2] = *reinterpret_cast<const uint32_t *>(&a2);
+                        }
                     }
                     // next layer's A operand: K-chunk c0 / 64, row r, 16-byte units j, j + 1
                     // of the 128-byte row, swizzled (unit index XOR row mod 8)
