@@ -143,12 +143,14 @@ typedef struct {
     float source_radius;      /* r_s, m, > 0 */
     uint32_t scene_id;        /* Philox counter word 1 */
     int32_t budget_refill;    /* 1: spend the unused part of the N*M segment budget on
-                                 extra primaries, in deterministic waves (Section 5).
-                                 rp_trace synchronises the stream while it sizes the
-                                 waves (N*M <= 2^28: a counting pass over candidate
-                                 rays, then all waves as one; larger budgets: waves
-                                 checked every 16), so such a call cannot be captured
-                                 into a CUDA graph */
+                                 extra primaries, in deterministic waves (Section 5);
+                                 their ray ids follow the first wave's, so
+                                 first_ray + N*M <= 2^32.  rp_trace synchronises the
+                                 stream while it sizes the waves (N*M <= 2^28: passes
+                                 over candidate rays that keep what they trace, the
+                                 candidates past the waves dropped; larger budgets:
+                                 waves checked every 16), so such a call cannot be
+                                 captured into a CUDA graph */
     int32_t flags;            /* RP_FLAG_* */
 } rp_trace_params;
 
@@ -636,12 +638,18 @@ int rp_trace_noalloc(rp_scene *scene, const rp_trace_params *params, const float
  *               is recorded.
  *   record_cap  contribution records held at once; normally the worst case of a record
  *               chunk.  Records past it are dropped and RP_ERR_CAPACITY is recorded.
+ *   spec_slots  the budget refill's planner (budget_refill): speculative candidates a
+ *               store pass keeps apart; normally max(4 N, 8192).  A store pass traces
+ *               candidate rays once and keeps their results; with too few slots it
+ *               gives up and the planned rays are traced again (the same results).
+ *               -1: no store passes (counting passes, then the planned rays).  A
+ *               nonzero hit_cap or record_cap also turns the store passes off.
  * The errors come back from rp_sync_status (and in rp_trace_stats.error); the context
  * stays usable, and the next call after the limits are reset runs normally.
  * limits = NULL resets them. */
 typedef struct {
     int32_t iter_cap;
-    int32_t reserved;
+    int32_t spec_slots;
     uint64_t hit_cap;
     uint64_t record_cap;
 } rp_debug_limits;

@@ -45,13 +45,22 @@ __global__ void k_clear_counts(TraceWork w, unsigned long long chunk)
     }
 }
 
+// a source-sphere record of a ray past the waves of a store pass (chunk 0 holds them)
+__device__ __forceinline__ bool dropped_record(const TraceWork &w, unsigned long long i)
+{
+    return (unsigned long long)w.rec.rid[i] >= w.rid_end;
+}
+
 __global__ void k_count(TraceWork w, unsigned long long chunk)
 {
     if (!chunk_active(w, chunk)) return;
     const unsigned long long n = min(w.ctr->n_records, w.rec.cap);
+    const bool drop = w.rid_end && chunk == 0;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        if (drop && dropped_record(w, i)) continue;
         if (RP_IN_RANGE(w.rec.key[i], (unsigned long long)w.k.S * w.k.T, w.status)) atomicAdd(&w.cnt[w.rec.key[i]], 1u);
+    }
 }
 
 // Exclusive scan of cnt[0..n) into off[0..n] (off[n] = total; off may be cnt).  A
@@ -167,8 +176,10 @@ __global__ void k_scatter(TraceWork w, unsigned long long chunk)
 {
     if (!chunk_active(w, chunk)) return;
     const unsigned long long n = min(w.ctr->n_records, w.rec.cap);
+    const bool drop = w.rid_end && chunk == 0;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
+        if (drop && dropped_record(w, i)) continue;
         const uint32_t key = w.rec.key[i];
         if (!RP_IN_RANGE(key, (unsigned long long)w.k.S * w.k.T, w.status)) continue;
         const uint32_t pos = w.off[key] + atomicAdd(&w.cur[key], 1u);

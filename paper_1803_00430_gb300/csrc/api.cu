@@ -70,11 +70,75 @@ void prof_collect(rp_ctx *c)
     c->pending.clear();
 }
 
+// Store passes of the planned refill (one job, FP64 paths, no hashes or visit counts):
+// reflection slots past the budget N M for the paths of candidates the waves do not
+// take (N M / 16 + 2^20), and one SpecRays slot per speculative candidate
+// (max(4 N, 8192), at most N M).
+bool store_capable(const rp_trace_params *p)
+{
+    const unsigned long long budget = p->num_rays * (unsigned long long)std::max(p->max_order, 0);
+    return p->budget_refill && budget > 0 && budget <= PLAN_MAX_RAYS &&
+           !(p->flags & (RP_FLAG_FP32_PATHS | RP_FLAG_COUNT_VISITS | RP_FLAG_RAY_HASH));
+}
+
 StepSizes trace_sizes(const rp_scene *sc, const rp_trace_params *p, int S)
 {
     const unsigned long long rays = p->num_rays;
     const int K = (p->sh_order + 1) * (p->sh_order + 1);
-    return step_sizes(&rays, &S, 1, p->max_order, sc->B, K, p->num_bins, REC_BUDGET);
+    StepSizes z = step_sizes(&rays, &S, 1, p->max_order, sc->B, K, p->num_bins, REC_BUDGET);
+    if (store_capable(p)) z.hit_cap += rays * (unsigned long long)p->max_order / 16 + (1ull << 20);
+    return z;
+}
+
+unsigned long long spec_slots(const rp_trace_params *p)
+{
+    const unsigned long long budget = p->num_rays * (unsigned long long)std::max(p->max_order, 0);
+    return std::min(budget, std::max(4ull * p->num_rays, 8192ull));
+}
+
+// The refill planner's buffers: each candidate's segments (plan_seg) and the store
+// passes' speculative rays (spec; none when early reflections are kept or test limits
+// shrink the capacities).  w = NULL: reserve only.
+int bind_planner(rp_ctx *c, const rp_scene *sc, const rp_trace_params *p, bool early, TraceWork *w)
+{
+    if (w) {
+        w->plan = 0;
+        w->plan_seg = nullptr;
+        w->spec = SpecRays{};
+    }
+    const unsigned long long budget = p->num_rays * (unsigned long long)std::max(p->max_order, 0);
+    if (!p->budget_refill || budget == 0 || budget > PLAN_MAX_RAYS) return RP_OK;
+    int rc;
+    if ((rc = ensure(c, c->plan_seg, budget * sizeof(uint32_t)))) return rc;
+    if (w) w->plan_seg = (uint32_t *)c->plan_seg.p;
+    if (!store_capable(p) || early || c->dbg.hit_cap != 0 || c->dbg.record_cap != 0 || c->dbg.spec_slots < 0)
+        return RP_OK;
+    const unsigned long long cap =
+        c->dbg.spec_slots > 0 ? std::min<unsigned long long>(c->dbg.spec_slots, spec_slots(p)) : spec_slots(p);
+    if ((rc = ensure(c, c->spec, spec_bytes(cap, sc->B)))) return rc;
+    if (!w) return RP_OK;
+    const size_t B = (size_t)sc->B;
+    char *q = (char *)c->spec.p;
+    SpecRays &r = w->spec;
+    r.saved = (rp_trace_stats *)q;
+    q += sizeof(rp_trace_stats);
+    r.late = (double *)q;
+    q += cap * B * sizeof(double);
+    r.L = (double *)q;
+    q += cap * sizeof(double);
+    r.t1 = (double *)q;
+    q += cap * sizeof(double);
+    r.w = (float *)q;
+    q += cap * B * sizeof(float);
+    r.absb = (float *)q;
+    q += cap * B * sizeof(float);
+    r.esc = (uint32_t *)q;
+    q += cap * sizeof(uint32_t);
+    r.sph = (uint32_t *)q;
+    q += cap * sizeof(uint32_t);
+    r.rerun = (uint32_t *)q;
+    r.cap = cap;
+    return RP_OK;
 }
 
 // make the context workspace hold a group of these sizes with `njobs` jobs
@@ -201,6 +265,9 @@ int check_params(const rp_scene *sc, const rp_trace_params *p, int S)
     // ray ids are 32-bit: first_ray + num_rays <= 2^32, written so that it cannot wrap
     if (p->num_rays > 0xffffffffull || p->first_ray > 0x100000000ull - p->num_rays) return RP_ERR_INVALID_ARG;
     if (p->num_rays * (unsigned long long)std::max(p->max_order, 1) >= (1ull << 40)) return RP_ERR_INVALID_ARG;
+    // the refill waves continue the ids after the first wave: at most N M rays in all
+    if (p->budget_refill && p->num_rays * (unsigned long long)std::max(p->max_order, 0) > 0x100000000ull - p->first_ray)
+        return RP_ERR_INVALID_ARG;
     if (!(p->ir_rate_hz > 0.f) || !(p->speed_of_sound > 0.f) || !(p->source_radius > 0.f))
         return RP_ERR_INVALID_ARG;
     if (!std::isfinite(p->ir_rate_hz) || !std::isfinite(p->speed_of_sound) || !std::isfinite(p->source_radius))
@@ -282,7 +349,7 @@ int rp_destroy(rp_ctx *c)
                    &c->rec_e, &c->perm, &c->rerun,
                    &c->cnt, &c->off, &c->cur, &c->scan_part, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H,
                    &c->direct,
-                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->plan_seg, &c->segkey, &c->seg_s, &c->seg_e, &c->rv_raw,
+                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->plan_seg, &c->spec, &c->segkey, &c->seg_s, &c->seg_e, &c->rv_raw,
                    &c->rv_bands, &c->rv_comb, &c->rv_ap, &c->rv_phi})
         free_buf(*b);
     for (auto &p : c->pending) {
@@ -302,7 +369,7 @@ int rp_set_debug_limits(rp_ctx *c, const rp_debug_limits *lim)
         c->dbg = rp_debug_limits{0, 0, 0ull, 0ull};
         return RP_OK;
     }
-    if (lim->iter_cap < 0) return RP_ERR_INVALID_ARG;
+    if (lim->iter_cap < 0 || lim->spec_slots < -1) return RP_ERR_INVALID_ARG;
     c->dbg = *lim;
     return RP_OK;
 }
@@ -470,7 +537,8 @@ int rp_trace_reserve(rp_scene *sc, const rp_trace_params *p, int32_t S)
     int rc = check_params(sc, p, S);
     if (rc) return rc;
     CK(cudaSetDevice(sc->ctx->device));
-    return reserve(sc->ctx, trace_sizes(sc, p, S), sc->B, 1, S, 1);
+    if ((rc = reserve(sc->ctx, trace_sizes(sc, p, S), sc->B, 1, S, 1))) return rc;
+    return bind_planner(sc->ctx, sc, p, false, nullptr);
 }
 
 }  // extern "C"
@@ -538,11 +606,7 @@ int rp::trace_enqueue(rp_scene *sc, const rp_trace_params *p, const float *liste
     w.shadow_packets = shadow_packets_for(p->flags);
     w.plan = 0;
     w.plan_seg = nullptr;
-    const unsigned long long budget = p->num_rays * (unsigned long long)std::max(p->max_order, 0);
-    if (p->budget_refill && budget > 0 && budget <= PLAN_MAX_RAYS) {
-        if ((rc = ensure(c, c->plan_seg, budget * sizeof(uint32_t)))) return rc;
-        w.plan_seg = (uint32_t *)c->plan_seg.p;
-    }
+    if ((rc = bind_planner(c, sc, p, early != nullptr, &w))) return rc;
 
     StepLaunch L;
     L.w = w;

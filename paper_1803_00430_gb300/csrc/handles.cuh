@@ -48,10 +48,11 @@ struct rp_ctx {
     // workspace
     //   stored reflections (hit_*), their cell-ordered copy (shit_*) and order (hord_*),
     //   contribution records and their counting sort, running histogram sums, positions,
-    //   counters, statistics, the host-buffer update's outputs, job tables
+    //   counters, statistics, the host-buffer update's outputs, job tables, the refill
+    //   planner's segment counts (plan_seg) and speculative rays (spec)
     Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, shit_p, shit_n, shit_ws, shit_rid, hord_cell, hord_perm, hord_cnt,
         rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, scan_part, Hs, He, src, ctr, stats, H, direct, params,
-        state, jobs, js, chunks, src_job, plan_seg, segkey, seg_s, seg_e;
+        state, jobs, js, chunks, src_job, plan_seg, spec, segkey, seg_s, seg_e;
     Buf rv_raw, rv_bands, rv_comb, rv_ap, rv_phi;  // reverberator rendering: band signals, comb and all-pass
                                                   // signals, the crossover's chunk transition
     // profiling

@@ -94,7 +94,9 @@ struct TraceCounters {
     unsigned long long plan_need, plan_rays, plan_waves;
     unsigned long long plan_used, plan_count, plan_started;
     unsigned long long n_er;  // early reflections stored (rp_trace_er)
-    unsigned long long pad[2];
+    // store passes of the planned refill: ~(lowest ray id whose reflection or record
+    // found no slot), 0 if none; reflections of rays past the waves, left out of the order
+    unsigned long long store_fail, dropped_hits;
 };
 
 // Contribution records: key = (global source - first source of the group) * T + bin,
@@ -124,6 +126,30 @@ struct EarlyHits {
     int *prev = nullptr;
     unsigned long long cap = 0ull;
 };
+
+// Store passes of the planned refill keep what the candidates' paths give: reflections,
+// records and statistics.  A candidate whose place in the waves is not yet known when it
+// is traced (speculative) keeps its statistics in a slot of its own; once the waves are
+// known, the slots of the rays inside them are added to the step's statistics and the
+// rest are dropped, with their reflections and records.  Slot q holds the candidate
+// first_ray + spec_lo + q.
+struct SpecRays {
+    double *late = nullptr;   // [cap][B] energy of source-sphere hits past the histogram
+    double *L = nullptr;      // [cap] path length over the reflections
+    double *t1 = nullptr;     // [cap] distance to the first reflection
+    float *w = nullptr;       // [cap][B] band weights when the path ended
+    float *absb = nullptr;    // [cap][B] absorbed weights
+    uint32_t *esc = nullptr;  // [cap] 1: the path escaped, 0: it reached M reflections
+    uint32_t *sph = nullptr;  // [cap] source-sphere hits
+    uint32_t *rerun = nullptr;         // [cap] FP64 re-decisions of the closest hit
+    rp_trace_stats *saved = nullptr;   // the statistics before the step (restored on a fallback)
+    unsigned long long cap = 0;        // slots; 0: no store passes (the counting passes re-trace)
+};
+// bytes of the SpecRays arrays for `cap` slots and B bands (the saved statistics first)
+inline size_t spec_bytes(unsigned long long cap, int B)
+{
+    return sizeof(rp_trace_stats) + (size_t)cap * ((size_t)B * (8 + 4 + 4) + 8 + 8 + 3 * 4);
+}
 
 struct TraceConsts {
     int S;           // sources of the group (keys and accumulation span them)
@@ -208,7 +234,7 @@ struct TraceWork {
     int njobs;
     JobState *js;          // [njobs], device
     int wave_mode;         // 1: one job, rays js[0].wave_begin + v (waves / refill)
-    int plan;              // 1: the paths kernel only counts each path's segments (planned refill)
+    int plan;              // planned refill: 1 a counting pass (each path's segments only), 2 a store pass
     uint32_t *plan_seg;    // [N M] segments of candidate ray first_ray + i, or null (refill in waves)
     const RayChunk *chunks;  // [nchunks] in LPT order (wave_mode == 0)
     int nchunks;
@@ -244,12 +270,16 @@ struct TraceWork {
     Hits shits;        // point, normal, weights and ray id of the reflections in that order (shadow
                        // rays read these; the FP64 residuals stay in `hits`, found through horder.perm)
     EarlyHits er;      // early reflections (single-job steps of rp_trace_er only)
+    SpecRays spec;     // store passes of the planned refill (one job)
+    unsigned long long spec_lo = 0;  // store pass: candidates from first_ray + spec_lo on are speculative
+    unsigned long long rid_end = 0;  // nonzero: reflections and records of rays >= rid_end are dropped
 };
 
 void launch_setup(const TraceWork &w, int wave, cudaStream_t st);
 void launch_plan_block(const TraceWork &w, unsigned long long begin, unsigned long long count, cudaStream_t st);
 void launch_refill_plan(const TraceWork &w, unsigned long long candidates, cudaStream_t st);
 void launch_plan_apply(const TraceWork &w, cudaStream_t st);
+void launch_spec_fold(const TraceWork &w, unsigned long long count, cudaStream_t st);
 void launch_paths(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_item_prefix(const TraceWork &w, cudaStream_t st);
 void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st);

@@ -97,6 +97,9 @@ extern "C" int rp_trace_noalloc(rp_scene *sc, const rp_trace_params *p, const fl
         return RP_ERR_INVALID_ARG;
     // ray ids are 32-bit: first_ray + num_rays <= 2^32, written so that it cannot wrap
     if (p->num_rays > 0xffffffffull || p->first_ray > 0x100000000ull - p->num_rays) return RP_ERR_INVALID_ARG;
+    // the refill waves continue the ids after the first wave: at most N M rays in all
+    if (p->budget_refill && p->num_rays * (unsigned long long)std::max(p->max_order, 0) > 0x100000000ull - p->first_ray)
+        return RP_ERR_INVALID_ARG;
     if ((p->flags & RP_FLAG_SHADOW_PACKETS) && (p->flags & RP_FLAG_SHADOW_LANES)) return RP_ERR_INVALID_ARG;
     if (!(p->ir_rate_hz > 0.f) || !(p->speed_of_sound > 0.f) || !(p->source_radius > 0.f)) return RP_ERR_INVALID_ARG;
     if (!std::isfinite(p->ir_rate_hz) || !std::isfinite(p->speed_of_sound) || !std::isfinite(p->source_radius))

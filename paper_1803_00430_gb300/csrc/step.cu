@@ -7,8 +7,8 @@
 //   -> finalize (normalise by primaries, bin direct sound) -> status copy
 //
 // Everything is enqueued on one stream without host synchronisation, except the
-// refill waves of a single-job step (the next wave's size is read back), so a step
-// without refill can be captured into a CUDA graph.
+// refill of a single-job step (the planner's passes or the next wave's size are read
+// back), so a step without refill can be captured into a CUDA graph.
 //
 // Every stage is enqueued inside an NVTX range named after it ("rp:paths",
 // "rp:shadow", ...), nested in one "rp:step" range, so that timeline and profiling
@@ -113,23 +113,106 @@ cudaError_t plan_refill(const TraceWork &w, int blocks, cudaStream_t st, ProfHoo
     return cudaGetLastError();
 }
 
+// Planned refill with store passes: the candidates' paths are traced once and keep
+// their reflections, records and statistics.  Pass 0 takes the N primaries of the first
+// wave and speculative candidates up to 4 N (at least 4096), no further than the spare
+// reflection slots hold at M reflections a path.  A later pass reaches to where the
+// waves are predicted to end (as in plan_refill); its last spec.cap candidates are
+// speculative, the ones before them are taken as inside the waves.  When the waves
+// end inside a pass, the speculative rays past them are dropped (their statistics are
+// never added; their reflections and records are left out by rid_end).
+// ok = false: the step has to be traced again with counting passes, because a kept
+// ray lost a reflection or record for want of a slot, the waves ended before a
+// candidate taken as inside them, or the source-sphere records leave the first record
+// chunk too little room.
+cudaError_t plan_store(const TraceWork &w, int blocks, cudaStream_t st, ProfHook hook, void *hook_ctx, bool &ok,
+                       unsigned long long &K)
+{
+    ok = false;
+    const unsigned long long N = w.job0.num_rays, M = (unsigned long long)w.k.M, budget = N * M;
+    const unsigned long long spare = w.job0.hit_cap > budget ? w.job0.hit_cap - budget : 0ull;
+    const size_t B = (size_t)w.k.B;
+    TraceWork wp = w;
+    wp.plan = 2;
+    unsigned long long done = 0, lo = N;
+    unsigned long long cand = std::min(std::min(budget, std::max(4ull * N, 4096ull)), N + spare / M);
+    cand = std::min(cand, lo + w.spec.cap);
+    for (int pass = 0; pass < 64; ++pass) {
+        wp.spec_lo = lo;
+        const unsigned long long nspec = cand - lo;  // cand >= lo: see below
+        if (nspec) {
+            CKS(cudaMemsetAsync(w.spec.late, 0, nspec * B * sizeof(double), st));
+            CKS(cudaMemsetAsync(w.spec.sph, 0, nspec * sizeof(uint32_t), st));
+            CKS(cudaMemsetAsync(w.spec.rerun, 0, nspec * sizeof(uint32_t), st));
+        }
+        {
+            Hook h(hook, hook_ctx, "paths");
+            launch_plan_block(w, done, cand - done, st);
+            launch_paths(wp, blocks, st);
+        }
+        launch_refill_plan(w, cand, st);
+        if (nspec) launch_spec_fold(wp, nspec, st);
+        TraceCounters c;
+        CKS(cudaMemcpyAsync(&c, w.ctr, sizeof(c), cudaMemcpyDeviceToHost, st));
+        CKS(cudaStreamSynchronize(st));
+        const unsigned long long need = c.plan_need, rays = c.plan_rays, used = c.plan_used;
+        const unsigned long long taken = need ? cand : rays;  // candidates inside the waves
+        if (c.store_fail && ~c.store_fail < w.job0.first_ray + taken) return cudaSuccess;
+        if (need == 0) {
+            if (rays < lo || c.n_records > w.rec.cap - std::min(w.rec.cap, w.items_per_chunk)) return cudaSuccess;
+            K = rays;
+            ok = true;
+            return cudaGetLastError();
+        }
+        unsigned long long next = 2 * cand;
+        if (rays > 0 && used > 0 && used < budget) {
+            const double per_ray = (double)used / (double)rays;
+            next = (unsigned long long)(1.03 * ((double)rays + (double)(budget - used) / per_ray)) + 1024;
+        }
+        done = cand;
+        cand = std::min(budget, std::max(next, need));
+        if (cand <= done) return cudaErrorUnknown;  // cannot happen: the waves hold at most N M rays
+        lo = std::max(need, cand > w.spec.cap ? cand - w.spec.cap : 0ull);  // need <= cand
+    }
+    return cudaSuccess;  // not planned within 64 passes: counting passes instead
+}
+
 }  // namespace
 
 cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, void *hook_ctx)
 {
     const StepRange step_range;
-    const TraceWork &w = L.w;
+    TraceWork w = L.w;  // rid_end is set below once store passes have planned the refill
     const int S = w.k.S;
     CKS(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
     CKS(cudaMemsetAsync(w.js, 0, sizeof(JobState) * (size_t)w.njobs, st));
     if (L.reset_stats) CKS(cudaMemsetAsync(w.stats, 0, sizeof(rp_trace_stats), st));
+    const bool planned = L.refill && w.k.M > 0 && w.njobs == 1 && w.plan_seg;
+    const bool store = planned && w.spec.cap > 0 && w.er.cap == 0 && !w.ray_hash &&
+                       !(w.k.flags & (RP_FLAG_COUNT_VISITS | RP_FLAG_FP32_PATHS));
+    if (store) CKS(cudaMemcpyAsync(w.spec.saved, w.stats, sizeof(rp_trace_stats), cudaMemcpyDeviceToDevice, st));
     {
         Hook h(hook, hook_ctx, "setup");
         launch_setup(w, 0, st);
     }
-    const bool planned = L.refill && w.k.M > 0 && w.njobs == 1 && w.plan_seg;
-    if (planned) CKS(plan_refill(w, L.paths_blocks, st, hook, hook_ctx));
-    if (w.k.M > 0) {
+    bool stored = false;
+    if (store) {
+        unsigned long long K = 0;
+        CKS(plan_store(w, L.paths_blocks, st, hook, hook_ctx, stored, K));
+        if (stored) {
+            launch_plan_apply(w, st);
+            w.rid_end = w.job0.first_ray + K;
+        } else {
+            // the step again from its start, with counting passes
+            CKS(cudaMemcpyAsync(w.stats, w.spec.saved, sizeof(rp_trace_stats), cudaMemcpyDeviceToDevice, st));
+            CKS(cudaMemsetAsync(w.ctr, 0, sizeof(TraceCounters), st));
+            CKS(cudaMemsetAsync(w.js, 0, sizeof(JobState) * (size_t)w.njobs, st));
+            Hook h(hook, hook_ctx, "setup");
+            launch_setup(w, 0, st);
+        }
+    }
+    if (planned && !stored) CKS(plan_refill(w, L.paths_blocks, st, hook, hook_ctx));
+    if (w.k.M > 0 && !stored) {
         Hook h(hook, hook_ctx, "paths");
         launch_paths(w, L.paths_blocks, st);
     }

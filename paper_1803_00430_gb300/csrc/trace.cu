@@ -8,9 +8,12 @@
 //   k_setup       sets each job's first wave; with budget refill (one job) later
 //                 waves spend the unused part of the N*M segment budget on
 //                 floor(unused / M) extra primaries (Section 5).
-//   k_plan_block, k_refill_plan, k_plan_apply
-//                 planned refill: a counting pass of k_paths over candidate rays,
-//                 the waves' sizes from their segment counts, then all waves as one.
+//   k_plan_block, k_refill_plan, k_spec_fold, k_plan_apply
+//                 planned refill: store passes of k_paths over candidate rays (each
+//                 kept as the real pass would keep it), the waves' sizes from their
+//                 segment counts, the speculative candidates inside the waves folded
+//                 into the statistics; the rest are dropped.  Without store passes: a
+//                 counting pass, then all waves as one.
 //   k_paths       persistent: each warp takes 32 primaries at a time from a global
 //                 counter; each thread follows its path bounce by bounce: closest
 //                 hit, absorption, storage of the reflection for next-event
@@ -136,8 +139,23 @@ __device__ __forceinline__ void acc_counters(BlockAcc &a, double mfp, double mfp
     }
 }
 
+// a store pass found no slot for a reflection or record of ray rid: the host falls
+// back to the counting passes if the ray is inside the waves
+__device__ __forceinline__ void store_failed(const TraceWork &w, uint32_t rid)
+{
+    atomicMax(&w.ctr->store_fail, ~(unsigned long long)rid);
+}
+
+// slot of candidate rid among the speculative rays of a store pass, or ~0 if the
+// waves are known to take it
+__device__ __forceinline__ unsigned long long spec_slot(const TraceWork &w, uint32_t rid)
+{
+    const unsigned long long rel = (unsigned long long)rid - w.job0.first_ray;
+    return rel >= w.spec_lo ? rel - w.spec_lo : ~0ull;
+}
+
 __device__ __forceinline__ void emit_record(const TraceWork &w, uint32_t key, uint32_t rid, const float *e,
-                                            int B)
+                                            int B, bool store = false)
 {
     const unsigned long long idx = warp_append(&w.ctr->n_records);
     if (idx < w.rec.cap) {
@@ -147,6 +165,8 @@ __device__ __forceinline__ void emit_record(const TraceWork &w, uint32_t key, ui
 #pragma unroll
         for (int b = 0; b < MAXB; ++b)
             if (b < B) dst[b] = e[b];
+    } else if (store) {
+        store_failed(w, rid);
     } else {
         raise_error(w.status, RP_ERR_CAPACITY);
     }
@@ -190,11 +210,13 @@ __global__ void k_setup(TraceWork w, int wave)
 
 // Planned refill (one job).  The waves of the segment-budget refill are sized by the
 // segments of the rays before them, so traced as waves they run one after another.
-// Instead a counting pass of the paths kernel traces candidate ray ids and records each
-// path's segments; k_refill_plan then finds the waves' sizes, and one wave of all their
-// rays is traced.  The rays, paths and results are those of the waves.
+// Instead passes of the paths kernel trace candidate ray ids and record each path's
+// segments; k_refill_plan then finds the waves' sizes.  A store pass keeps everything
+// its paths give and drops the candidates past the waves afterwards; a counting pass
+// keeps only the segments, and one wave of all the waves' rays is traced after it.
+// Either way the rays, paths and results are those of the waves.
 
-// candidate rays first_ray + begin .. first_ray + begin + count for the counting pass
+// candidate rays first_ray + begin .. first_ray + begin + count for the next pass
 __global__ void k_plan_block(TraceWork w, unsigned long long begin, unsigned long long count)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -274,11 +296,53 @@ __global__ void k_plan_apply(TraceWork w)
     w.ctr->next_ray = 0;
 }
 
+// After a store pass: the statistics of its speculative candidates that the waves take
+// (all of them while the waves reach past the candidates, else those before the
+// waves' end), as the real pass would have added them.  A path's segments, its
+// reflections (one fewer if it escaped), its path length and the part after the first
+// reflection give the segment and free-path sums.
+__global__ void k_spec_fold(TraceWork w, unsigned long long count)
+{
+    __shared__ BlockAcc acc;
+    acc_init(acc);
+    __syncthreads();
+    const int B = w.k.B;
+    const unsigned long long K = w.ctr->plan_rays;
+    const unsigned long long keep =
+        w.ctr->plan_need > 0 ? count : (K > w.spec_lo ? min(count, K - w.spec_lo) : 0ull);
+    double mfp = 0.0, mfp_np = 0.0;
+    unsigned long long mc = 0, mcnp = 0, segs = 0, sph = 0, reruns = 0;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < keep;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long h = w.plan_seg[w.spec_lo + q];
+        const bool esc = w.spec.esc[q] != 0u;
+        const unsigned long long hits = esc ? h - 1 : h;
+        segs += h;
+        mc += hits;
+        if (hits > 0) {
+            mcnp += hits - 1;
+            mfp += w.spec.L[q];
+            mfp_np += w.spec.L[q] - w.spec.t1[q];
+        }
+        sph += w.spec.sph[q];
+        reruns += w.spec.rerun[q];
+        for (int b = 0; b < B; ++b) {
+            atomicAdd(esc ? &acc.esc[b] : &acc.rem[b], (double)w.spec.w[q * B + b]);
+            atomicAdd(&acc.absb[b], (double)w.spec.absb[q * B + b]);
+            const double late = w.spec.late[q * B + b];
+            if (late != 0.0) atomicAdd(&acc.late[b], late);
+        }
+    }
+    acc_counters(acc, mfp, mfp_np, mc, mcnp, segs, 0ull, sph, sph, TravStats{0u, 0u});
+    for (int o = 16; o > 0; o >>= 1) reruns += __shfl_xor_sync(FULL, reruns, o);
+    if ((threadIdx.x & 31) == 0 && reruns) atomicAdd((unsigned long long *)&w.stats->fp64_reruns, reruns);
+    acc_flush(acc, w.stats, B, 0);
+}
+
 // first shadow item of every job (sum over earlier jobs of stored reflections x
 // sources) and first reflection in the flattened order of the step
-__global__ void k_item_prefix(TraceWork w)
+__device__ __forceinline__ void item_prefix(const TraceWork &w)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     unsigned long long acc = 0, hits = 0;
     for (int j = 0; j < w.njobs; ++j) {
         w.js[j].item_off = acc;
@@ -289,6 +353,20 @@ __global__ void k_item_prefix(TraceWork w)
     }
     w.ctr->total_items = acc;
     w.ctr->total_hits = hits;
+}
+
+__global__ void k_item_prefix(TraceWork w)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) item_prefix(w);
+}
+
+// after the reflection order of a step with dropped rays: the job keeps the
+// reflections left in the order, and its shadow items follow from those
+__global__ void k_hits_kept(TraceWork w)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    w.js[0].n_hits = w.ctr->total_hits - w.ctr->dropped_hits;
+    item_prefix(w);
 }
 
 // job of flattened reflection f: the last job whose first reflection is <= f
@@ -335,6 +413,8 @@ __device__ __forceinline__ uint32_t cell_code(const SceneView &sc, float3 p, int
     return code;
 }
 
+constexpr uint32_t DROPPED_CELL = 0xffffffffu;
+
 // cell of every stored reflection, and the cell counts
 __global__ void k_hit_cells(TraceWork w)
 {
@@ -346,6 +426,11 @@ __global__ void k_hit_cells(TraceWork w)
         const SceneJob &J = w.njobs > 1 ? w.jobs[job] : w.job0;
         const unsigned long long slot = J.hit_off + (f - (w.njobs > 1 ? w.js[job].hit_prefix : 0ull));
         if (!RP_IN_RANGE(slot, w.hits.cap, w.status) || !RP_IN_RANGE(f, w.hits.cap, w.status)) continue;
+        if (w.rid_end && (unsigned long long)w.hits.rid[slot] >= w.rid_end) {
+            w.horder.cell[f] = DROPPED_CELL;  // a ray past the waves of a store pass
+            atomicAdd(&w.ctr->dropped_hits, 1ull);
+            continue;
+        }
         const float4 P = w.hits.p[slot];
         const uint32_t cell = ((uint32_t)job << bits) | cell_code(J.sc, xyz(P), bits);
         if (!RP_IN_RANGE(cell, w.horder.ncells, w.status)) continue;
@@ -363,6 +448,7 @@ __global__ void k_hit_scatter(TraceWork w)
         const int job = w.njobs > 1 ? job_of_hit(w, f) : 0;
         const SceneJob &J = w.njobs > 1 ? w.jobs[job] : w.job0;
         const unsigned long long slot = J.hit_off + (f - (w.njobs > 1 ? w.js[job].hit_prefix : 0ull));
+        if (w.horder.cell[f] == DROPPED_CELL) continue;
         if (!RP_IN_RANGE(w.horder.cell[f], w.horder.ncells, w.status)) continue;
         const uint32_t pos = atomicAdd(&w.horder.cnt[w.horder.cell[f]], 1u);
         if (RP_IN_RANGE(pos, w.hits.cap, w.status)) w.horder.perm[pos] = (uint32_t)slot;
@@ -478,7 +564,9 @@ __device__ __forceinline__ V3<R> primary_dir_r(uint32_t rid, uint32_t scene_id, 
     return v3<R>(rad * c, rad * s, z);
 }
 
-template <typename R, bool HASH, bool COUNT, bool BATCH>
+// STORE: a store pass of the planned refill (one job, FP64 paths): everything of the
+// real pass, with the statistics of speculative candidates kept per ray (SpecRays)
+template <typename R, bool HASH, bool COUNT, bool BATCH, bool STORE = false>
 __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
 {
     __shared__ int sstack[SMEM_STACK * PATH_THREADS];
@@ -495,7 +583,7 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
     const unsigned long long wave_count = BATCH ? 0ull : w.js[0].wave_count;
     const unsigned long long vtotal = BATCH ? (unsigned long long)w.nchunks * w.chunk_rays : wave_count;
     const float inv_pi_rs2 = 1.0f / (PI_F * k.rs * k.rs);
-    const bool plan = !BATCH && w.plan;  // count each path's segments only (planned refill)
+    const bool plan = !BATCH && !STORE && w.plan;  // count each path's segments only (planned refill)
 
     double mfp_np = 0.0;
     unsigned long long mcnp = 0, sphere = 0, contrib = 0, reruns = 0, segs_all = 0, mc_all = 0;
@@ -584,13 +672,15 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                 exact = true;
                 t_exact = (R)te;
                 tf = (float)te;
-                ++reruns;
+                const unsigned long long q = STORE ? spec_slot(w, rid) : ~0ull;
+                if (q != ~0ull) ++w.spec.rerun[q];
+                else ++reruns;
             }
         } else {
             tri = traverse<false, COUNT, false>(sc, of, df, sc.tmin, INFINITY, prev, sstack + threadIdx.x, tf, ts,
                                                 w.status);
         }
-        ++segs_all;
+        if (!STORE || spec_slot(w, rid) == ~0ull) ++segs_all;
         if (!plan && spec_prev && h - 1 >= k.min_order) {
             // the job's sources as spheres of radius r_s, seen through the specular bounce
             for (int s = 0; s < J.S; ++s) {
@@ -603,8 +693,13 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                 if (disc < 0.f) continue;
                 const float tsph = -bq - sqrtf(disc);
                 if (!(tsph > sc.tmin) || (tri >= 0 && !(tsph < tf))) continue;
-                ++sphere;
-                ++contrib;
+                const unsigned long long q = STORE ? spec_slot(w, rid) : ~0ull;
+                if (q != ~0ull) {
+                    ++w.spec.sph[q];
+                } else {
+                    ++sphere;
+                    ++contrib;
+                }
                 float e[MAXB];
 #pragma unroll
                 for (int b = 0; b < MAXB; ++b) e[b] = wgt[b * PATH_THREADS] * inv_pi_rs2;
@@ -621,7 +716,9 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                     binf = floorf(x);
                 }
                 if (binf < (float)T) {
-                    emit_record(w, (uint32_t)(gs - w.src_base) * (uint32_t)T + (uint32_t)binf, rid, e, B);
+                    emit_record(w, (uint32_t)(gs - w.src_base) * (uint32_t)T + (uint32_t)binf, rid, e, B, STORE);
+                } else if (q != ~0ull) {
+                    for (int b = 0; b < B; ++b) w.spec.late[q * B + b] += (double)e[b];
                 } else {
 #pragma unroll
                     for (int b = 0; b < MAXB; ++b)
@@ -635,9 +732,11 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
         }
         bool end_ray = false;
         if (tri < 0) {
+            if (!STORE || spec_slot(w, rid) == ~0ull) {
 #pragma unroll
-            for (int b = 0; b < MAXB; ++b)
-                if (b < B) atomicAdd(&acc.esc[b], (double)wgt[b * PATH_THREADS]);
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < B) atomicAdd(&acc.esc[b], (double)wgt[b * PATH_THREADS]);
+            }
             end_ray = true;
         } else {
             const float4 ta = __ldg(sc.tris + 3 * tri), tb = __ldg(sc.tris + 3 * tri + 1),
@@ -652,11 +751,16 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
             }
             L += t;
             const V3<R> p = o + d * t;
-            mfp_all += (double)t;
-            ++mc_all;
-            if (h > 1) {
-                mfp_np += (double)t;
-                ++mcnp;
+            const unsigned long long qs = STORE ? spec_slot(w, rid) : ~0ull;
+            if (qs != ~0ull) {
+                if (h == 1) w.spec.t1[qs] = (double)t;
+            } else {
+                mfp_all += (double)t;
+                ++mc_all;
+                if (h > 1) {
+                    mfp_np += (double)t;
+                    ++mcnp;
+                }
             }
             V3<R> n = cross3(e1, e2);
             n = n * ((R)1 / sqrt(dot3(n, n)));
@@ -693,14 +797,18 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
                         if (b < B) dst.ws[j * B + b] = wgt[b * PATH_THREADS] * __ldg(sb + b);
                     dst.rid[j] = rid;
                     if (early) w.er.prev[j] = prev;
+                } else if (STORE) {
+                    store_failed(w, rid);
                 } else {
                     raise_error(w.status, RP_ERR_CAPACITY);
                 }
             }
             if (h == M) {
+                if (!STORE || spec_slot(w, rid) == ~0ull) {
 #pragma unroll
-                for (int b = 0; b < MAXB; ++b)
-                    if (b < B) atomicAdd(&acc.rem[b], (double)wgt[b * PATH_THREADS]);
+                    for (int b = 0; b < MAXB; ++b)
+                        if (b < B) atomicAdd(&acc.rem[b], (double)wgt[b * PATH_THREADS]);
+                }
                 end_ray = true;
             } else {
                 const U4 r = philox4x32_10(rid, J.scene_id, (uint32_t)h, 0u, key0, key1);
@@ -737,12 +845,23 @@ __global__ void __launch_bounds__(PATH_THREADS, 4) k_paths(TraceWork w)
             }
         }
         if (end_ray) {
+            const unsigned long long q = STORE ? spec_slot(w, rid) : ~0ull;
+            if (q != ~0ull) {
+                // the speculative ray's end: band weights, absorbed weights, path length
+                for (int b = 0; b < B; ++b) {
+                    w.spec.w[q * B + b] = wgt[b * PATH_THREADS];
+                    w.spec.absb[q * B + b] = absorbed[b * PATH_THREADS];
+                }
+                w.spec.L[q] = (double)L;
+                w.spec.esc[q] = tri < 0 ? 1u : 0u;
+            } else {
 #pragma unroll
-            for (int b = 0; b < MAXB; ++b)
-                if (b < B) atomicAdd(&acc.absb[b], (double)absorbed[b * PATH_THREADS]);
+                for (int b = 0; b < MAXB; ++b)
+                    if (b < B) atomicAdd(&acc.absb[b], (double)absorbed[b * PATH_THREADS]);
+            }
             if (HASH && w.ray_hash && rid >= J.first_ray && rid - J.first_ray < J.num_rays)
                 w.ray_hash[rid - J.first_ray] = hash;
-            if (plan && RP_IN_RANGE(rid - J.first_ray, J.num_rays * (unsigned long long)M, w.status))
+            if ((plan || STORE) && RP_IN_RANGE(rid - J.first_ray, J.num_rays * (unsigned long long)M, w.status))
                 w.plan_seg[rid - J.first_ray] = (uint32_t)h;  // the path's segments
             have = false;
         }
@@ -1232,12 +1351,19 @@ void launch_refill_plan(const TraceWork &w, unsigned long long candidates, cudaS
 
 void launch_plan_apply(const TraceWork &w, cudaStream_t st) { k_plan_apply<<<1, 32, 0, st>>>(w); }
 
+void launch_spec_fold(const TraceWork &w, unsigned long long count, cudaStream_t st)
+{
+    const int blocks = (int)std::max(1ull, std::min<unsigned long long>((count + 255) / 256, 4096ull));
+    k_spec_fold<<<blocks, 256, 0, st>>>(w, count);
+}
+
 void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st)
 {
     cudaMemsetAsync(w.horder.cnt, 0, sizeof(uint32_t) * ((size_t)w.horder.ncells + 1), st);
     k_hit_cells<<<blocks, 256, 0, st>>>(w);
     launch_scan_u32(w.horder.cnt, w.horder.cnt, w.horder.ncells, w.scan_part, st);
     k_hit_scatter<<<blocks, 256, 0, st>>>(w);
+    if (w.rid_end) k_hits_kept<<<1, 32, 0, st>>>(w);
     k_hit_gather<<<blocks, 256, 0, st>>>(w);
 }
 
@@ -1254,6 +1380,10 @@ void launch_paths_r(const TraceWork &w, int blocks, cudaStream_t st)
 
 void launch_paths(const TraceWork &w, int blocks, cudaStream_t st)
 {
+    if (w.plan == 2) {  // a store pass (one job, FP64 paths, no hashes or visit counts)
+        k_paths<double, false, false, false, true><<<blocks, PATH_THREADS, 0, st>>>(w);
+        return;
+    }
     const bool batch = !w.wave_mode;
     if (w.k.flags & RP_FLAG_FP32_PATHS) {
         if (batch) launch_paths_r<float, true>(w, blocks, st);

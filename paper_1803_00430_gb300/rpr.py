@@ -136,7 +136,7 @@ class rp_reverb_render_config(C.Structure):
 
 
 class rp_debug_limits(C.Structure):
-    _fields_ = [("iter_cap", C.c_int32), ("reserved", C.c_int32), ("hit_cap", C.c_uint64),
+    _fields_ = [("iter_cap", C.c_int32), ("spec_slots", C.c_int32), ("hit_cap", C.c_uint64),
                 ("record_cap", C.c_uint64)]
 
 
@@ -343,9 +343,10 @@ class Context:
     def set_stream(self, stream):
         check(self.lib.rp_set_stream(self.h, _stream_handle(stream)), "rp_set_stream")
 
-    def set_debug_limits(self, iter_cap: int = 0, hit_cap: int = 0, record_cap: int = 0):
-        """Lower limits that exercise the error paths (all zero: the normal limits)."""
-        lim = rp_debug_limits(iter_cap, 0, hit_cap, record_cap)
+    def set_debug_limits(self, iter_cap: int = 0, hit_cap: int = 0, record_cap: int = 0, spec_slots: int = 0):
+        """Lower limits that exercise the error paths (all zero: the normal limits);
+        spec_slots limits the refill planner's speculative slots (-1: no store passes)."""
+        lim = rp_debug_limits(iter_cap, spec_slots, hit_cap, record_cap)
         check(self.lib.rp_set_debug_limits(self.h, C.byref(lim)), "rp_set_debug_limits")
 
     def pipe_peaks(self) -> tuple:

@@ -7,8 +7,8 @@ library-allocated workspace.
 Checked through the C ABI against rp_trace on the same inputs, on two calls in a
 row (the array keeps the previous call's contents, so the second call also checks
 that what must start at zero is cleared), with budget refill (rp_trace plans the
-refill waves with a counting pass, rp_trace_noalloc traces them wave by wave: the
-rays and results must be the same), plus the size limit.  This file is collected
+refill waves with store passes, rp_trace_noalloc traces them wave by wave: the rays
+and results must be the same), plus the size limit.  This file is collected
 last on purpose."""
 import numpy as np
 import pytest
