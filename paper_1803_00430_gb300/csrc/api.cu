@@ -175,6 +175,8 @@ int reserve(rp_ctx *c, const StepSizes &z, int B, int njobs, int total_sources, 
     if ((r = ensure(c, c->He, z.cells * sizeof(float)))) return r;
     if ((r = ensure(c, c->src, (size_t)(total_sources + njobs) * sizeof(float4)))) return r;
     if ((r = ensure(c, c->src_job, (size_t)std::max(total_sources, 1) * sizeof(int)))) return r;
+    if ((r = ensure(c, c->src_node, (1 + SRC_HINT_STRIDE) * (size_t)std::max(total_sources, 1) * sizeof(int))))
+        return r;
     if ((r = ensure(c, c->jobs, (size_t)njobs * sizeof(SceneJob)))) return r;
     if ((r = ensure(c, c->js, (size_t)njobs * sizeof(JobState)))) return r;
     if ((r = ensure(c, c->chunks, (size_t)std::max(nchunks, 1) * sizeof(RayChunk)))) return r;
@@ -211,6 +213,10 @@ void bind_workspace(rp_ctx *c, const StepSizes &z, TraceWork &w)
     w.js = (JobState *)c->js.p;
     w.chunks = (const RayChunk *)c->chunks.p;
     w.src_job = (const int *)c->src_job.p;
+    w.src_node = (int *)c->src_node.p;
+    // the hints after the start nodes (the buffer holds at least as many sources as this step)
+    w.src_hint = (int *)c->src_node.p + (c->src_node.bytes / sizeof(int)) / (1 + SRC_HINT_STRIDE);
+    w.region_frac = c->region_frac;
     w.pos = (const float4 *)c->src.p;
     w.shits = {(float4 *)c->shit_p.p, nullptr, (float4 *)c->shit_n.p, (float *)c->shit_ws.p,
                (uint32_t *)c->shit_rid.p, z.hit_cap};
@@ -349,7 +355,7 @@ int rp_destroy(rp_ctx *c)
                    &c->rec_e, &c->perm, &c->rerun,
                    &c->cnt, &c->off, &c->cur, &c->scan_part, &c->Hs, &c->He, &c->src, &c->ctr, &c->stats, &c->H,
                    &c->direct,
-                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->plan_seg, &c->spec, &c->segkey, &c->seg_s, &c->seg_e, &c->rv_raw,
+                   &c->params, &c->state, &c->jobs, &c->js, &c->chunks, &c->src_job, &c->src_node, &c->plan_seg, &c->spec, &c->segkey, &c->seg_s, &c->seg_e, &c->rv_raw,
                    &c->rv_bands, &c->rv_comb, &c->rv_ap, &c->rv_phi})
         free_buf(*b);
     for (auto &p : c->pending) {
@@ -448,6 +454,7 @@ int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
         (err = cudaMalloc(&sc->vidx, sizeof(int32_t) * 3 * (size_t)nt)) != cudaSuccess ||
         (err = cudaMalloc(&sc->pleaf, sizeof(int) * (size_t)nt)) != cudaSuccess ||
         (err = cudaMalloc(&sc->pint, sizeof(int) * (size_t)std::max(nt - 1, 1))) != cudaSuccess ||
+        (err = cudaMalloc(&sc->anc, sizeof(int) * (size_t)nt)) != cudaSuccess ||
         (err = cudaMemcpyAsync(sc->vidx, dt, sizeof(int32_t) * 3 * (size_t)nt, cudaMemcpyDeviceToDevice,
                                c->stream)) != cudaSuccess) {
         rc = cuda_status(err);
@@ -463,6 +470,7 @@ int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
     o.thr = sc->thr;
     o.pleaf = sc->pleaf;
     o.pint = sc->pint;
+    o.anc = sc->anc;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
@@ -511,6 +519,7 @@ int rp_scene_destroy(rp_scene *sc)
     cudaFree(sc->vidx);
     cudaFree(sc->pleaf);
     cudaFree(sc->pint);
+    cudaFree(sc->anc);
     delete sc;
     return RP_OK;
 }

@@ -46,6 +46,7 @@ struct rp_batch {
     SceneJob *d_jobs = nullptr;
     RayChunk *d_chunks = nullptr;
     int *d_src_job = nullptr;
+    int *d_src_node = nullptr;  // start node of each source's shadow-ray packets, then their latest hints
     float4 *d_pos = nullptr;
     unsigned long long *d_seed = nullptr;
     unsigned long long *h_seed = nullptr;  // pinned
@@ -218,6 +219,9 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
     w.nchunks = g.nchunks;
     w.chunk_rays = b->tuning.chunk_rays;
     w.src_job = b->d_src_job;
+    w.src_node = b->d_src_node;
+    w.src_hint = b->d_src_node + b->h_src_job.size();
+    w.region_frac = c->region_frac;
     w.src_base = g.src_begin;
     w.k.S = g.src_count;
     w.k.B = b->B;
@@ -491,6 +495,7 @@ int rp_batch_create(rp_ctx *c, const rp_batch_item *items, int32_t n, const rp_t
     }
     if ((e = cudaMalloc(&b->d_jobs, sizeof(SceneJob) * n)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_src_job, sizeof(int) * b->h_src_job.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_src_node, (1 + SRC_HINT_STRIDE) * sizeof(int) * b->h_src_job.size())) != cudaSuccess ||
         (e = cudaMalloc(&b->d_pos, sizeof(float4) * pos.size())) != cudaSuccess ||
         (e = cudaMalloc(&b->d_seed, sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMallocHost(&b->h_seed, sizeof(unsigned long long))) != cudaSuccess) {
@@ -522,6 +527,7 @@ int rp_batch_destroy(rp_batch *b)
     cudaFree(b->d_jobs);
     cudaFree(b->d_chunks);
     cudaFree(b->d_src_job);
+    cudaFree(b->d_src_node);
     cudaFree(b->d_pos);
     cudaFree(b->d_seed);
     if (b->h_seed) cudaFreeHost(b->h_seed);

@@ -331,6 +331,17 @@ __device__ __forceinline__ void child_box(int c, const uint32_t *__restrict__ or
     }
 }
 
+// the node SHADOW_HINT_UP levels above each leaf (the root where the tree is shallower)
+__global__ void k_leaf_anc(int n, const int *__restrict__ parent_int, const int *__restrict__ parent_leaf,
+                           int *__restrict__ anc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p = parent_leaf[i];
+    for (int u = 1; u < SHADOW_HINT_UP && p > 0; ++u) p = parent_int[p];
+    anc[i] = p > 0 ? p : 0;
+}
+
 __global__ void k_depth(int n, const int *__restrict__ parent_int, const int *__restrict__ parent_leaf,
                         int *__restrict__ max_depth)
 {
@@ -546,6 +557,10 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
         if (out.pleaf) RP_TRY(cudaMemcpyAsync(out.pleaf, pleaf, sizeof(int) * nt, cudaMemcpyDeviceToDevice, st));
         if (out.pint && nt > 1)
             RP_TRY(cudaMemcpyAsync(out.pint, pint, sizeof(int) * (nt - 1), cudaMemcpyDeviceToDevice, st));
+        if (out.anc) {
+            if (nt > 1) k_leaf_anc<<<nblk_tri, 256, 0, st>>>(nt, pint, pleaf, out.anc);
+            else RP_TRY(cudaMemsetAsync(out.anc, 0, sizeof(int) * nt, st));
+        }
         k_materials<<<(a.nmat + 127) / 128, 128, 0, st>>>(a.alpha, a.scat, a.nmat, a.B, out.alpha, out.scat,
                                                           out.wdiff, out.wspec, out.thr, d_status);
         RP_TRY(cudaGetLastError());

@@ -43,6 +43,7 @@ struct rp_ctx {
     int *d_status = nullptr;
     int paths_blocks = 0, shadow_blocks = 0;
     int shadow_steps = 8;  // node visits a shadow-ray lane makes between refills (one-ray-per-lane mode)
+    float region_frac = 1.0f / 32;  // a source's region: at least this share of the scene's extent
     rp_debug_limits dbg = {0, 0, 0ull, 0ull};  // rp_set_debug_limits (all zero: the normal limits)
     unsigned long long ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
     // workspace
@@ -52,7 +53,7 @@ struct rp_ctx {
     //   planner's segment counts (plan_seg) and speculative rays (spec)
     Buf hit_p, hit_plo, hit_n, hit_ws, hit_rid, shit_p, shit_n, shit_ws, shit_rid, hord_cell, hord_perm, hord_cnt,
         rec_key, rec_rid, rec_e, perm, rerun, cnt, off, cur, scan_part, Hs, He, src, ctr, stats, H, direct, params,
-        state, jobs, js, chunks, src_job, plan_seg, spec, segkey, seg_s, seg_e;
+        state, jobs, js, chunks, src_job, src_node, plan_seg, spec, segkey, seg_s, seg_e;
     Buf rv_raw, rv_bands, rv_comb, rv_ap, rv_phi;  // reverberator rendering: band signals, comb and all-pass
                                                   // signals, the crossover's chunk transition
     // profiling
@@ -70,6 +71,7 @@ struct rp_scene {
     float ray_eps = 0.f;             // the mesh's ray_epsilon (0: t_min follows the bounds)
     int32_t *vidx = nullptr;         // [num_tris][3] vertex indices (input order), for refits
     int *pleaf = nullptr, *pint = nullptr;  // parents of leaves and internal nodes (refits)
+    int *anc = nullptr;                     // ancestors of the leaves (shadow-ray hints)
     double tmin_d = 0.0;
     float4 *nodes = nullptr, *tris = nullptr;
     float *alpha = nullptr, *scat = nullptr, *wdiff = nullptr, *wspec = nullptr;
@@ -94,6 +96,7 @@ inline rp::SceneView make_view(const rp_scene *sc)
         v.lo[a] = sc->lo[a];
         v.ext[a] = sc->hi[a] - sc->lo[a];
     }
+    v.anc = sc->anc;
     return v;
 }
 

@@ -45,7 +45,13 @@ struct SceneView {
     double tmin_d;  // the same guard for FP64 re-decisions
     float lo[3];    // bounding box of the vertices (cells of the shadow-ray order)
     float ext[3];
+    const int *anc = nullptr;  // [num_tris] the node SHADOW_HINT_UP levels above each leaf (0: the root), or null
 };
+
+// A shadow-ray packet that found a blocker leaves its warp a hint: the node this many
+// levels above the blocking leaf, where the warp's next packet towards the same source
+// (the neighbouring tile) starts its walk.
+constexpr int SHADOW_HINT_UP = 3;
 
 // One scene of a trace step.  A single-scene step is a batch of one job; a
 // batched step runs many jobs (scenes, each with its own sources, listener and
@@ -182,6 +188,7 @@ struct BvhOut {
     int max_depth;
     int *pleaf = nullptr;  // if set: [nt] parent node of each leaf (Morton order), kept for refits
     int *pint = nullptr;   // if set: [nt - 1] parent node of each internal node (-1: the root)
+    int *anc = nullptr;    // if set: [nt] the node SHADOW_HINT_UP levels above each leaf (shadow-ray hints)
 };
 
 // Builds the BVH; all temporaries are allocated and freed inside.  Returns a
@@ -205,7 +212,11 @@ constexpr int SCAN_TILE = 4096;
 inline unsigned long long scan_parts(unsigned long long n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 // shadow items of a job with h stored reflections and S sources: tiles of 32
-// reflections x S sources, a short last tile padded to 32 per source
+// reflections x S sources, a short last tile padded to 32 per source.  The tiles go in
+// groups of SHADOW_TILE_GROUP, source-major inside a group, so that a warp's block of
+// SHADOW_TILE_GROUP x 32 items is neighbouring tiles towards one source.
+constexpr int SHADOW_TILE_GROUP = 32;
+constexpr int SRC_HINT_STRIDE = 8;  // ints between two sources' hints (one 32-byte sector each)
 __host__ __device__ inline unsigned long long shadow_items(unsigned long long h, int S)
 {
     return ((h + 31ull) / 32ull) * 32ull * (unsigned long long)S;
@@ -270,6 +281,12 @@ struct TraceWork {
     Hits shits;        // point, normal, weights and ray id of the reflections in that order (shadow
                        // rays read these; the FP64 residuals stay in `hits`, found through horder.perm)
     EarlyHits er;      // early reflections (single-job steps of rp_trace_er only)
+    // shadow-ray packets start at a node of the BVH around their source (src_node[global
+    // source], filled by k_src_region; null: at the root); the region is the deepest
+    // node on the source's side whose box is still at least region_frac of the scene
+    int *src_node = nullptr;
+    int *src_hint = nullptr;  // [global source * SRC_HINT_STRIDE] the latest block's hint towards it (0: none), or null
+    float region_frac = 0.f;
     SpecRays spec;     // store passes of the planned refill (one job)
     unsigned long long spec_lo = 0;  // store pass: candidates from first_ray + spec_lo on are speculative
     unsigned long long rid_end = 0;  // nonzero: reflections and records of rays >= rid_end are dropped
@@ -286,6 +303,7 @@ void launch_hit_order(const TraceWork &w, int blocks, cudaStream_t st);
 void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_shadow_exact(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_direct(const TraceWork &w, cudaStream_t st);
+void launch_src_region(const TraceWork &w, cudaStream_t st);
 void launch_clear_counts(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_count(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st);
 void launch_scan(const TraceWork &w, unsigned long long chunk, cudaStream_t st);

@@ -247,6 +247,7 @@ cudaError_t enqueue_step(const StepLaunch &L, cudaStream_t st, ProfHook hook, vo
     {
         Hook h(hook, hook_ctx, "direct");
         launch_direct(w, st);
+        launch_src_region(w, st);
     }
     for (unsigned long long ch = 0; ch < L.n_rec_chunks && S > 0; ++ch) {
         if (ch > 0) CKS(cudaMemsetAsync(&w.ctr->n_records, 0, sizeof(unsigned long long), st));
@@ -305,8 +306,9 @@ StepSizes step_sizes(const unsigned long long *rays, const int *sources, int njo
     z.hit_cap = std::max(1ull, z.hit_cap);
     z.sph_cap = z.hit_cap / 2 + 4096;
     const unsigned long long room = rec_budget > z.sph_cap + 1 ? rec_budget - z.sph_cap : 1ull << 20;
-    // a multiple of 32, so that a warp's 32 consecutive items stay one run of a tile
-    z.items_per_chunk = std::max(32ull, std::min(std::max(z.items, 1ull), room) / 32ull * 32ull);
+    // a multiple of a warp's block of tiles, so that a block's runs stay whole
+    const unsigned long long blk = 32ull * SHADOW_TILE_GROUP;
+    z.items_per_chunk = std::max(blk, std::min(std::max(z.items, 1ull), room) / blk * blk);
     z.n_chunks = (std::max(z.items, 1ull) + z.items_per_chunk - 1) / z.items_per_chunk;
     z.rec_cap = z.sph_cap + z.items_per_chunk;
     z.rerun_cap = z.rec_cap / 8 + 4096;

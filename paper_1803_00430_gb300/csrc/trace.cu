@@ -913,11 +913,12 @@ __device__ __forceinline__ void shadow_contribution(const TraceWork &w, BlockAcc
 
 // (reflection in the cell-ordered copy, global source) of shadow item q of job `job`;
 // false for a hole.  A job's items come in tiles of 32 reflections (consecutive in
-// cell order) x its S sources, source-major inside a tile: each run of 32 items is
-// rays from nearby points to one source.  The last tile of a job may hold fewer than
-// 32 reflections; its runs keep 32 slots and the slots past its reflections are
-// holes, so that every job's items and every run start at a multiple of 32 and a
-// warp's 32 consecutive items are one run.
+// cell order) x its S sources; the tiles go in groups of SHADOW_TILE_GROUP, source-major
+// inside a group: each run of 32 items is rays from nearby points to one source, and
+// consecutive runs are neighbouring tiles towards the same source.  The last tile of a
+// job may hold fewer than 32 reflections; its runs keep 32 slots and the slots past its
+// reflections are holes, so that every job's items and every run start at a multiple of
+// 32 and a warp's 32 consecutive items are one run.
 __device__ __forceinline__ bool item_slot(const TraceWork &w, bool batch, int job, unsigned long long q,
                                           unsigned long long &j, int &gs)
 {
@@ -925,11 +926,28 @@ __device__ __forceinline__ bool item_slot(const TraceWork &w, bool batch, int jo
     const JobState &js = w.js[job];
     const unsigned long long local = q - (batch ? js.item_off : 0ull);
     const unsigned long long n = min(js.n_hits, J.hit_cap);
-    const unsigned long long run = local >> 5;  // tile * S + source
-    const unsigned long long tile = run / (unsigned long long)J.S;
+    // run of 32 items: group of SHADOW_TILE_GROUP tiles, then source, then tile in the group
+    const unsigned long long run = local >> 5;
+    const unsigned long long gS = (unsigned long long)SHADOW_TILE_GROUP * (unsigned long long)J.S;
+    const unsigned long long ntiles = (n + 31ull) / 32ull;
+    unsigned long long grp, within, src, gc;
+    if (run < 0x100000000ull) {  // 32-bit divisions (64-bit ones are long instruction sequences)
+        grp = (uint32_t)run / (uint32_t)gS;  // gS <= 32 x RP_MAX_SOURCES
+        within = run - grp * gS;
+        gc = ntiles > grp * SHADOW_TILE_GROUP ? min((unsigned long long)SHADOW_TILE_GROUP, ntiles - grp * SHADOW_TILE_GROUP)
+                                              : 1ull;  // tiles in this group
+        src = (uint32_t)within / (uint32_t)gc;
+    } else {
+        grp = run / gS;
+        within = run - grp * gS;
+        gc = ntiles > grp * SHADOW_TILE_GROUP ? min((unsigned long long)SHADOW_TILE_GROUP, ntiles - grp * SHADOW_TILE_GROUP)
+                                              : 1ull;
+        src = within / gc;
+    }
+    const unsigned long long tile = grp * SHADOW_TILE_GROUP + (within - src * gc);
     const unsigned r = (unsigned)(local & 31u);
     j = js.hit_prefix + tile * 32ull + r;
-    gs = J.src_off + (int)(run - tile * (unsigned long long)J.S);
+    gs = J.src_off + (int)src;
     const bool real = tile * 32ull + r < n;
     return real && RP_IN_RANGE(j, w.shits.cap, w.status);
 }
@@ -1062,13 +1080,20 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
     acc_flush(acc, w.stats, w.k.B, 1);
 }
 
-// Shadow rays as packets.  A warp takes 32 consecutive items -- in the cell-ordered
-// tiles, rays from nearby points towards one source -- and walks the BVH with them
-// together: one node fetch per warp, and a stack of the warp's own in shared memory
-// whose entries carry the mask of lanes whose ray reached the node.  A lane tests only
-// the nodes its own ray reaches and leaves the walk once it has a clear blocker, so its
-// answer is the single-ray answer of any_hit_steps.  Items of different jobs in one
-// packet walk their own BVHs one after the other.
+// Shadow rays as packets.  A packet is 32 consecutive items -- in the cell-ordered
+// tiles, rays from nearby points towards one source -- that walk the BVH together: one
+// node fetch per warp, and a stack of the warp's own in shared memory whose entries
+// carry the mask of lanes whose ray reached the node.  A lane tests only the nodes its
+// own ray reaches and leaves the walk once it has a clear blocker, so its answer is the
+// single-ray answer of any_hit_steps.  Items of different jobs in one packet walk their
+// own BVHs one after the other.
+// A warp takes up to SHADOW_TILE_GROUP packets at a time: neighbouring tiles towards one
+// source.  Rays from neighbouring points to the same source are mostly blocked by the
+// same few triangles, so each packet first walks the subtree where the warp's previous
+// packet found a blocker (SHADOW_HINT_UP levels above that leaf; for a group's first
+// packet, the latest hint any warp left for the source, else the region around the
+// source), and only the lanes still without an answer then walk the whole tree.  Which
+// triangles are tested first changes the work, not the answers.
 template <bool COUNT, bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w, unsigned long long chunk)
 {
@@ -1089,10 +1114,21 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
     int *const sn = pnode[wid];
     unsigned *const sm = pmask[wid];
 
+    // where the warp's last packet towards source hint_gs found a blocker: the node
+    // hint_up levels above that leaf (0: none).  The next packet towards the same
+    // source starts there.
+    int hint = 0, hint_gs = -1;
+    // packets per fetch: a whole group of tiles when every warp gets several, fewer on
+    // small problems so that they still spread over the GPU
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x / 32);
+    const int per_fetch = (int)max(1ull, min((unsigned long long)SHADOW_TILE_GROUP, items / (64ull * warps)));
     while (true) {
-        unsigned long long b0 = 0;
-        if (lane == 0) b0 = atomicAdd(&w.ctr->next_item, 32ull);
-        b0 = __shfl_sync(FULL, b0, 0);
+    unsigned long long blk = 0;
+    if (lane == 0) blk = atomicAdd(&w.ctr->next_item, 32ull * per_fetch);
+    blk = __shfl_sync(FULL, blk, 0);
+    if (blk >= items) break;
+    for (int pk = 0; pk < per_fetch; ++pk) {
+        const unsigned long long b0 = blk + 32ull * pk;
         if (b0 >= items) break;
         const unsigned long long item = q0 + b0 + lane;
         bool traced = false;  // this lane traces a shadow ray
@@ -1102,11 +1138,16 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
         float3 dir = mk3(0.f, 0.f, 0.f);
         float f = 0.f, dist = 0.f;
         AnyState st = {-1, 0, INFINITY, false, false};
+        int start = 0;   // the region around the lane's source
+        int my_gs = -1;  // the lane's source
+        int blk_leaf = -1;  // the leaf whose triangle blocked this lane's ray
         if (b0 + lane < items) {
             unsigned long long j;
             int gs;
             if (BATCH) job = job_from(w, job, item);
             const bool real = item_slot(w, BATCH, job, item, j, gs);
+            my_gs = gs;
+            if (w.src_node) start = w.src_node[gs];
             const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
             const float4 P = real ? w.shits.p[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 N = real ? w.shits.n[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1155,6 +1196,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 if (!EXACT || (fabsf(margin) >= AMBIG_BARY && t >= tnear)) {
                     st.clear = true;
                     fin = true;
+                    blk_leaf = tri;
                 }
             };
             if (sc.num_nodes == 0) {
@@ -1162,9 +1204,23 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 continue;
             }
             const int iter_cap = sc.iter_cap;
-            int node = 0, sp = 0, iters = 0;
-            unsigned mask = grp;  // lanes of the group that reach `node` and have no answer yet
-            if (COUNT && lane == 0) ts.walks++;
+            int iters = 0;
+            // a run of 32 items has one source: the leader's; the packet starts where the
+            // warp's last packet towards it found a blocker, else in the source's region
+            const int pk_gs = __shfl_sync(FULL, my_gs, leader);
+            int start_node = (hint > 0 && pk_gs == hint_gs) ? hint : __shfl_sync(FULL, start, leader);
+            if (w.src_hint && pk == 0 && !(hint > 0 && pk_gs == hint_gs)) {
+                // another warp's latest hint towards this source (the previous group of tiles)
+                int th = 0;
+                if (lane == leader) th = __ldcg(w.src_hint + (size_t)pk_gs * SRC_HINT_STRIDE);
+                th = __shfl_sync(FULL, th, leader);
+                if (th > 0 && th < sc.num_nodes) start_node = th;
+            }
+            for (int phase = start_node > 0 ? 0 : 1; phase < 2; ++phase) {
+            int node = phase == 0 ? start_node : 0, sp = 0;
+            // lanes of the group that reach `node` and have no answer yet
+            unsigned mask = grp & ~__ballot_sync(FULL, fin);
+            if (COUNT && lane == 0 && mask) ts.walks++;
             while (mask) {
                 if (++iters > iter_cap) {
                     if (lane == 0) raise_error(w.status, RP_ERR_TIMEOUT);
@@ -1230,6 +1286,22 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 }
             }
             __syncwarp();
+            }
+            // the next hint: SHADOW_HINT_UP levels above the first blocking leaf of this group
+            const unsigned cl = __ballot_sync(FULL, ((grp >> lane) & 1u) && st.clear);
+            if (cl && sc.anc) {
+                const int src_lane = __ffs(cl) - 1;
+                int a = 0;
+                if (lane == src_lane && (unsigned)blk_leaf < (unsigned)sc.num_tris) {
+                    a = sc.anc[blk_leaf];
+                    if ((unsigned)a >= (unsigned)sc.num_nodes) a = 0;
+                }
+                a = __shfl_sync(FULL, a, src_lane);
+                if (a > 0) {
+                    hint = a;
+                    hint_gs = pk_gs;
+                }
+            }
         }
         if (!traced) continue;
         const bool amb = EXACT && !st.clear && st.amb_t < INFINITY;
@@ -1247,6 +1319,9 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
             ++contrib;
             shadow_contribution(w, acc, j, gs, f, dist);
         }
+    }
+    // the block's last hint, for the warp that takes the next group of tiles
+    if (w.src_hint && hint > 0 && hint_gs >= 0 && lane == 0) __stcg(w.src_hint + (size_t)hint_gs * SRC_HINT_STRIDE, hint);
     }
     acc_counters(acc, 0.0, 0.0, 0ull, 0ull, 0ull, shadow, contrib, 0ull, ts);
     acc_flush(acc, w.stats, w.k.B, 1);
@@ -1293,6 +1368,44 @@ __global__ void __launch_bounds__(SHADOW_THREADS) k_shadow_exact(TraceWork w, un
 
 // Direct sound of the group's sources: distance, time and bin in FP64, the
 // visibility ray in FP32 (re-decided in FP64 when rounding-sensitive).
+// Start node of each source's shadow-ray packets: from the root, into the child whose
+// box alone holds the source, while that child's box is at least region_frac of the
+// scene's largest extent.  Rays that end at the source cross this region last; the
+// packets walk it first, then (the lanes still without an answer) the whole tree.
+__global__ void k_src_region(TraceWork w)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.k.S) return;
+    const int gs = w.src_base + i;
+    const SceneJob &J = w.njobs > 1 ? w.jobs[w.src_job[gs]] : w.job0;
+    const SceneView &sc = J.sc;
+    const float4 s4 = __ldg(w.pos + gs);
+    const float lim = w.region_frac * fmaxf(sc.ext[0], fmaxf(sc.ext[1], sc.ext[2]));
+    int node = 0;
+    for (int d = 0; d < STACK_DEPTH && sc.num_nodes > 0 && w.region_frac > 0.f; ++d) {
+        if ((unsigned)node >= (unsigned)sc.num_nodes) {
+            node = 0;
+            break;
+        }
+        const float4 *np = sc.nodes + 4 * node;
+        const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+        const bool in0 = s4.x >= n0.x && s4.x <= n0.y && s4.y >= n0.z && s4.y <= n0.w && s4.z >= n2.x && s4.z <= n2.y;
+        const bool in1 = s4.x >= n1.x && s4.x <= n1.y && s4.y >= n1.z && s4.y <= n1.w && s4.z >= n2.z && s4.z <= n2.w;
+        const int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
+        const float e0 = fmaxf(n0.y - n0.x, fmaxf(n0.w - n0.z, n2.y - n2.x));
+        const float e1 = fmaxf(n1.y - n1.x, fmaxf(n1.w - n1.z, n2.w - n2.z));
+        // the child whose box alone holds the source
+        const bool take0 = in0 && !in1 && ch0 >= 0;
+        const bool take1 = in1 && !in0 && ch1 >= 0;
+        if (!take0 && !take1) break;
+        const float ext = take0 ? e0 : e1;
+        if (ext < lim) break;
+        node = take0 ? ch0 : ch1;
+    }
+    w.src_node[gs] = node;
+    if (w.src_hint) w.src_hint[(size_t)gs * SRC_HINT_STRIDE] = 0;
+}
+
 __global__ void __launch_bounds__(128) k_direct(TraceWork w)
 {
     __shared__ int sstack[SMEM_STACK * 128];
@@ -1421,6 +1534,11 @@ void launch_shadow(const TraceWork &w, unsigned long long chunk, int blocks, cud
 void launch_shadow_exact(const TraceWork &w, unsigned long long chunk, int blocks, cudaStream_t st)
 {
     if ((w.k.flags & RP_FLAG_FP32_PATHS) == 0) k_shadow_exact<<<blocks, SHADOW_THREADS, 0, st>>>(w, chunk);
+}
+
+void launch_src_region(const TraceWork &w, cudaStream_t st)
+{
+    if (w.k.S > 0 && w.src_node) k_src_region<<<(w.k.S + 127) / 128, 128, 0, st>>>(w);
 }
 
 void launch_direct(const TraceWork &w, cudaStream_t st)
