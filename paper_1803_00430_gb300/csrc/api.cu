@@ -217,6 +217,7 @@ void bind_workspace(rp_ctx *c, const StepSizes &z, TraceWork &w)
     // the hints after the start nodes (the buffer holds at least as many sources as this step)
     w.src_hint = (int *)c->src_node.p + (c->src_node.bytes / sizeof(int)) / (1 + SRC_HINT_STRIDE);
     w.region_frac = c->region_frac;
+    w.escalate = c->escalate;
     w.pos = (const float4 *)c->src.p;
     w.shits = {(float4 *)c->shit_p.p, nullptr, (float4 *)c->shit_n.p, (float *)c->shit_ws.p,
                (uint32_t *)c->shit_rid.p, z.hit_cap};
@@ -455,6 +456,7 @@ int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
         (err = cudaMalloc(&sc->pleaf, sizeof(int) * (size_t)nt)) != cudaSuccess ||
         (err = cudaMalloc(&sc->pint, sizeof(int) * (size_t)std::max(nt - 1, 1))) != cudaSuccess ||
         (err = cudaMalloc(&sc->anc, sizeof(int) * (size_t)nt)) != cudaSuccess ||
+        (err = cudaMalloc(&sc->up, sizeof(int) * (size_t)std::max(nt - 1, 1))) != cudaSuccess ||
         (err = cudaMemcpyAsync(sc->vidx, dt, sizeof(int32_t) * 3 * (size_t)nt, cudaMemcpyDeviceToDevice,
                                c->stream)) != cudaSuccess) {
         rc = cuda_status(err);
@@ -471,6 +473,7 @@ int rp_scene_create(rp_ctx *c, const rp_mesh_desc *m, rp_scene **out)
     o.pleaf = sc->pleaf;
     o.pint = sc->pint;
     o.anc = sc->anc;
+    o.up = sc->up;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
@@ -520,6 +523,7 @@ int rp_scene_destroy(rp_scene *sc)
     cudaFree(sc->pleaf);
     cudaFree(sc->pint);
     cudaFree(sc->anc);
+    cudaFree(sc->up);
     delete sc;
     return RP_OK;
 }

@@ -222,6 +222,7 @@ StepLaunch group_launch(const rp_batch *b, const rp_batch::Group &g)
     w.src_node = b->d_src_node;
     w.src_hint = b->d_src_node + b->h_src_job.size();
     w.region_frac = c->region_frac;
+    w.escalate = c->escalate;
     w.src_base = g.src_begin;
     w.k.S = g.src_count;
     w.k.B = b->B;

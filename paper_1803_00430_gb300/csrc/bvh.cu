@@ -342,6 +342,16 @@ __global__ void k_leaf_anc(int n, const int *__restrict__ parent_int, const int 
     anc[i] = p > 0 ? p : 0;
 }
 
+// the node SHADOW_HINT_UP levels above each internal node (the root above the top levels)
+__global__ void k_node_up(int n, const int *__restrict__ parent_int, int *__restrict__ up)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p = i;
+    for (int u = 0; u < SHADOW_HINT_UP && p > 0; ++u) p = parent_int[p];
+    up[i] = p > 0 ? p : 0;
+}
+
 __global__ void k_depth(int n, const int *__restrict__ parent_int, const int *__restrict__ parent_leaf,
                         int *__restrict__ max_depth)
 {
@@ -561,6 +571,7 @@ cudaError_t build_bvh(const BvhBuildArgs &a, BvhOut &out, int *d_status, cudaStr
             if (nt > 1) k_leaf_anc<<<nblk_tri, 256, 0, st>>>(nt, pint, pleaf, out.anc);
             else RP_TRY(cudaMemsetAsync(out.anc, 0, sizeof(int) * nt, st));
         }
+        if (out.up && nt > 1) k_node_up<<<(nt - 1 + 255) / 256, 256, 0, st>>>(nt - 1, pint, out.up);
         k_materials<<<(a.nmat + 127) / 128, 128, 0, st>>>(a.alpha, a.scat, a.nmat, a.B, out.alpha, out.scat,
                                                           out.wdiff, out.wspec, out.thr, d_status);
         RP_TRY(cudaGetLastError());

@@ -44,6 +44,7 @@ struct rp_ctx {
     int paths_blocks = 0, shadow_blocks = 0;
     int shadow_steps = 8;  // node visits a shadow-ray lane makes between refills (one-ray-per-lane mode)
     float region_frac = 1.0f / 32;  // a source's region: at least this share of the scene's extent
+    int escalate = 2;  // shadow packets: walks from further up before the root walk
     rp_debug_limits dbg = {0, 0, 0ull, 0ull};  // rp_set_debug_limits (all zero: the normal limits)
     unsigned long long ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
     // workspace
@@ -72,6 +73,7 @@ struct rp_scene {
     int32_t *vidx = nullptr;         // [num_tris][3] vertex indices (input order), for refits
     int *pleaf = nullptr, *pint = nullptr;  // parents of leaves and internal nodes (refits)
     int *anc = nullptr;                     // ancestors of the leaves (shadow-ray hints)
+    int *up = nullptr;                      // ancestors of the internal nodes (shadow-ray hints)
     double tmin_d = 0.0;
     float4 *nodes = nullptr, *tris = nullptr;
     float *alpha = nullptr, *scat = nullptr, *wdiff = nullptr, *wspec = nullptr;
@@ -97,6 +99,7 @@ inline rp::SceneView make_view(const rp_scene *sc)
         v.ext[a] = sc->hi[a] - sc->lo[a];
     }
     v.anc = sc->anc;
+    v.up = sc->up;
     return v;
 }
 

@@ -46,6 +46,7 @@ struct SceneView {
     float lo[3];    // bounding box of the vertices (cells of the shadow-ray order)
     float ext[3];
     const int *anc = nullptr;  // [num_tris] the node SHADOW_HINT_UP levels above each leaf (0: the root), or null
+    const int *up = nullptr;   // [num_nodes] the node SHADOW_HINT_UP levels above each internal node, or null
 };
 
 // A shadow-ray packet that found a blocker leaves its warp a hint: the node this many
@@ -189,6 +190,7 @@ struct BvhOut {
     int *pleaf = nullptr;  // if set: [nt] parent node of each leaf (Morton order), kept for refits
     int *pint = nullptr;   // if set: [nt - 1] parent node of each internal node (-1: the root)
     int *anc = nullptr;    // if set: [nt] the node SHADOW_HINT_UP levels above each leaf (shadow-ray hints)
+    int *up = nullptr;     // if set: [nt - 1] the node SHADOW_HINT_UP levels above each internal node
 };
 
 // Builds the BVH; all temporaries are allocated and freed inside.  Returns a
@@ -286,6 +288,7 @@ struct TraceWork {
     // node on the source's side whose box is still at least region_frac of the scene
     int *src_node = nullptr;
     int *src_hint = nullptr;  // [global source * SRC_HINT_STRIDE] the latest block's hint towards it (0: none), or null
+    int escalate = 0;  // walks from SHADOW_HINT_UP levels further up before the root walk
     float region_frac = 0.f;
     SpecRays spec;     // store passes of the planned refill (one job)
     unsigned long long spec_lo = 0;  // store pass: candidates from first_ray + spec_lo on are speculative

@@ -1216,11 +1216,22 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 th = __shfl_sync(FULL, th, leader);
                 if (th > 0 && th < sc.num_nodes) start_node = th;
             }
-            for (int phase = start_node > 0 ? 0 : 1; phase < 2; ++phase) {
-            int node = phase == 0 ? start_node : 0, sp = 0;
+            // walks from start_node, then from SHADOW_HINT_UP levels further up (escalate
+            // times, at most twice: the walks of one packet then visit a well-formed tree's
+            // nodes at most four times, within the iteration cap), then from the root, each
+            // for the lanes still without an answer
+            const int esc = min(w.escalate, 2);
+            int from = start_node;
+            for (int phase = 0; phase <= esc + 1; ++phase) {
+            if (phase > 0) {
+                if (from == 0) break;  // the root's walk answered every lane
+                from = (phase <= esc && sc.up && (unsigned)from < (unsigned)sc.num_nodes) ? sc.up[from] : 0;
+            }
+            int node = from, sp = 0;
             // lanes of the group that reach `node` and have no answer yet
             unsigned mask = grp & ~__ballot_sync(FULL, fin);
-            if (COUNT && lane == 0 && mask) ts.walks++;
+            if (!mask) break;
+            if (COUNT && lane == 0) ts.walks++;
             while (mask) {
                 if (++iters > iter_cap) {
                     if (lane == 0) raise_error(w.status, RP_ERR_TIMEOUT);
