@@ -1080,6 +1080,19 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow(TraceWork w, unsig
     acc_flush(acc, w.stats, w.k.B, 1);
 }
 
+// the vector from reflection j (cell-ordered copy) to global source gs, its squared length
+// and the cosine at the reflection; the packet kernel decides with it whether an item
+// needs a ray, and again when it sets the ray up (the same instructions, the same answer)
+__device__ __forceinline__ void shadow_geometry(const TraceWork &w, unsigned long long j, int gs, float3 &v,
+                                                float &dist2, float &cth)
+{
+    const float4 P = w.shits.p[j];
+    const float4 N = w.shits.n[j];
+    v = xyz(__ldg(w.pos + gs)) - xyz(P);
+    dist2 = dot(v, v);
+    cth = dot(xyz(N), v) / sqrtf(dist2);
+}
+
 // Shadow rays as packets.  A packet is 32 consecutive items -- in the cell-ordered
 // tiles, rays from nearby points towards one source -- that walk the BVH together: one
 // node fetch per warp, and a stack of the warp's own in shared memory whose entries
@@ -1103,6 +1116,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
     if (items == 0) return;  // a record chunk past the step's items (the whole block)
     __shared__ int pnode[SHADOW_THREADS / 32][STACK_DEPTH];
     __shared__ unsigned pmask[SHADOW_THREADS / 32][STACK_DEPTH];
+    __shared__ uint32_t pqueue[SHADOW_THREADS / 32][64];  // the warp's items to trace (offsets in the chunk)
     __shared__ BlockAcc acc;
     acc_init(acc);
     __syncthreads();
@@ -1122,18 +1136,55 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
     // small problems so that they still spread over the GPU
     const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x / 32);
     const int per_fetch = (int)max(1ull, min((unsigned long long)SHADOW_TILE_GROUP, items / (64ull * warps)));
+    uint32_t *const queue = pqueue[wid];
+    // a chunk's items fit 32 bits (a chunk holds at most the record budget's items)
+    if (items >= 0xffffff00ull) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) raise_error(w.status, RP_ERR_INVALID_ARG);
+        return;
+    }
     while (true) {
-    unsigned long long blk = 0;
-    if (lane == 0) blk = atomicAdd(&w.ctr->next_item, 32ull * per_fetch);
-    blk = __shfl_sync(FULL, blk, 0);
-    if (blk >= items) break;
-    for (int pk = 0; pk < per_fetch; ++pk) {
-        const unsigned long long b0 = blk + 32ull * pk;
-        if (b0 >= items) break;
-        const unsigned long long item = q0 + b0 + lane;
+    unsigned long long blk64 = 0;
+    if (lane == 0) blk64 = atomicAdd(&w.ctr->next_item, 32ull * per_fetch);
+    blk64 = __shfl_sync(FULL, blk64, 0);
+    if (blk64 >= items) break;
+    // The block's items whose reflection faces the source go through the warp's queue, and
+    // packets are made of 32 of them at a time: a packet's lanes all carry a ray.
+    const uint32_t bend = (uint32_t)min(blk64 + 32ull * per_fetch, items);
+    uint32_t cur = (uint32_t)blk64;
+    int nq = 0;        // queued items (warp-uniform)
+    bool first = true;  // the block's first packet
+    while (true) {
+        while (nq < 32 && cur < bend) {
+            const uint32_t it = cur + lane;
+            bool want = false;
+            if (it < bend) {
+                const int jb = BATCH ? job_of_item(w, q0 + it) : 0;
+                unsigned long long j;
+                int gs;
+                const bool real = item_slot(w, BATCH, jb, q0 + it, j, gs);
+                float3 v;
+                float dist2, cth;
+                if (real) shadow_geometry(w, j, gs, v, dist2, cth);
+                want = real && cth > 0.f;
+            }
+            const unsigned bal = __ballot_sync(FULL, want);
+            if (want) queue[nq + __popc(bal & ((1u << lane) - 1u))] = it;  // < 63
+            nq += __popc(bal);
+            cur += 32;
+        }
+        if (nq == 0) break;
+        __syncwarp();
+        const int take = min(nq, 32);
+        const bool has = lane < take;
+        const uint32_t b0 = has ? queue[lane] : 0u;
+        __syncwarp();
+        if (nq > 32 && lane < nq - 32) queue[lane] = queue[32 + lane];  // the rest to the front
+        __syncwarp();
+        nq -= take;
+        const unsigned long long item = q0 + b0;
         bool traced = false;  // this lane traces a shadow ray
-        // the job of the batch's first item (warp-uniform), then each lane's own
-        int job = BATCH ? job_of_item(w, q0 + b0) : 0;
+        // the job of the packet's first item (warp-uniform), then each lane's own
+        int job = BATCH ? job_of_item(w, q0 + __shfl_sync(FULL, b0, 0)) : 0;
         AnyRay ray;
         float3 dir = mk3(0.f, 0.f, 0.f);
         float f = 0.f, dist = 0.f;
@@ -1141,7 +1192,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
         int start = 0;   // the region around the lane's source
         int my_gs = -1;  // the lane's source
         int blk_leaf = -1;  // the leaf whose triangle blocked this lane's ray
-        if (b0 + lane < items) {
+        if (has) {
             unsigned long long j;
             int gs;
             if (BATCH) job = job_from(w, job, item);
@@ -1149,14 +1200,13 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
             my_gs = gs;
             if (w.src_node) start = w.src_node[gs];
             const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
-            const float4 P = real ? w.shits.p[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 N = real ? w.shits.n[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float3 p = xyz(P);
-            const float3 v = xyz(__ldg(w.pos + gs)) - p;
-            const float dist2 = dot(v, v);
-            dist = sqrtf(dist2);
-            const float cth = dot(xyz(N), v) / dist;
+            float3 v;
+            float dist2, cth;
+            if (real) shadow_geometry(w, j, gs, v, dist2, cth);
+            dist = real ? sqrtf(dist2) : 0.f;
             if (real && cth > 0.f) {
+                const float3 p = xyz(w.shits.p[j]);
+                const float4 N = w.shits.n[j];
                 ++shadow;
                 dir = v * (1.0f / dist);
                 ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
@@ -1209,7 +1259,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
             // warp's last packet towards it found a blocker, else in the source's region
             const int pk_gs = __shfl_sync(FULL, my_gs, leader);
             int start_node = (hint > 0 && pk_gs == hint_gs) ? hint : __shfl_sync(FULL, start, leader);
-            if (w.src_hint && pk == 0 && !(hint > 0 && pk_gs == hint_gs)) {
+            if (w.src_hint && first && !(hint > 0 && pk_gs == hint_gs)) {
                 // another warp's latest hint towards this source (the previous group of tiles)
                 int th = 0;
                 if (lane == leader) th = __ldcg(w.src_hint + (size_t)pk_gs * SRC_HINT_STRIDE);
@@ -1314,6 +1364,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
                 }
             }
         }
+        first = false;
         if (!traced) continue;
         const bool amb = EXACT && !st.clear && st.amb_t < INFINITY;
         if (amb) {
