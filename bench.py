@@ -73,8 +73,8 @@ FMA_OPS_PER_TRI = 36.0
 # DRAM bytes (read + write) of the shadow-ray launches (k_shadow_packet, the default
 # mode) of one update in an ncu capture at fewer primaries, and the shadow rays those
 # launches traced; a full-size update is credited with the same bytes per shadow ray.
-NCU_SHADOW_DRAM = {"medium": (95_254_784 + 17_812_224, 18_874_205),
-                   "large": (246_137_856 + 103_631_360, 478_253_471)}
+NCU_SHADOW_DRAM = {"medium": (96_559_360 + 20_052_736, 18_874_205),
+                   "large": (248_466_944 + 106_848_256, 478_253_471)}
 
 
 def _peaks():
