@@ -1129,7 +1129,7 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
     unsigned *const sm = pmask[wid];
 
     // where the warp's last packet towards source hint_gs found a blocker: the node
-    // hint_up levels above that leaf (0: none).  The next packet towards the same
+    // SHADOW_HINT_UP levels above that leaf (0: none).  The next packet towards the same
     // source starts there.
     int hint = 0, hint_gs = -1;
     // packets per fetch: a whole group of tiles when every warp gets several, fewer on
@@ -1143,247 +1143,248 @@ __global__ void __launch_bounds__(SHADOW_THREADS, 7) k_shadow_packet(TraceWork w
         return;
     }
     while (true) {
-    unsigned long long blk64 = 0;
-    if (lane == 0) blk64 = atomicAdd(&w.ctr->next_item, 32ull * per_fetch);
-    blk64 = __shfl_sync(FULL, blk64, 0);
-    if (blk64 >= items) break;
-    // The block's items whose reflection faces the source go through the warp's queue, and
-    // packets are made of 32 of them at a time: a packet's lanes all carry a ray.
-    const uint32_t bend = (uint32_t)min(blk64 + 32ull * per_fetch, items);
-    uint32_t cur = (uint32_t)blk64;
-    int nq = 0;        // queued items (warp-uniform)
-    bool first = true;  // the block's first packet
-    while (true) {
-        while (nq < 32 && cur < bend) {
-            const uint32_t it = cur + lane;
-            bool want = false;
-            if (it < bend) {
-                const int jb = BATCH ? job_of_item(w, q0 + it) : 0;
+        unsigned long long blk64 = 0;
+        if (lane == 0) blk64 = atomicAdd(&w.ctr->next_item, 32ull * per_fetch);
+        blk64 = __shfl_sync(FULL, blk64, 0);
+        if (blk64 >= items) break;
+        // The block's items whose reflection faces the source go through the warp's queue, and
+        // packets are made of 32 of them at a time: a packet's lanes all carry a ray.
+        const uint32_t bend = (uint32_t)min(blk64 + 32ull * per_fetch, items);
+        uint32_t cur = (uint32_t)blk64;
+        int nq = 0;        // queued items (warp-uniform)
+        bool first = true;  // the block's first packet
+        while (true) {
+            while (nq < 32 && cur < bend) {
+                const uint32_t it = cur + lane;
+                bool want = false;
+                if (it < bend) {
+                    const int jb = BATCH ? job_of_item(w, q0 + it) : 0;
+                    unsigned long long j;
+                    int gs;
+                    const bool real = item_slot(w, BATCH, jb, q0 + it, j, gs);
+                    float3 v;
+                    float dist2, cth;
+                    if (real) shadow_geometry(w, j, gs, v, dist2, cth);
+                    want = real && cth > 0.f;
+                }
+                const unsigned bal = __ballot_sync(FULL, want);
+                if (want) queue[nq + __popc(bal & ((1u << lane) - 1u))] = it;  // < 63
+                nq += __popc(bal);
+                cur += 32;
+            }
+            if (nq == 0) break;
+            __syncwarp();
+            const int take = min(nq, 32);
+            const bool has = lane < take;
+            const uint32_t b0 = has ? queue[lane] : 0u;
+            __syncwarp();
+            if (nq > 32 && lane < nq - 32) queue[lane] = queue[32 + lane];  // the rest to the front
+            __syncwarp();
+            nq -= take;
+            const unsigned long long item = q0 + b0;
+            bool traced = false;  // this lane traces a shadow ray
+            // the job of the packet's first item (warp-uniform), then each lane's own
+            int job = BATCH ? job_of_item(w, q0 + __shfl_sync(FULL, b0, 0)) : 0;
+            AnyRay ray;
+            float3 dir = mk3(0.f, 0.f, 0.f);
+            float f = 0.f, dist = 0.f;
+            AnyState st = {-1, 0, INFINITY, false, false};
+            int start = 0;   // the region around the lane's source
+            int my_gs = -1;  // the lane's source
+            int blk_leaf = -1;  // the leaf whose triangle blocked this lane's ray
+            if (has) {
                 unsigned long long j;
                 int gs;
-                const bool real = item_slot(w, BATCH, jb, q0 + it, j, gs);
+                if (BATCH) job = job_from(w, job, item);
+                const bool real = item_slot(w, BATCH, job, item, j, gs);
+                my_gs = gs;
+                if (w.src_node) start = w.src_node[gs];
+                const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
                 float3 v;
                 float dist2, cth;
                 if (real) shadow_geometry(w, j, gs, v, dist2, cth);
-                want = real && cth > 0.f;
-            }
-            const unsigned bal = __ballot_sync(FULL, want);
-            if (want) queue[nq + __popc(bal & ((1u << lane) - 1u))] = it;  // < 63
-            nq += __popc(bal);
-            cur += 32;
-        }
-        if (nq == 0) break;
-        __syncwarp();
-        const int take = min(nq, 32);
-        const bool has = lane < take;
-        const uint32_t b0 = has ? queue[lane] : 0u;
-        __syncwarp();
-        if (nq > 32 && lane < nq - 32) queue[lane] = queue[32 + lane];  // the rest to the front
-        __syncwarp();
-        nq -= take;
-        const unsigned long long item = q0 + b0;
-        bool traced = false;  // this lane traces a shadow ray
-        // the job of the packet's first item (warp-uniform), then each lane's own
-        int job = BATCH ? job_of_item(w, q0 + __shfl_sync(FULL, b0, 0)) : 0;
-        AnyRay ray;
-        float3 dir = mk3(0.f, 0.f, 0.f);
-        float f = 0.f, dist = 0.f;
-        AnyState st = {-1, 0, INFINITY, false, false};
-        int start = 0;   // the region around the lane's source
-        int my_gs = -1;  // the lane's source
-        int blk_leaf = -1;  // the leaf whose triangle blocked this lane's ray
-        if (has) {
-            unsigned long long j;
-            int gs;
-            if (BATCH) job = job_from(w, job, item);
-            const bool real = item_slot(w, BATCH, job, item, j, gs);
-            my_gs = gs;
-            if (w.src_node) start = w.src_node[gs];
-            const SceneView &sc = BATCH ? w.jobs[job].sc : w.job0.sc;
-            float3 v;
-            float dist2, cth;
-            if (real) shadow_geometry(w, j, gs, v, dist2, cth);
-            dist = real ? sqrtf(dist2) : 0.f;
-            if (real && cth > 0.f) {
-                const float3 p = xyz(w.shits.p[j]);
-                const float4 N = w.shits.n[j];
-                ++shadow;
-                dir = v * (1.0f / dist);
-                ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
-                f = cth * inv_pi / dist2;
-                traced = true;
-            }
-        }
-        const float tlo = ray.tmin * (1.0f - AMBIG_T), tnear = ray.tmin * (1.0f + AMBIG_T);
-        bool fin = !traced;  // the lane has its answer
-        unsigned todo = __ballot_sync(FULL, traced);
-        while (todo) {
-            // the lanes of one job walk that job's BVH
-            const int leader = __ffs(todo) - 1;
-            const int jl = __shfl_sync(FULL, job, leader);
-            const unsigned grp = __ballot_sync(FULL, traced && job == jl) & todo;
-            todo &= ~grp;
-            const SceneView sc = BATCH ? w.jobs[jl].sc : w.job0.sc;  // in registers for the walk
-            // direction signs of the leader's ray (the packet's rays are nearly parallel)
-            const unsigned dsign = __shfl_sync(
-                FULL, (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u), leader);
-            auto leaf = [&](int tri) {  // the lane's any-hit test of one triangle
-                if (COUNT) ts.tris++;
-                if ((unsigned)tri >= (unsigned)sc.num_tris) {
-                    raise_error(w.status, RP_ERR_INVALID_ARG);
-                    fin = true;
-                    return;
+                dist = real ? sqrtf(dist2) : 0.f;
+                if (real && cth > 0.f) {
+                    const float3 p = xyz(w.shits.p[j]);
+                    const float4 N = w.shits.n[j];
+                    ++shadow;
+                    dir = v * (1.0f / dist);
+                    ray = make_any_ray(p, dir, sc.tmin, dist, __float_as_int(N.w));
+                    f = cth * inv_pi / dist2;
+                    traced = true;
                 }
-                if (tri == ray.exclude) return;
-                float t, margin;
-                uint32_t orig;
-                const bool inside = tri_intersect(sc.tris, tri, ray.o, dir, t, orig, margin);
-                if (EXACT && t > tlo && t < ray.tmax * (1.0f + AMBIG_T) &&
-                    (fabsf(margin) < AMBIG_BARY || (inside && t < tnear)))
-                    st.amb_t = fminf(st.amb_t, t);
-                if (!inside || !(t > ray.tmin) || !(t < ray.tmax)) return;
-                st.blocked = true;
-                if (!EXACT || (fabsf(margin) >= AMBIG_BARY && t >= tnear)) {
-                    st.clear = true;
-                    fin = true;
-                    blk_leaf = tri;
-                }
-            };
-            if (sc.num_nodes == 0) {
-                if (((grp >> lane) & 1u) && sc.num_tris > 0) leaf(0);
-                continue;
             }
-            const int iter_cap = sc.iter_cap;
-            int iters = 0;
-            // a run of 32 items has one source: the leader's; the packet starts where the
-            // warp's last packet towards it found a blocker, else in the source's region
-            const int pk_gs = __shfl_sync(FULL, my_gs, leader);
-            int start_node = (hint > 0 && pk_gs == hint_gs) ? hint : __shfl_sync(FULL, start, leader);
-            if (w.src_hint && first && !(hint > 0 && pk_gs == hint_gs)) {
-                // another warp's latest hint towards this source (the previous group of tiles)
-                int th = 0;
-                if (lane == leader) th = __ldcg(w.src_hint + (size_t)pk_gs * SRC_HINT_STRIDE);
-                th = __shfl_sync(FULL, th, leader);
-                if (th > 0 && th < sc.num_nodes) start_node = th;
-            }
-            // walks from start_node, then from SHADOW_HINT_UP levels further up (escalate
-            // times, at most twice: the walks of one packet then visit a well-formed tree's
-            // nodes at most four times, within the iteration cap), then from the root, each
-            // for the lanes still without an answer
-            const int esc = min(w.escalate, 2);
-            int from = start_node;
-            for (int phase = 0; phase <= esc + 1; ++phase) {
-            if (phase > 0) {
-                if (from == 0) break;  // the root's walk answered every lane
-                from = (phase <= esc && sc.up && (unsigned)from < (unsigned)sc.num_nodes) ? sc.up[from] : 0;
-            }
-            int node = from, sp = 0;
-            // lanes of the group that reach `node` and have no answer yet
-            unsigned mask = grp & ~__ballot_sync(FULL, fin);
-            if (!mask) break;
-            if (COUNT && lane == 0) ts.walks++;
-            while (mask) {
-                if (++iters > iter_cap) {
-                    if (lane == 0) raise_error(w.status, RP_ERR_TIMEOUT);
-                    break;
-                }
-                if ((unsigned)node >= (unsigned)sc.num_nodes) {
-                    if (lane == 0) raise_error(w.status, RP_ERR_INVALID_ARG);
-                    break;
-                }
-                const bool need = (mask >> lane) & 1u;
-                if (COUNT && need) ts.nodes++;
-                if (COUNT && lane == 0) ts.steps++;
-                const float4 *np = sc.nodes + 4 * node;
-                const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
-                const float a0 = n0.x * ray.idir.x - ray.ood.x, b0 = n0.y * ray.idir.x - ray.ood.x;
-                const float a1 = n0.z * ray.idir.y - ray.ood.y, b1 = n0.w * ray.idir.y - ray.ood.y;
-                const float a2 = n2.x * ray.idir.z - ray.ood.z, b2 = n2.y * ray.idir.z - ray.ood.z;
-                const float c0min = slab_in(a0, b0, a1, b1, a2, b2, ray.tmin);
-                const float c0max = slab_out(a0, b0, a1, b1, a2, b2, ray.tmax);
-                const float a3 = n1.x * ray.idir.x - ray.ood.x, b3 = n1.y * ray.idir.x - ray.ood.x;
-                const float a4 = n1.z * ray.idir.y - ray.ood.y, b4 = n1.w * ray.idir.y - ray.ood.y;
-                const float a5 = n2.z * ray.idir.z - ray.ood.z, b5 = n2.w * ray.idir.z - ray.ood.z;
-                const float c1min = slab_in(a3, b3, a4, b4, a5, b5, ray.tmin);
-                const float c1max = slab_out(a3, b3, a4, b4, a5, b5, ray.tmax);
-                const bool h0 = need && c0min <= c0max, h1 = need && c1min <= c1max;
-                const int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
-                if (h0 && ch0 < 0) leaf(~ch0);
-                if (h1 && ch1 < 0 && !fin) leaf(~ch1);
-                const unsigned m0 = __ballot_sync(FULL, h0 && ch0 >= 0 && !fin);
-                const unsigned m1 = __ballot_sync(FULL, h1 && ch1 >= 0 && !fin);
-                if (m0 && m1) {
-                    // the child on the side the rays head to goes first: on the node's
-                    // split axis, the higher child for rays heading up the axis
-                    const int split = __float_as_int(n3.z);
-                    const bool swap = (((dsign >> (split & 3)) ^ (unsigned)(split >> 2)) & 1u) == 0u;
-                    if (sp >= STACK_DEPTH) {
-                        if (lane == 0) raise_error(w.status, RP_ERR_STACK_OVERFLOW);
-                        break;
+            const float tlo = ray.tmin * (1.0f - AMBIG_T), tnear = ray.tmin * (1.0f + AMBIG_T);
+            bool fin = !traced;  // the lane has its answer
+            unsigned todo = __ballot_sync(FULL, traced);
+            while (todo) {
+                // the lanes of one job walk that job's BVH
+                const int leader = __ffs(todo) - 1;
+                const int jl = __shfl_sync(FULL, job, leader);
+                const unsigned grp = __ballot_sync(FULL, traced && job == jl) & todo;
+                todo &= ~grp;
+                const SceneView sc = BATCH ? w.jobs[jl].sc : w.job0.sc;  // in registers for the walk
+                // direction signs of the leader's ray (the packet's rays are nearly parallel)
+                const unsigned dsign = __shfl_sync(
+                    FULL, (dir.x < 0.f ? 1u : 0u) | (dir.y < 0.f ? 2u : 0u) | (dir.z < 0.f ? 4u : 0u), leader);
+                auto leaf = [&](int tri) {  // the lane's any-hit test of one triangle
+                    if (COUNT) ts.tris++;
+                    if ((unsigned)tri >= (unsigned)sc.num_tris) {
+                        raise_error(w.status, RP_ERR_INVALID_ARG);
+                        fin = true;
+                        return;
                     }
-                    if (lane == 0) {
-                        sn[sp] = swap ? ch0 : ch1;
-                        sm[sp] = swap ? m0 : m1;
+                    if (tri == ray.exclude) return;
+                    float t, margin;
+                    uint32_t orig;
+                    const bool inside = tri_intersect(sc.tris, tri, ray.o, dir, t, orig, margin);
+                    if (EXACT && t > tlo && t < ray.tmax * (1.0f + AMBIG_T) &&
+                        (fabsf(margin) < AMBIG_BARY || (inside && t < tnear)))
+                        st.amb_t = fminf(st.amb_t, t);
+                    if (!inside || !(t > ray.tmin) || !(t < ray.tmax)) return;
+                    st.blocked = true;
+                    if (!EXACT || (fabsf(margin) >= AMBIG_BARY && t >= tnear)) {
+                        st.clear = true;
+                        fin = true;
+                        blk_leaf = tri;
+                    }
+                };
+                if (sc.num_nodes == 0) {
+                    if (((grp >> lane) & 1u) && sc.num_tris > 0) leaf(0);
+                    continue;
+                }
+                const int iter_cap = sc.iter_cap;
+                int iters = 0;
+                // the packet's items are neighbouring tiles towards one source (two at the edge
+                // of a group): it starts where the warp's last packet towards the leader's source
+                // found a blocker, else in that source's region (any start gives the same answers)
+                const int pk_gs = __shfl_sync(FULL, my_gs, leader);
+                int start_node = (hint > 0 && pk_gs == hint_gs) ? hint : __shfl_sync(FULL, start, leader);
+                if (w.src_hint && first && !(hint > 0 && pk_gs == hint_gs)) {
+                    // another warp's latest hint towards this source (the previous group of tiles)
+                    int th = 0;
+                    if (lane == leader) th = __ldcg(w.src_hint + (size_t)pk_gs * SRC_HINT_STRIDE);
+                    th = __shfl_sync(FULL, th, leader);
+                    if (th > 0 && th < sc.num_nodes) start_node = th;
+                }
+                // walks from start_node, then from SHADOW_HINT_UP levels further up (escalate
+                // times, at most twice: the walks of one packet then visit a well-formed tree's
+                // nodes at most four times, within the iteration cap), then from the root, each
+                // for the lanes still without an answer
+                const int esc = min(w.escalate, 2);
+                int from = start_node;
+                for (int phase = 0; phase <= esc + 1; ++phase) {
+                    if (phase > 0) {
+                        if (from == 0) break;  // the root's walk answered every lane
+                        from = (phase <= esc && sc.up && (unsigned)from < (unsigned)sc.num_nodes) ? sc.up[from] : 0;
+                    }
+                    int node = from, sp = 0;
+                    // lanes of the group that reach `node` and have no answer yet
+                    unsigned mask = grp & ~__ballot_sync(FULL, fin);
+                    if (!mask) break;
+                    if (COUNT && lane == 0) ts.walks++;
+                    while (mask) {
+                        if (++iters > iter_cap) {
+                            if (lane == 0) raise_error(w.status, RP_ERR_TIMEOUT);
+                            break;
+                        }
+                        if ((unsigned)node >= (unsigned)sc.num_nodes) {
+                            if (lane == 0) raise_error(w.status, RP_ERR_INVALID_ARG);
+                            break;
+                        }
+                        const bool need = (mask >> lane) & 1u;
+                        if (COUNT && need) ts.nodes++;
+                        if (COUNT && lane == 0) ts.steps++;
+                        const float4 *np = sc.nodes + 4 * node;
+                        const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+                        const float a0 = n0.x * ray.idir.x - ray.ood.x, b0 = n0.y * ray.idir.x - ray.ood.x;
+                        const float a1 = n0.z * ray.idir.y - ray.ood.y, b1 = n0.w * ray.idir.y - ray.ood.y;
+                        const float a2 = n2.x * ray.idir.z - ray.ood.z, b2 = n2.y * ray.idir.z - ray.ood.z;
+                        const float c0min = slab_in(a0, b0, a1, b1, a2, b2, ray.tmin);
+                        const float c0max = slab_out(a0, b0, a1, b1, a2, b2, ray.tmax);
+                        const float a3 = n1.x * ray.idir.x - ray.ood.x, b3 = n1.y * ray.idir.x - ray.ood.x;
+                        const float a4 = n1.z * ray.idir.y - ray.ood.y, b4 = n1.w * ray.idir.y - ray.ood.y;
+                        const float a5 = n2.z * ray.idir.z - ray.ood.z, b5 = n2.w * ray.idir.z - ray.ood.z;
+                        const float c1min = slab_in(a3, b3, a4, b4, a5, b5, ray.tmin);
+                        const float c1max = slab_out(a3, b3, a4, b4, a5, b5, ray.tmax);
+                        const bool h0 = need && c0min <= c0max, h1 = need && c1min <= c1max;
+                        const int ch0 = __float_as_int(n3.x), ch1 = __float_as_int(n3.y);
+                        if (h0 && ch0 < 0) leaf(~ch0);
+                        if (h1 && ch1 < 0 && !fin) leaf(~ch1);
+                        const unsigned m0 = __ballot_sync(FULL, h0 && ch0 >= 0 && !fin);
+                        const unsigned m1 = __ballot_sync(FULL, h1 && ch1 >= 0 && !fin);
+                        if (m0 && m1) {
+                            // the child on the side the rays head to goes first: on the node's
+                            // split axis, the higher child for rays heading up the axis
+                            const int split = __float_as_int(n3.z);
+                            const bool swap = (((dsign >> (split & 3)) ^ (unsigned)(split >> 2)) & 1u) == 0u;
+                            if (sp >= STACK_DEPTH) {
+                                if (lane == 0) raise_error(w.status, RP_ERR_STACK_OVERFLOW);
+                                break;
+                            }
+                            if (lane == 0) {
+                                sn[sp] = swap ? ch0 : ch1;
+                                sm[sp] = swap ? m0 : m1;
+                            }
+                            __syncwarp();
+                            ++sp;
+                            node = swap ? ch1 : ch0;
+                            mask = swap ? m1 : m0;
+                        } else if (m0) {
+                            node = ch0;
+                            mask = m0;
+                        } else if (m1) {
+                            node = ch1;
+                            mask = m1;
+                        } else {
+                            // pop until an entry still has lanes without an answer
+                            const unsigned answered = __ballot_sync(FULL, fin);
+                            mask = 0;
+                            while (mask == 0 && sp > 0) {
+                                --sp;
+                                node = sn[sp];
+                                mask = sm[sp] & ~answered;
+                            }
+                        }
                     }
                     __syncwarp();
-                    ++sp;
-                    node = swap ? ch1 : ch0;
-                    mask = swap ? m1 : m0;
-                } else if (m0) {
-                    node = ch0;
-                    mask = m0;
-                } else if (m1) {
-                    node = ch1;
-                    mask = m1;
-                } else {
-                    // pop until an entry still has lanes without an answer
-                    const unsigned answered = __ballot_sync(FULL, fin);
-                    mask = 0;
-                    while (mask == 0 && sp > 0) {
-                        --sp;
-                        node = sn[sp];
-                        mask = sm[sp] & ~answered;
+                }
+                // the next hint: SHADOW_HINT_UP levels above the first blocking leaf of this group
+                const unsigned cl = __ballot_sync(FULL, ((grp >> lane) & 1u) && st.clear);
+                if (cl && sc.anc) {
+                    const int src_lane = __ffs(cl) - 1;
+                    int a = 0;
+                    if (lane == src_lane && (unsigned)blk_leaf < (unsigned)sc.num_tris) {
+                        a = sc.anc[blk_leaf];
+                        if ((unsigned)a >= (unsigned)sc.num_nodes) a = 0;
+                    }
+                    a = __shfl_sync(FULL, a, src_lane);
+                    if (a > 0) {
+                        hint = a;
+                        hint_gs = pk_gs;
                     }
                 }
             }
-            __syncwarp();
-            }
-            // the next hint: SHADOW_HINT_UP levels above the first blocking leaf of this group
-            const unsigned cl = __ballot_sync(FULL, ((grp >> lane) & 1u) && st.clear);
-            if (cl && sc.anc) {
-                const int src_lane = __ffs(cl) - 1;
-                int a = 0;
-                if (lane == src_lane && (unsigned)blk_leaf < (unsigned)sc.num_tris) {
-                    a = sc.anc[blk_leaf];
-                    if ((unsigned)a >= (unsigned)sc.num_nodes) a = 0;
-                }
-                a = __shfl_sync(FULL, a, src_lane);
-                if (a > 0) {
-                    hint = a;
-                    hint_gs = pk_gs;
+            first = false;
+            if (!traced) continue;
+            const bool amb = EXACT && !st.clear && st.amb_t < INFINITY;
+            if (amb) {
+                const unsigned long long r = warp_append(&w.ctr->n_rerun);
+                if (r < w.rerun_cap) {
+                    w.rerun[r] = item;
+                    continue;
                 }
             }
-        }
-        first = false;
-        if (!traced) continue;
-        const bool amb = EXACT && !st.clear && st.amb_t < INFINITY;
-        if (amb) {
-            const unsigned long long r = warp_append(&w.ctr->n_rerun);
-            if (r < w.rerun_cap) {
-                w.rerun[r] = item;
-                continue;
+            if (!st.blocked) {
+                unsigned long long j;
+                int gs;
+                item_slot(w, BATCH, job, item, j, gs);
+                ++contrib;
+                shadow_contribution(w, acc, j, gs, f, dist);
             }
         }
-        if (!st.blocked) {
-            unsigned long long j;
-            int gs;
-            item_slot(w, BATCH, job, item, j, gs);
-            ++contrib;
-            shadow_contribution(w, acc, j, gs, f, dist);
-        }
-    }
-    // the block's last hint, for the warp that takes the next group of tiles
-    if (w.src_hint && hint > 0 && hint_gs >= 0 && lane == 0) __stcg(w.src_hint + (size_t)hint_gs * SRC_HINT_STRIDE, hint);
+        // the block's last hint, for the warp that takes the next group of tiles
+        if (w.src_hint && hint > 0 && hint_gs >= 0 && lane == 0) __stcg(w.src_hint + (size_t)hint_gs * SRC_HINT_STRIDE, hint);
     }
     acc_counters(acc, 0.0, 0.0, 0ull, 0ull, 0ull, shadow, contrib, 0ull, ts);
     acc_flush(acc, w.stats, w.k.B, 1);
