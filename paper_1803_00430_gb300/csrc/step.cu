@@ -306,9 +306,10 @@ StepSizes step_sizes(const unsigned long long *rays, const int *sources, int njo
     z.hit_cap = std::max(1ull, z.hit_cap);
     z.sph_cap = z.hit_cap / 2 + 4096;
     const unsigned long long room = rec_budget > z.sph_cap + 1 ? rec_budget - z.sph_cap : 1ull << 20;
-    // a multiple of a warp's block of tiles, so that a block's runs stay whole
-    const unsigned long long blk = 32ull * SHADOW_TILE_GROUP;
-    z.items_per_chunk = std::max(blk, std::min(std::max(z.items, 1ull), room) / blk * blk);
+    // a multiple of a warp's block of tiles, so that a block's runs stay whole (a multiple
+    // of 32 when the room is smaller: a warp's 32 consecutive items stay one run)
+    const unsigned long long blk = 32ull * SHADOW_TILE_GROUP, fit = std::min(std::max(z.items, 1ull), room);
+    z.items_per_chunk = fit >= blk ? fit / blk * blk : std::max(32ull, fit / 32ull * 32ull);
     z.n_chunks = (std::max(z.items, 1ull) + z.items_per_chunk - 1) / z.items_per_chunk;
     z.rec_cap = z.sph_cap + z.items_per_chunk;
     z.rerun_cap = z.rec_cap / 8 + 4096;
