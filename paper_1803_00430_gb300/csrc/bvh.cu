@@ -281,7 +281,7 @@ __global__ void k_ploc_flags(int c, const int *__restrict__ nn, uint32_t *__rest
     keep[i] = mutual && i > j ? 0u : 1u;
 }
 
-// merges (new node id = c - 2 - rank among this round's merges) and compaction
+// merges (new node id = c - 2 - rank among this iteration's merges) and compaction
 __global__ void k_ploc_merge(int c, const int *__restrict__ cref, const float4 *__restrict__ clo,
                              const float4 *__restrict__ chi, const int *__restrict__ nn,
                              const uint32_t *__restrict__ keep, const uint32_t *__restrict__ kpos,
