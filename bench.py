@@ -75,6 +75,23 @@ FMA_OPS_PER_TRI = 36.0
 # launches traced; a full-size update is credited with the same bytes per shadow ray.
 NCU_SHADOW_DRAM = {"medium": (96_559_360 + 20_052_736, 18_874_205),
                    "large": (248_466_944 + 106_848_256, 478_253_471)}
+# warp instructions (smsp__inst_executed.sum) of the same captures, and their shadow rays
+NCU_SHADOW_INST = {"medium": (1_518_944_434, 18_874_205), "large": (26_590_588_617, 478_253_471)}
+
+
+def issue_roofline(workload: str, kernel: str, shadow_rays: float, seconds: float, sms: int, sm_mhz):
+    """The shadow-ray kernel against the SMs' instruction issue: warp instructions per shadow
+    ray from the ncu capture at fewer primaries, times the update's shadow rays, over the
+    kernel's time; the peak is one warp instruction per clock on each of an SM's four
+    schedulers.  None when there is no capture for the workload or no clock."""
+    ins = NCU_SHADOW_INST.get(workload)
+    if kernel != "shadow" or not ins or not sm_mhz or seconds <= 0 or sms <= 0:
+        return None
+    achieved = ins[0] / ins[1] * shadow_rays / seconds / 1e12
+    peak = sms * 4 * sm_mhz * 1e6 / 1e12
+    return {"achieved": achieved, "peak": peak, "frac": achieved / peak, "unit": "T warp instructions/s",
+            "note": "warp instructions per shadow ray from an ncu capture at fewer primaries; peak = SMs x 4 "
+                    "schedulers x the median SM clock sampled during the timed steps"}
 
 
 def _peaks():
@@ -494,6 +511,12 @@ def main():
                 "ms_per_step": 1000 * e2e_total / e2e_steps if e2e_total > 0 else None, "steps": e2e_steps},
         "clocks": clocks,
     }
+    issue = issue_roofline(args.workload if not args.fp32_paths and args.shadow_mode != "lanes" else "",
+                           name, float(st["shadow_rays"]), avg_s,
+                           torch.cuda.get_device_properties(0).multi_processor_count,
+                           clocks.get("sm_mhz") or clocks.get("sm_max_mhz"))
+    if issue:
+        line["roofline"]["issue"] = issue
     if cpu:
         line["cpu_baseline"] = cpu
     if ws == 1 and not args.no_learned:

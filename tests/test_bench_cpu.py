@@ -58,3 +58,17 @@ def test_reference_arm_on_the_medium_workload():
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
     assert d["config"]["workload"].startswith("medium") and d["steps"] == 2 and d["value"] > 0
+
+
+def test_issue_roofline_of_the_shadow_kernel():
+    sys.path.insert(0, ROOT)
+    import bench
+    # the city's update: 23.9G shadow rays in 1.344 s on 152 SMs at 2070 MHz
+    r = bench.issue_roofline("large", "shadow", 23.9e9, 1.344, 152, 2070.0)
+    per_ray = bench.NCU_SHADOW_INST["large"][0] / bench.NCU_SHADOW_INST["large"][1]
+    assert abs(r["achieved"] - per_ray * 23.9e9 / 1.344 / 1e12) < 1e-9
+    assert abs(r["peak"] - 152 * 4 * 2070e6 / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12 and 0.0 < r["frac"] < 1.0
+    assert bench.issue_roofline("large", "paths", 23.9e9, 1.344, 152, 2070.0) is None
+    assert bench.issue_roofline("paper", "shadow", 2.1e4, 1e-4, 152, 2070.0) is None
+    assert bench.issue_roofline("large", "shadow", 23.9e9, 1.344, 152, None) is None
